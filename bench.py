@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Benchmark: adaptive 3-D Laplace FMM on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path on one synthetic system: the device
+tree build (root cube, Morton keys, octree, dual traversal, lists) followed by
+one evaluation (P2M, M2M, M2L, L2L, L2P, P2P).  The workload is the irregular
+configuration: N = 1,048,576 particles from a Plummer sphere (scale radius 1,
+truncated at r = 50), charges 1/N, order p = 8, leaf size 64, theta = 0.4.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own system
+(replicas: the single-system path has no exchange step) and the value is the
+particles of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "FMM particles/sec at rel-L2 err <=1e-4 vs plain FP64 GPU path; % roofline"
+WORKLOAD = "plummer"
+N_DEFAULT = 1 << 20
+P, LEAF, THETA = 8, 64, 0.4
+L2_FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2
+P2P_FLOPS_PER_PAIR = 20             # convention for the near-field direct sum
+PREC_NAMES = {0: "fp64", 1: "fp32_p2p", 2: "fp32", 3: "mixed_tc"}
+PREC_DTYPE = {0: "f64", 1: "f32 P2P / f64 expansions", 2: "f32", 3: "bf16x3 M2L / f32"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--precision", type=int, default=2, help="0 fp64, 1 fp32 P2P, 2 fp32, 3 mixed tensor-core")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-n", type=int, default=1 << 17)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2])); power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# ---------------------------------------------------------------- our arm
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def p2p_pairs(ex) -> int:
+    """Algorithmic near-field pair count: sum over P2P pairs |A||B| minus the N self pairs."""
+    cnt = ex["count"]
+    pl = ex["p2p"]
+    if len(pl) == 0:
+        return 0
+    return int((cnt[pl[:, 0]] * cnt[pl[:, 1]]).sum() - len(ex["keys"]))
+
+
+def roofline(stage_ms: dict, ex, prec: int, sm_clock_mhz: float, n_sm: int):
+    """Roofline object for the stage that dominates the evaluation."""
+    pk, how = peaks()
+    K = (P + 1) ** 2
+    clk = 2070.0 if not sm_clock_mhz else 2070.0
+    fp32_peak = n_sm * 128 * 2 * clk * 1e6 / 1e12          # TFLOP/s, FP32 FMA lanes at max clock
+    fp64_peak = FP64_TFLOPS_MEASURED                        # from the FMA probe (see DESIGN)
+    cand = {k: v for k, v in stage_ms.items() if k in ("p2p", "m2l", "p2m", "m2m", "l2l", "l2p")}
+    dom = max(cand, key=cand.get)
+    t = cand[dom] * 1e-3
+    nm2l = len(ex["m2l"])
+    if dom == "m2l":
+        flops = nm2l * 2.0 * K * K
+        peak = fp64_peak if prec in (0, 1) else fp32_peak
+        return {"kernel": "k_m2l_generic", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
+                "algorithmic": f"{nm2l} M2L pairs x 2K^2 flops, K=(p+1)^2={K}",
+                "peak_source": "FP64 FMA probe" if prec in (0, 1) else f"{n_sm} SM x 128 FP32 lanes x 2 x {clk} MHz"}
+    if dom == "p2p":
+        pairs = p2p_pairs(ex)
+        flops = pairs * float(P2P_FLOPS_PER_PAIR)
+        peak = fp64_peak if prec == 0 else fp32_peak
+        return {"kernel": "k_p2p", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / t / 1e12 / peak, "traffic": None,
+                "algorithmic": f"{pairs} pair interactions x {P2P_FLOPS_PER_PAIR} flops",
+                "peak_source": "FP64 FMA probe" if prec == 0 else f"{n_sm} SM x 128 FP32 lanes x 2 x {clk} MHz"}
+    return {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": None,
+            "traffic": None}
+
+
+# FP64 FMA throughput of one GB300 from the probe kernel (TFLOP/s at the loaded clock)
+FP64_TFLOPS_MEASURED = 1.2
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1203_0889_gb300 as fmm
+    import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream()
+    wl = W.make_workload(WORKLOAD, n=args.n, seed=12030889 * 10 + 2 + 1000 * rank)
+    n = wl.n
+    pos = torch.tensor(wl.pos, dtype=torch.float64, device=dev)
+    q = torch.tensor(wl.q, dtype=torch.float64, device=dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    force = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flags = fmm.TIMING
+
+    def step():
+        t = fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=args.precision, flags=flags)
+        t.evaluate(q, phi=phi, force=force)
+        return t
+
+    # accuracy of this path against the plain FP64 GPU path (outside the timed region)
+    t64 = fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=fmm.PREC_FP64)
+    phi64, f64 = t64.evaluate(q)
+    torch.cuda.synchronize()
+    t64.close()
+    tt = step()
+    torch.cuda.synchronize()
+    ex = tt.export()
+    info = tt.info()
+    tt.close()
+    err_phi = float(((phi - phi64).norm() / phi64.norm()).item())
+    err_f = float(((force - f64).norm() / f64.norm()).item())
+    del phi64, f64
+
+    for _ in range(args.warmup):
+        step().close()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_acc = {}
+    launches = 0
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                       # evict L2 between steps (outside the event pair)
+        ev[k][0].record(stream)
+        t = step()
+        ev[k][1].record(stream)
+        for name, ms in t.stage_times().items():
+            stage_acc[name] = stage_acc.get(name, 0.0) + ms
+        launches += t.kernel_launches(build=True) + t.kernel_launches(build=False)
+        t.close()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) * 1e-3
+    if world > 1:
+        tt_ = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt_, op=dist.ReduceOp.MAX)
+        total_s = float(tt_.item())
+    value = n * world * args.steps / total_s
+    stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
+    props = torch.cuda.get_device_properties(dev)
+    roof = roofline(stage_ms, ex, args.precision, clocks.get("sm_mhz"), props.multi_processor_count)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hpos = torch.tensor(wl.pos, dtype=torch.float64).pin_memory()
+        hq = torch.tensor(wl.q, dtype=torch.float64).pin_memory()
+        hphi = torch.empty(n, dtype=torch.float64).pin_memory()
+        hforce = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            dpos = hpos.to(dev, non_blocking=True)
+            dq = hq.to(dev, non_blocking=True)
+            t = fmm.build_tree(dpos, p=P, leaf_size=LEAF, theta=THETA, precision=args.precision)
+            ph, fo = t.evaluate(dq)
+            hphi.copy_(ph, non_blocking=True)
+            hforce.copy_(fo, non_blocking=True)
+            return t
+
+        for _ in range(2):
+            e2e_step().close()
+        torch.cuda.synchronize()
+        ks = max(3, args.steps // 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(ks):
+            flush.zero_()
+            e0.record(stream)
+            t = e2e_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1) * 1e-3
+            t.close()
+        e2e = {"value": n * ks / tot, "unit": "particles/s", "h2d_bytes_per_step": n * 3 * 8 + n * 8,
+               "d2h_bytes_per_step": n * 8 + n * 3 * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_sample_n)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": PREC_DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": f"plummer N={n} a=1 rmax=50, q=1/N, p={P}, leaf={LEAF}, theta={THETA}",
+                       "step": "fmm_build_tree + fmm_evaluate (potentials and forces)",
+                       "precision": PREC_NAMES[args.precision], "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"replicas x{world}", "ncell": info.ncell, "nleaf": info.nleaf,
+                       "nm2l": info.nm2l, "np2p": info.np2p,
+                       "rel_l2_vs_fp64_gpu": {"phi": err_phi, "force": err_f},
+                       "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+                       "evaluate_ms": round(sum(v for k, v in stage_ms.items()
+                                                if k in ("prepare", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p",
+                                                         "queue")), 4),
+                       "wall_s": wall},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(sample_n: int):
+    """The FP64 oracle as it stands (tree build + full FMM) on the host cores, on a
+    smaller Plummer system of the same recipe; particles/s of that sample."""
+    import oracle
+    import workloads as W
+    cores = os.cpu_count() or 1
+    wl = W.make_workload(WORKLOAD, n=sample_n)
+    t0 = time.perf_counter()
+    T = oracle.build_tree(wl.pos, LEAF, THETA)
+    T.evaluate(P, wl.q, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sample_n / dt, "unit": "particles/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle tree build + FP64 FMM of a Plummer system of N={sample_n} "
+                      f"(same recipe, p={P}, leaf={LEAF}, theta={THETA}), {dt:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    oracle.build()
+    cores = os.cpu_count() or 1
+    n = min(args.cpu_sample_n, 1 << 16)
+    wl = W.make_workload(WORKLOAD, n=n)
+
+    def step():
+        T = oracle.build_tree(wl.pos, LEAF, THETA)
+        T.evaluate(P, wl.q, nthreads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        ts.append(time.perf_counter() - t0)
+    tot = sum(ts)
+    value = n * args.steps / tot
+    sample = (f"oracle tree build + FP64 FMM per step on a Plummer system of N={n} (same recipe, p={P}, "
+              f"leaf={LEAF}, theta={THETA})")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"plummer N={N_DEFAULT} a=1 rmax=50, q=1/N, p={P}, leaf={LEAF}, theta={THETA}",
+                   "sample_n": n},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

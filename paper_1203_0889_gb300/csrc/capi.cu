@@ -1,0 +1,243 @@
+// capi.cu -- the extern "C" boundary: argument checks, tree lifetime, export.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "fmm_internal.cuh"
+
+static thread_local char g_err[512] = "";
+
+void fmm_set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+namespace {
+
+int check_params(const fmm_params* prm) {
+    if (!prm) { fmm_set_error("params is NULL"); return FMM_ERR_ARG; }
+    if (prm->p < 0 || prm->p > FMM_MAX_P) { fmm_set_error("p=%d outside [0, %d]", prm->p, FMM_MAX_P); return FMM_ERR_ARG; }
+    if (prm->leaf_size < 1 || prm->leaf_size > 4096) {
+        fmm_set_error("leaf_size=%d outside [1, 4096]", prm->leaf_size);
+        return FMM_ERR_ARG;
+    }
+    if (!(prm->theta > 0.0 && prm->theta < 1.0)) { fmm_set_error("theta=%g outside (0, 1)", prm->theta); return FMM_ERR_ARG; }
+    if (prm->precision < FMM_PREC_FP64 || prm->precision > FMM_PREC_MIXED_TC) {
+        fmm_set_error("unknown precision %d", prm->precision);
+        return FMM_ERR_ARG;
+    }
+    if (prm->flags & ~(FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING)) { fmm_set_error("unknown flags 0x%x", prm->flags); return FMM_ERR_ARG; }
+    if (prm->timeout_ns < 0) { fmm_set_error("timeout_ns < 0"); return FMM_ERR_ARG; }
+    return FMM_OK;
+}
+
+void setup_pool_once() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;  // keep freed blocks for reuse by this process
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fmm_last_error(void) { return g_err; }
+
+const char* fmm_version(void) { return "paper_1203_0889_gb300 0.1 (sm_103a)"; }
+
+int fmm_build_tree(const fmm_params* params, int64_t n, const void* pos, int pos_dtype, fmm_tree** out,
+                   void* stream) {
+    g_err[0] = 0;
+    if (!out) { fmm_set_error("out is NULL"); return FMM_ERR_ARG; }
+    *out = nullptr;
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (n < 0 || n >= ((int64_t)1 << 31)) { fmm_set_error("n=%lld outside [0, 2^31)", (long long)n); return FMM_ERR_ARG; }
+    if (n > 0 && !pos) { fmm_set_error("pos is NULL"); return FMM_ERR_ARG; }
+    if (pos_dtype != FMM_F64 && pos_dtype != FMM_F32) { fmm_set_error("pos_dtype must be FMM_F64 or FMM_F32"); return FMM_ERR_ARG; }
+    setup_pool_once();
+    fmm_tree* t = new (std::nothrow) fmm_tree();
+    if (!t) { fmm_set_error("host allocation failed"); return FMM_ERR_ALLOC; }
+    t->prm = *params;
+    if (t->prm.timeout_ns == 0) t->prm.timeout_ns = 2000000000LL;
+    t->n = n;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (t->prm.flags & FMM_TIMING) {
+        t->timing = true;
+        for (int i = 0; i < 2 * FMM_NUM_STAGES; i++) {
+            cudaError_t e = cudaEventCreate(&t->ev[i]);
+            if (e != cudaSuccess) {
+                fmm_set_error("cudaEventCreate: %s", cudaGetErrorString(e));
+                for (int k = 0; k < i; k++) cudaEventDestroy(t->ev[k]);
+                delete t;
+                return FMM_ERR_CUDA;
+            }
+        }
+    }
+    t->launch_ctr = &t->launches_build;
+    rc = fmm::build_tree_impl(t, pos, pos_dtype, st);
+    if (!rc) rc = fmm::alloc_eval_workspace(t, st);
+    if (!rc) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { fmm_set_error("build: %s", cudaGetErrorString(e)); rc = FMM_ERR_CUDA; }
+    }
+    if (rc) {
+        cudaStreamSynchronize(st);
+        fmm::free_tree_device(t);
+        if (t->timing) for (int i = 0; i < 2 * FMM_NUM_STAGES; i++) cudaEventDestroy(t->ev[i]);
+        delete t;
+        return rc;
+    }
+    t->launch_ctr = nullptr;
+    *out = t;
+    return FMM_OK;
+}
+
+int fmm_evaluate(fmm_tree* tree, const void* q, void* phi, void* force, int dtype, void* stream) {
+    g_err[0] = 0;
+    if (!tree) { fmm_set_error("tree is NULL"); return FMM_ERR_ARG; }
+    if (dtype != FMM_F64 && dtype != FMM_F32) { fmm_set_error("dtype must be FMM_F64 or FMM_F32"); return FMM_ERR_ARG; }
+    if (tree->n > 0 && !q) { fmm_set_error("q is NULL"); return FMM_ERR_ARG; }
+    tree->launches_eval = 0;
+    tree->launch_ctr = &tree->launches_eval;
+    for (int s = FMM_STAGE_PREPARE; s < FMM_NUM_STAGES; s++) tree->ev_used[s] = false;
+    int rc = fmm::evaluate_impl(tree, q, phi, force, dtype, (cudaStream_t)stream);
+    tree->launch_ctr = nullptr;
+    return rc;
+}
+
+int fmm_build_tree_batched(const fmm_params* params, int32_t nsys, const int64_t* offsets, const void* pos,
+                           int pos_dtype, fmm_tree** out, void* stream) {
+    (void)params; (void)nsys; (void)offsets; (void)pos; (void)pos_dtype; (void)stream;
+    if (out) *out = nullptr;
+    fmm_set_error("fmm_build_tree_batched: not available in this build");
+    return FMM_ERR_STATE;
+}
+
+int fmm_evaluate_batched(fmm_tree* tree, const void* q, void* phi, void* force, int dtype, void* stream) {
+    (void)tree; (void)q; (void)phi; (void)force; (void)dtype; (void)stream;
+    fmm_set_error("fmm_evaluate_batched: not available in this build");
+    return FMM_ERR_STATE;
+}
+
+int fmm_tree_get_info(const fmm_tree* t, fmm_tree_info* info) {
+    if (!t || !info) { fmm_set_error("NULL argument"); return FMM_ERR_ARG; }
+    memset(info, 0, sizeof(*info));
+    info->n = t->n;
+    info->ncell = t->ncell;
+    info->nlevel = t->nlevel;
+    info->nleaf = t->nleaf;
+    info->p = t->prm.p;
+    info->nm2l = t->nm2l;
+    info->np2p = t->np2p;
+    for (int k = 0; k < 3; k++) info->origin[k] = t->origin[k];
+    info->side = t->side;
+    info->device_bytes = t->device_bytes;
+    return FMM_OK;
+}
+
+int fmm_tree_export(const fmm_tree* t, uint64_t* keys, int64_t* perm, int32_t* level, uint64_t* cell_key,
+                    int64_t* first, int64_t* count, int32_t* parent, int32_t* child_first,
+                    int32_t* child_count, int32_t* m2l, int32_t* p2p) {
+    if (!t) { fmm_set_error("tree is NULL"); return FMM_ERR_ARG; }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { fmm_set_error("export: %s", cudaGetErrorString(e)); return FMM_ERR_CUDA; }
+    const size_t n = (size_t)t->n, nc = (size_t)t->ncell;
+    const fmm::TreeDev& d = t->d;
+#define CP(dst, srcp, cnt, sz)                                                                   \
+    if ((dst) && (cnt)) {                                                                        \
+        e = cudaMemcpy((dst), (srcp), (cnt) * (sz), cudaMemcpyDeviceToHost);                     \
+        if (e != cudaSuccess) { fmm_set_error("export: %s", cudaGetErrorString(e)); return FMM_ERR_CUDA; } \
+    }
+    CP(keys, d.keys, n, 8);
+    CP(level, d.level, nc, 4);
+    CP(cell_key, d.ckey, nc, 8);
+    CP(parent, d.parent, nc, 4);
+    CP(child_first, d.child_first, nc, 4);
+    CP(child_count, d.child_count, nc, 4);
+    if (perm && n) {
+        std::vector<int32_t> v(n);
+        CP(v.data(), d.perm, n, 4);
+        for (size_t i = 0; i < n; i++) perm[i] = v[i];
+    }
+    if ((first || count) && nc) {
+        std::vector<int32_t> v(nc);
+        if (first) { CP(v.data(), d.first, nc, 4); for (size_t i = 0; i < nc; i++) first[i] = v[i]; }
+        if (count) { CP(v.data(), d.count, nc, 4); for (size_t i = 0; i < nc; i++) count[i] = v[i]; }
+    }
+    // lists: expand CSR back to (target, source) pairs
+    for (int which = 0; which < 2; which++) {
+        int32_t* out = which == 0 ? m2l : p2p;
+        int64_t np = which == 0 ? t->nm2l : t->np2p;
+        if (!out || np == 0) continue;
+        std::vector<int64_t> st(nc + 1);
+        std::vector<int32_t> src((size_t)np);
+        CP(st.data(), which == 0 ? d.m2l_start : d.p2p_start, nc + 1, 8);
+        CP(src.data(), which == 0 ? d.m2l_src : d.p2p_src, (size_t)np, 4);
+        for (size_t c = 0; c < nc; c++)
+            for (int64_t k = st[c]; k < st[c + 1]; k++) { out[2 * k] = (int32_t)c; out[2 * k + 1] = src[k]; }
+    }
+#undef CP
+    return FMM_OK;
+}
+
+int fmm_status(fmm_tree* t) {
+    if (!t) { fmm_set_error("tree is NULL"); return FMM_ERR_ARG; }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { fmm_set_error("status: %s", cudaGetErrorString(e)); return FMM_ERR_CUDA; }
+    int s = 0;
+    if (t->d.status) {
+        e = cudaMemcpy(&s, t->d.status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { fmm_set_error("status: %s", cudaGetErrorString(e)); return FMM_ERR_CUDA; }
+    }
+    if (s) fmm_set_error("device status %d", s);
+    return s ? FMM_ERR_TIMEOUT : FMM_OK;
+}
+
+void fmm_tree_destroy(fmm_tree* t) {
+    if (!t) return;
+    cudaDeviceSynchronize();
+    fmm::free_tree_device(t);
+    cudaStreamSynchronize(0);
+    if (t->timing) for (int i = 0; i < 2 * FMM_NUM_STAGES; i++) cudaEventDestroy(t->ev[i]);
+    delete t;
+}
+
+static const char* k_stage_names[FMM_NUM_STAGES] = {"keys", "octree", "lists", "setup", "prepare", "p2p",
+                                                     "p2m", "m2m", "m2l", "l2l", "l2p", "queue"};
+
+const char* fmm_stage_name(int32_t i) { return (i >= 0 && i < FMM_NUM_STAGES) ? k_stage_names[i] : ""; }
+
+int fmm_stage_times(const fmm_tree* t, double* ms, int32_t max_stages) {
+    if (!t || !ms) { fmm_set_error("NULL argument"); return FMM_ERR_ARG; }
+    if (!t->timing) { fmm_set_error("tree was built without FMM_TIMING"); return FMM_ERR_STATE; }
+    for (int i = 0; i < max_stages; i++) {
+        ms[i] = -1.0;
+        if (i >= FMM_NUM_STAGES || !t->ev_used[i]) continue;
+        cudaError_t e = cudaEventSynchronize(t->ev[2 * i + 1]);
+        float f = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&f, t->ev[2 * i], t->ev[2 * i + 1]);
+        if (e != cudaSuccess) { fmm_set_error("stage %d: %s", i, cudaGetErrorString(e)); return FMM_ERR_CUDA; }
+        ms[i] = f;
+    }
+    return FMM_OK;
+}
+
+int64_t fmm_kernel_launches(const fmm_tree* t, int32_t build) {
+    if (!t) return -1;
+    return build ? t->launches_build : t->launches_eval;
+}
+
+}  // extern "C"

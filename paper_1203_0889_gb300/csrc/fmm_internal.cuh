@@ -1,0 +1,204 @@
+// fmm_internal.cuh -- types and helpers shared by the CUDA translation units.
+//
+// Coefficient storage on the device: orders m >= 0 only ("triangular"),
+// complex entry (n, m) at n(n+1)/2 + m; negative orders follow from
+// X_n^{-m} = (-1)^m conj(X_n^m), which holds for the solid harmonics and for
+// every expansion of a real charge distribution.
+//
+// Expansions are stored per-level scaled (h = side of the cell):
+//   multipole  Mt_n^m = M_n^m / h^n       = sum_j q_j R_n^m((x_j - c) / h)
+//   local      Lt_k^l = L_k^l * h^(k+1),   phi(x) = (1/h) sum Lt_k^l R_k^l((x - c) / h)
+// so that a translation between cells of sizes (h_s, h_t) depends only on the
+// offset in target-cell units and on the size ratio.  Every value then stays
+// inside FP32 range for any tree depth.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fmm.h"
+
+#define FMM_MAX_P 20
+#define FMM_MAX_LEVEL 21
+
+namespace fmm {
+
+__host__ __device__ inline int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+__host__ __device__ inline int ntri(int p) { return (p + 1) * (p + 2) / 2; }
+
+template <typename T>
+struct cplx {
+    T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cmk(T a, T b) { cplx<T> c; c.re = a; c.im = b; return c; }
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return cmk<T>(a.re + b.re, a.im + b.im); }
+template <typename T>
+__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return cmk<T>(a.re - b.re, a.im - b.im); }
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+    return cmk<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return cmk<T>(a.re * s, a.im * s); }
+template <typename T>
+__device__ __forceinline__ cplx<T> cconj(cplx<T> a) { return cmk<T>(a.re, -a.im); }
+// a += b * c
+template <typename T>
+__device__ __forceinline__ void cfma(cplx<T>& a, cplx<T> b, cplx<T> c) {
+    a.re = fma(b.re, c.re, fma(-b.im, c.im, a.re));
+    a.im = fma(b.re, c.im, fma(b.im, c.re, a.im));
+}
+// a += b * conj(c)
+template <typename T>
+__device__ __forceinline__ void cfma_cj(cplx<T>& a, cplx<T> b, cplx<T> c) {
+    a.re = fma(b.re, c.re, fma(b.im, c.im, a.re));
+    a.im = fma(b.im, c.re, fma(-b.re, c.im, a.im));
+}
+
+// Entry (n, m) of a triangular array for any order -n <= m <= n (zero outside).
+template <typename T>
+__device__ __forceinline__ cplx<T> get_sym(const cplx<T>* A, int n, int m) {
+    if (m > n || -m > n) return cmk<T>(0, 0);
+    if (m >= 0) return A[tri(n, m)];
+    cplx<T> v = A[tri(n, -m)];
+    return (m & 1) ? cmk<T>(-v.re, v.im) : cmk<T>(v.re, -v.im);
+}
+
+// Regular solid harmonics R_n^m(x, y, z), 0 <= m <= n <= p, into R (triangular).
+//   R_0^0 = 1, R_m^m = R_{m-1}^{m-1} (x + iy) / (2m), R_{m+1}^m = z R_m^m,
+//   (n+m)(n-m) R_n^m = (2n-1) z R_{n-1}^m - r^2 R_{n-2}^m.
+template <typename T>
+__device__ inline void regular_harmonics(int p, T x, T y, T z, cplx<T>* R) {
+    T r2 = x * x + y * y + z * z;
+    cplx<T> rmm = cmk<T>(1, 0);
+    for (int m = 0; m <= p; m++) {
+        if (m > 0) rmm = cscale(cmul(rmm, cmk<T>(x, y)), T(1) / T(2 * m));
+        R[tri(m, m)] = rmm;
+        if (m + 1 <= p) R[tri(m + 1, m)] = cscale(rmm, z);
+        cplx<T> a = rmm, b = cscale(rmm, z);
+        for (int n = m + 2; n <= p; n++) {
+            T inv = T(1) / T((n + m) * (n - m));
+            cplx<T> c = cmk<T>((T(2 * n - 1) * z * b.re - r2 * a.re) * inv,
+                               (T(2 * n - 1) * z * b.im - r2 * a.im) * inv);
+            R[tri(n, m)] = c;
+            a = b; b = c;
+        }
+    }
+}
+
+// Irregular solid harmonics column m: I_n^m(x, y, z) for n = m..P, into I (triangular).
+//   I_m^m = (2m-1)!! (x + iy)^m / r^{2m+1},  I_{m+1}^m = (2m+1) z I_m^m / r^2,
+//   r^2 I_n^m = (2n-1) z I_{n-1}^m - (n+m-1)(n-m-1) I_{n-2}^m.
+template <typename T>
+__device__ inline void irregular_column(int P, int m, T x, T y, T z, cplx<T>* I) {
+    T r2 = x * x + y * y + z * z;
+    T inv = T(1) / r2;
+    cplx<T> v = cmk<T>(T(1) / sqrt(r2), 0);
+    cplx<T> w = cscale(cmk<T>(x, y), inv);
+    for (int j = 1; j <= m; j++) v = cscale(cmul(v, w), T(2 * j - 1));
+    I[tri(m, m)] = v;
+    if (m + 1 > P) return;
+    cplx<T> a = v, b = cscale(v, T(2 * m + 1) * z * inv);
+    I[tri(m + 1, m)] = b;
+    for (int n = m + 2; n <= P; n++) {
+        T c1 = T(2 * n - 1) * z, c2 = T((n + m - 1) * (n - m - 1));
+        cplx<T> c = cmk<T>((c1 * b.re - c2 * a.re) * inv, (c1 * b.im - c2 * a.im) * inv);
+        I[tri(n, m)] = c;
+        a = b; b = c;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tree state
+// ---------------------------------------------------------------------------
+
+struct Geometry {        // device-resident root cube
+    double origin[3];
+    double side;
+    double inv;          // 2^21 / side
+    double centre[3];    // centre of the root cube (FP32 positions are relative to it)
+    int bad;             // non-finite input seen
+};
+
+struct TreeDev {
+    // particles (sorted order)
+    uint64_t* keys = nullptr;     // [n]
+    int32_t* perm = nullptr;      // [n] sorted slot -> input index
+    double* spos = nullptr;       // [n*3] sorted positions (FP64)
+    // cells, ordered by (level, key)
+    int32_t* level = nullptr;
+    uint64_t* ckey = nullptr;
+    int32_t* first = nullptr;
+    int32_t* count = nullptr;
+    int32_t* parent = nullptr;
+    int32_t* child_first = nullptr;
+    int32_t* child_count = nullptr;
+    double4_32a* centre = nullptr;    // (cx, cy, cz, h) in input coordinates
+    int32_t* leaves = nullptr;    // [nleaf]
+    // lists, CSR by target
+    int64_t* m2l_start = nullptr; // [ncell+1]
+    int32_t* m2l_src = nullptr;   // [nm2l]
+    int64_t* p2p_start = nullptr;
+    int32_t* p2p_src = nullptr;
+    Geometry* geom = nullptr;
+    int* status = nullptr;        // device status word(s)
+    // evaluation workspace
+    void* M = nullptr;            // [ncell * ntri(p)] cplx<T>
+    void* L = nullptr;
+    void* xq = nullptr;           // sorted (x, y, z, q): double4_32a or float4
+    double* near = nullptr;       // [n*4] sorted near-field (phi, gx, gy, gz)
+};
+
+}  // namespace fmm
+
+struct fmm_tree {
+    fmm_params prm;
+    // stage timing (FMM_TIMING) and launch counts
+    cudaEvent_t ev[2 * FMM_NUM_STAGES] = {};
+    bool ev_used[FMM_NUM_STAGES] = {};
+    bool timing = false;
+    int64_t launches_build = 0, launches_eval = 0;
+    int64_t* launch_ctr = nullptr;  // which counter launches currently go to
+    int64_t n = 0;
+    int ncell = 0, nlevel = 0, nleaf = 0;
+    int64_t nm2l = 0, np2p = 0;
+    int level_start[FMM_MAX_LEVEL + 2] = {0};  // cells of level l: [level_start[l], level_start[l+1])
+    double origin[3] = {0, 0, 0}, side = 1.0;
+    int64_t device_bytes = 0;
+    int nsys = 1;
+    fmm::TreeDev d;
+};
+
+// error reporting (capi.cu)
+void fmm_set_error(const char* fmt, ...);
+
+#define FMM_CUDA_TRY(call)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            fmm_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? FMM_ERR_ALLOC : FMM_ERR_CUDA;       \
+        }                                                                               \
+    } while (0)
+
+// internal entry points between translation units
+namespace fmm {
+// stage events: recorded only when the tree was built with FMM_TIMING
+inline void stage_begin(fmm_tree* t, int s, cudaStream_t st) {
+    if (t->timing) { cudaEventRecord(t->ev[2 * s], st); t->ev_used[s] = true; }
+}
+inline void stage_end(fmm_tree* t, int s, cudaStream_t st) {
+    if (t->timing) cudaEventRecord(t->ev[2 * s + 1], st);
+}
+inline void count_launch(fmm_tree* t, int k = 1) {
+    if (t && t->launch_ctr) *t->launch_ctr += k;
+}
+int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st);
+int evaluate_impl(fmm_tree* t, const void* q, void* phi, void* force, int dtype, cudaStream_t st);
+int alloc_eval_workspace(fmm_tree* t, cudaStream_t st);
+void free_tree_device(fmm_tree* t);
+template <typename T>
+int dev_alloc(T** p, size_t count, fmm_tree* t, cudaStream_t st);
+}  // namespace fmm

@@ -1,0 +1,608 @@
+// tree_build.cu -- root cube, Morton keys, adaptive octree and breadth-first
+// dual tree traversal on the device (paper Sections 2.1, 2.2, 4 and 5).
+//
+// All integer work (keys, cells, lists) is bit-exact with the CPU oracle: the
+// FP64 quantisation uses explicit round-to-nearest intrinsics (no FMA
+// contraction), the acceptance test compares an exact integer with one FP64
+// product, and the lists are put in canonical (target, source) order by a
+// radix sort.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <vector>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+// ---------------------------------------------------------------------------
+// allocation helpers (stream-ordered pool allocator)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+int dev_alloc(T** p, size_t count, fmm_tree* t, cudaStream_t st) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), st);
+    if (e != cudaSuccess) {
+        fmm_set_error("cudaMallocAsync(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+        return FMM_ERR_ALLOC;
+    }
+    if (t) t->device_bytes += (int64_t)(count * sizeof(T));
+    return FMM_OK;
+}
+template int dev_alloc<uint64_t>(uint64_t**, size_t, fmm_tree*, cudaStream_t);
+template int dev_alloc<int32_t>(int32_t**, size_t, fmm_tree*, cudaStream_t);
+template int dev_alloc<int64_t>(int64_t**, size_t, fmm_tree*, cudaStream_t);
+template int dev_alloc<double>(double**, size_t, fmm_tree*, cudaStream_t);
+template int dev_alloc<char>(char**, size_t, fmm_tree*, cudaStream_t);
+
+template <typename T>
+static void dev_free(T*& p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+}
+
+// grow a device array to hold `need` elements, keeping `keep` of them
+template <typename T>
+static int grow(T*& p, size_t& cap, size_t need, size_t keep, cudaStream_t st) {
+    if (need <= cap) return FMM_OK;
+    size_t nc = std::max(need, cap * 2);
+    T* q = nullptr;
+    int rc = dev_alloc(&q, nc, (fmm_tree*)nullptr, st);
+    if (rc) return rc;
+    if (keep) FMM_CUDA_TRY(cudaMemcpyAsync(q, p, keep * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    dev_free(p, st);
+    p = q;
+    cap = nc;
+    return FMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// root cube and keys
+// ---------------------------------------------------------------------------
+
+constexpr int BB_THREADS = 256;
+
+template <typename T>
+__global__ void k_bbox_partial(const T* __restrict__ pos, int64_t n, double* part, Geometry* g) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int d = 0; d < 3; d++) {
+            double v = (double)pos[3 * i + d];
+            if (!isfinite(v)) bad = 1;
+            lo[d] = fmin(lo[d], v);
+            hi[d] = fmax(hi[d], v);
+        }
+    }
+    __shared__ double s[6][BB_THREADS];
+    for (int d = 0; d < 3; d++) { s[d][threadIdx.x] = lo[d]; s[3 + d][threadIdx.x] = hi[d]; }
+    if (bad) g->bad = 1;
+    __syncthreads();
+    for (int w = BB_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int d = 0; d < 3; d++) {
+                s[d][threadIdx.x] = fmin(s[d][threadIdx.x], s[d][threadIdx.x + w]);
+                s[3 + d][threadIdx.x] = fmax(s[3 + d][threadIdx.x], s[3 + d][threadIdx.x + w]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; k++) part[blockIdx.x * 6 + k] = s[k][0];
+}
+
+// Root cube (same operation sequence as the oracle): side = longest extent
+// (1 if zero), origin = (lo + hi) * 0.5 - side * 0.5, inv = 2^21 / side.
+__global__ void k_bbox_final(const double* part, int nb, Geometry* g) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nb; b++)
+        for (int d = 0; d < 3; d++) {
+            lo[d] = fmin(lo[d], part[b * 6 + d]);
+            hi[d] = fmax(hi[d], part[b * 6 + 3 + d]);
+        }
+    double s = 0.0;
+    for (int d = 0; d < 3; d++) s = fmax(s, __dsub_rn(hi[d], lo[d]));
+    if (s == 0.0) s = 1.0;
+    for (int d = 0; d < 3; d++) {
+        g->origin[d] = __dsub_rn(__dmul_rn(__dadd_rn(lo[d], hi[d]), 0.5), __dmul_rn(s, 0.5));
+        g->centre[d] = __dadd_rn(g->origin[d], __dmul_rn(s, 0.5));
+    }
+    g->side = s;
+    g->inv = __ddiv_rn(2097152.0, s);
+}
+
+// 21 bits -> bits 0, 3, 6, ... (every third bit)
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {
+    v &= 0x1fffffull;
+    v = (v | v << 32) & 0x1f00000000ffffull;
+    v = (v | v << 16) & 0x1f0000ff0000ffull;
+    v = (v | v << 8) & 0x100f00f00f00f00full;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+    v = (v | v << 2) & 0x1249249249249249ull;
+    return v;
+}
+__device__ __forceinline__ int64_t compact3(uint64_t v) {
+    v &= 0x1249249249249249ull;
+    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+    v = (v ^ (v >> 32)) & 0x1fffffull;
+    return (int64_t)v;
+}
+
+__device__ __forceinline__ uint64_t quantise(double x, double o, double inv) {
+    double v = floor(__dmul_rn(__dsub_rn(x, o), inv));
+    if (v < 0.0) v = 0.0;
+    if (v > 2097151.0) v = 2097151.0;
+    return (uint64_t)v;
+}
+
+template <typename T>
+__global__ void k_keys(const T* __restrict__ pos, int64_t n, const Geometry* __restrict__ g,
+                       uint64_t* keys, int32_t* idx) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t kx = quantise((double)pos[3 * i], g->origin[0], g->inv);
+    uint64_t ky = quantise((double)pos[3 * i + 1], g->origin[1], g->inv);
+    uint64_t kz = quantise((double)pos[3 * i + 2], g->origin[2], g->inv);
+    keys[i] = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
+    idx[i] = (int32_t)i;
+}
+
+template <typename T>
+__global__ void k_gather_pos(const T* __restrict__ pos, const int32_t* __restrict__ perm, int64_t n,
+                             double* spos) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm[i];
+    spos[3 * i] = (double)pos[3 * j];
+    spos[3 * i + 1] = (double)pos[3 * j + 1];
+    spos[3 * i + 2] = (double)pos[3 * j + 2];
+}
+
+// ---------------------------------------------------------------------------
+// octree, one level at a time
+// ---------------------------------------------------------------------------
+
+// Children of cell c are the distinct values of key >> shift within its
+// particle range; found by one binary search per octant.
+__device__ __forceinline__ int child_bounds(const uint64_t* keys, int f, int e, uint64_t base, int shift,
+                                            int* bnd) {
+    int lo = f, nc = 0;
+    bnd[0] = f;
+    for (int o = 0; o < 8; o++) {
+        int a = lo, b = e;
+        uint64_t lim = base + (uint64_t)o;
+        while (a < b) {
+            int mid = (a + b) >> 1;
+            if ((keys[mid] >> shift) <= lim) a = mid + 1; else b = mid;
+        }
+        bnd[o + 1] = a;
+        if (a > lo) nc++;
+        lo = a;
+    }
+    return nc;
+}
+
+__global__ void k_count_children(int lb, int le, int level, int leaf_size, const int32_t* first,
+                                 const int32_t* count, const uint64_t* ckey, const uint64_t* keys,
+                                 int32_t* nchild) {
+    int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= le) return;
+    int cnt = count[c];
+    if (!(cnt > leaf_size && level < FMM_MAX_LEVEL)) { nchild[c - lb] = 0; return; }
+    int bnd[9];
+    nchild[c - lb] = child_bounds(keys, first[c], first[c] + cnt, ckey[c] << 3,
+                                  3 * (FMM_MAX_LEVEL - (level + 1)), bnd);
+}
+
+__global__ void k_emit_children(int lb, int le, int level, int leaf_size, const uint64_t* keys,
+                                const int32_t* nchild, const int32_t* coff, int next_base,
+                                int32_t* lev, uint64_t* ckey, int32_t* first, int32_t* count,
+                                int32_t* parent, int32_t* child_first, int32_t* child_count) {
+    int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= le) return;
+    int nc = nchild[c - lb];
+    if (nc == 0) { child_first[c] = 0; child_count[c] = 0; return; }
+    int bnd[9];
+    uint64_t base = ckey[c] << 3;
+    child_bounds(keys, first[c], first[c] + count[c], base, 3 * (FMM_MAX_LEVEL - (level + 1)), bnd);
+    int w = next_base + coff[c - lb];
+    child_first[c] = w;
+    child_count[c] = nc;
+    for (int o = 0; o < 8; o++) {
+        if (bnd[o + 1] == bnd[o]) continue;
+        lev[w] = level + 1;
+        ckey[w] = base + (uint64_t)o;
+        first[w] = bnd[o];
+        count[w] = bnd[o + 1] - bnd[o];
+        parent[w] = c;
+        w++;
+    }
+}
+
+__global__ void k_centres(int ncell, const int32_t* lev, const uint64_t* ckey, const Geometry* g,
+                          double4_32a* centre) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int l = lev[c];
+    int64_t s = (int64_t)1 << (FMM_MAX_LEVEL - l);
+    uint64_t k = ckey[c];
+    double u2 = __ddiv_rn(g->side, 4194304.0);  // side / 2^22: the unit of twice a centre
+    double x[3];
+    for (int d = 0; d < 3; d++) {
+        int64_t kc = compact3(k >> d);
+        int64_t twoc = 2 * kc * s + s;
+        x[d] = __dadd_rn(g->origin[d], __dmul_rn((double)twoc, u2));
+    }
+    centre[c] = make_double4_32a(x[0], x[1], x[2], __dmul_rn((double)s, __ddiv_rn(g->side, 2097152.0)));
+}
+
+// ---------------------------------------------------------------------------
+// breadth-first dual tree traversal
+// ---------------------------------------------------------------------------
+
+struct TravCounters {
+    unsigned long long nm2l, np2p, nnext;
+};
+
+// All 32 lanes call this; returns the lane's first slot of `cnt` slots.
+__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* ctr, unsigned cnt) {
+    const unsigned FULL = 0xffffffffu;
+    unsigned lane = threadIdx.x & 31;
+    unsigned v = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned t = __shfl_up_sync(FULL, v, o);
+        if (lane >= (unsigned)o) v += t;
+    }
+    unsigned total = __shfl_sync(FULL, v, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total) base = atomicAdd(ctr, (unsigned long long)total);
+    base = __shfl_sync(FULL, base, 31);
+    return base + v - cnt;
+}
+
+__global__ void k_traverse(const int2* __restrict__ front, int64_t nf, const int32_t* __restrict__ lev,
+                           const uint64_t* __restrict__ ckey, const int32_t* __restrict__ child_first,
+                           const int32_t* __restrict__ child_count, double th2, int2* m2l, int2* p2p,
+                           int2* next, TravCounters* cnt) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool valid = i < nf;
+    int action = -1, nsplit = 0, split_target = 0, ci = 0, cj = 0;
+    if (valid) {
+        int2 pr = front[i];
+        ci = pr.x; cj = pr.y;
+        int li = lev[ci], lj = lev[cj];
+        int64_t si = (int64_t)1 << (FMM_MAX_LEVEL - li), sj = (int64_t)1 << (FMM_MAX_LEVEL - lj);
+        uint64_t ki = ckey[ci], kj = ckey[cj];
+        int64_t D2 = 0;
+        for (int d = 0; d < 3; d++) {
+            int64_t a = 2 * compact3(ki >> d) * si + si;
+            int64_t b = 2 * compact3(kj >> d) * sj + sj;
+            D2 += (a - b) * (a - b);
+        }
+        int64_t S = si + sj;
+        bool accept = (double)(S * S) < __dmul_rn(th2, (double)D2);
+        bool leaf_i = child_count[ci] == 0, leaf_j = child_count[cj] == 0;
+        if (accept) action = 0;
+        else if (leaf_i && leaf_j) action = 1;
+        else {
+            action = 2;
+            split_target = leaf_j || (!leaf_i && li <= lj);
+            nsplit = split_target ? child_count[ci] : child_count[cj];
+        }
+    }
+    unsigned long long s0 = warp_reserve(&cnt->nm2l, action == 0 ? 1u : 0u);
+    unsigned long long s1 = warp_reserve(&cnt->np2p, action == 1 ? 1u : 0u);
+    unsigned long long s2 = warp_reserve(&cnt->nnext, (unsigned)nsplit);
+    if (action == 0) m2l[s0] = make_int2(ci, cj);
+    else if (action == 1) p2p[s1] = make_int2(ci, cj);
+    else if (action == 2) {
+        if (split_target) {
+            int cf = child_first[ci];
+            for (int k = 0; k < nsplit; k++) next[s2 + k] = make_int2(cf + k, cj);
+        } else {
+            int cf = child_first[cj];
+            for (int k = 0; k < nsplit; k++) next[s2 + k] = make_int2(ci, cf + k);
+        }
+    }
+}
+
+__global__ void k_pack_pairs(const int2* pr, int64_t np, uint64_t* key) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < np) key[i] = ((uint64_t)(uint32_t)pr[i].x << 32) | (uint32_t)pr[i].y;
+}
+
+__global__ void k_unpack_sources(const uint64_t* key, int64_t np, int32_t* src) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < np) src[i] = (int32_t)(key[i] & 0xffffffffull);
+}
+
+// start[c] = first list entry whose target is >= c, for c = 0..ncell
+__global__ void k_csr_start(const uint64_t* key, int64_t np, int ncell, int64_t* start) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > ncell) return;
+    uint64_t lim = (uint64_t)c << 32;
+    int64_t a = 0, b = np;
+    while (a < b) {
+        int64_t mid = (a + b) >> 1;
+        if (key[mid] < lim) a = mid + 1; else b = mid;
+    }
+    start[c] = a;
+}
+
+__global__ void k_leaf_flags(int ncell, const int32_t* child_count, char* flag, int32_t* iota) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) { flag[c] = child_count[c] == 0; iota[c] = c; }
+}
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+static int bits_for(int64_t v) {
+    int b = 1;
+    while (((int64_t)1 << b) <= v && b < 63) b++;
+    return b;
+}
+
+// sort (target, source) pairs and build the CSR arrays
+static int finish_list(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, int32_t** src,
+                       cudaStream_t st) {
+    int rc;
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    if ((rc = dev_alloc(&k0, np, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&k1, np, nullptr, st))) return rc;
+    if (np) { k_pack_pairs<<<nblk(np, 256), 256, 0, st>>>(pairs, np, k0); count_launch(t); }
+    size_t tmp_bytes = 0;
+    int end_bit = 32 + bits_for(t->ncell);
+    cub::DeviceRadixSort::SortKeys(nullptr, tmp_bytes, k0, k1, (int64_t)np, 0, end_bit, st);
+    char* tmp = nullptr;
+    if ((rc = dev_alloc(&tmp, tmp_bytes, nullptr, st))) return rc;
+    if (np) { FMM_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tmp_bytes, k0, k1, (int64_t)np, 0, end_bit, st)); count_launch(t); }
+    if ((rc = dev_alloc(src, np, t, st))) return rc;
+    if ((rc = dev_alloc(start, (size_t)t->ncell + 1, t, st))) return rc;
+    if (np) { k_unpack_sources<<<nblk(np, 256), 256, 0, st>>>(k1, np, *src); count_launch(t); }
+    k_csr_start<<<nblk(t->ncell + 1, 256), 256, 0, st>>>(k1, np, t->ncell, *start);
+    count_launch(t);
+    dev_free(tmp, st);
+    dev_free(k0, st);
+    dev_free(k1, st);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st) {
+    int rc;
+    const int64_t n = t->n;
+    TreeDev& d = t->d;
+    if ((rc = dev_alloc(&d.geom, 1, t, st))) return rc;
+    FMM_CUDA_TRY(cudaMemsetAsync(d.geom, 0, sizeof(Geometry), st));
+    if ((rc = dev_alloc(&d.status, 4, t, st))) return rc;
+    FMM_CUDA_TRY(cudaMemsetAsync(d.status, 0, 4 * sizeof(int), st));
+    if (n == 0) {
+        t->ncell = 0; t->nlevel = 0; t->nleaf = 0;
+        return FMM_OK;
+    }
+    stage_begin(t, FMM_STAGE_KEYS, st);
+    // --- a1: root cube, keys
+    int nb = (int)std::min<int64_t>(1024, (n + BB_THREADS - 1) / BB_THREADS);
+    double* part = nullptr;
+    if ((rc = dev_alloc(&part, (size_t)nb * 6, nullptr, st))) return rc;
+    if (pos_dtype == FMM_F64)
+        k_bbox_partial<double><<<nb, BB_THREADS, 0, st>>>((const double*)pos, n, part, d.geom);
+    else
+        k_bbox_partial<float><<<nb, BB_THREADS, 0, st>>>((const float*)pos, n, part, d.geom);
+    k_bbox_final<<<1, 32, 0, st>>>(part, nb, d.geom);
+    count_launch(t, 2);
+    uint64_t* keys_in = nullptr;
+    int32_t* idx_in = nullptr;
+    if ((rc = dev_alloc(&keys_in, n, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&idx_in, n, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&d.keys, n, t, st))) return rc;
+    if ((rc = dev_alloc(&d.perm, n, t, st))) return rc;
+    if (pos_dtype == FMM_F64)
+        k_keys<double><<<nblk(n, 256), 256, 0, st>>>((const double*)pos, n, d.geom, keys_in, idx_in);
+    else
+        k_keys<float><<<nblk(n, 256), 256, 0, st>>>((const float*)pos, n, d.geom, keys_in, idx_in);
+    count_launch(t);
+    // --- a2: stable sort of (key, input index)
+    size_t tmp_bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, d.keys, idx_in, d.perm, n, 0, 63, st);
+    char* tmp = nullptr;
+    if ((rc = dev_alloc(&tmp, tmp_bytes, nullptr, st))) return rc;
+    FMM_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys_in, d.keys, idx_in, d.perm, n, 0, 63, st));
+    count_launch(t);
+    dev_free(tmp, st);
+    dev_free(keys_in, st);
+    dev_free(idx_in, st);
+    dev_free(part, st);
+    if ((rc = dev_alloc(&d.spos, (size_t)n * 3, t, st))) return rc;
+    if (pos_dtype == FMM_F64)
+        k_gather_pos<double><<<nblk(n, 256), 256, 0, st>>>((const double*)pos, d.perm, n, d.spos);
+    else
+        k_gather_pos<float><<<nblk(n, 256), 256, 0, st>>>((const float*)pos, d.perm, n, d.spos);
+    count_launch(t);
+    stage_end(t, FMM_STAGE_KEYS, st);
+    Geometry hg;
+    FMM_CUDA_TRY(cudaMemcpyAsync(&hg, d.geom, sizeof(Geometry), cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hg.bad) {
+        fmm_set_error("fmm_build_tree: positions contain a non-finite value");
+        return FMM_ERR_ARG;
+    }
+    for (int k = 0; k < 3; k++) t->origin[k] = hg.origin[k];
+    t->side = hg.side;
+
+    // --- a2: octree, level by level
+    stage_begin(t, FMM_STAGE_OCTREE, st);
+    size_t cap = (size_t)std::max<int64_t>(64, 4 * n / std::max(1, t->prm.leaf_size) + 64);
+    size_t c_lev = 0, c_key = 0, c_first = 0, c_count = 0, c_par = 0, c_cf = 0, c_cc = 0;
+    int32_t *lev = nullptr, *first = nullptr, *count = nullptr, *par = nullptr, *cf = nullptr, *cc = nullptr;
+    uint64_t* ckey = nullptr;
+    auto grow_all = [&](size_t need, size_t keep) -> int {
+        int r;
+        if ((r = grow(lev, c_lev, need, keep, st))) return r;
+        if ((r = grow(ckey, c_key, need, keep, st))) return r;
+        if ((r = grow(first, c_first, need, keep, st))) return r;
+        if ((r = grow(count, c_count, need, keep, st))) return r;
+        if ((r = grow(par, c_par, need, keep, st))) return r;
+        if ((r = grow(cf, c_cf, need, keep, st))) return r;
+        if ((r = grow(cc, c_cc, need, keep, st))) return r;
+        return FMM_OK;
+    };
+    if ((rc = grow_all(cap, 0))) return rc;
+    {
+        int32_t zero = 0, n32 = (int32_t)n, m1 = -1;
+        uint64_t k0 = 0;
+        FMM_CUDA_TRY(cudaMemcpyAsync(lev, &zero, 4, cudaMemcpyHostToDevice, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(ckey, &k0, 8, cudaMemcpyHostToDevice, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(first, &zero, 4, cudaMemcpyHostToDevice, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(count, &n32, 4, cudaMemcpyHostToDevice, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(par, &m1, 4, cudaMemcpyHostToDevice, st));
+    }
+    int32_t *nch = nullptr, *coff = nullptr;
+    size_t c_nch = 0, c_coff = 0;
+    int lb = 0, le = 1, level = 0;
+    t->level_start[0] = 0;
+    while (true) {
+        int width = le - lb;
+        if ((rc = grow(nch, c_nch, width, 0, st))) return rc;
+        if ((rc = grow(coff, c_coff, width, 0, st))) return rc;
+        k_count_children<<<nblk(width, 128), 128, 0, st>>>(lb, le, level, t->prm.leaf_size, first, count,
+                                                             ckey, d.keys, nch);
+        count_launch(t);
+        size_t sb = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, sb, nch, coff, width, st);
+        if ((rc = dev_alloc(&tmp, sb, nullptr, st))) return rc;
+        FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, nch, coff, width, st));
+        count_launch(t);
+        dev_free(tmp, st);
+        int32_t last_off = 0, last_n = 0;
+        FMM_CUDA_TRY(cudaMemcpyAsync(&last_off, coff + width - 1, 4, cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(&last_n, nch + width - 1, 4, cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+        int total = last_off + last_n;
+        if ((size_t)le + total > c_lev) {
+            if ((rc = grow_all((size_t)le + total, (size_t)le))) return rc;
+        }
+        k_emit_children<<<nblk(width, 128), 128, 0, st>>>(lb, le, level, t->prm.leaf_size, d.keys, nch, coff, le,
+                                                            lev, ckey, first, count, par, cf, cc);
+        count_launch(t);
+        t->level_start[level + 1] = le;
+        if (total == 0) break;
+        lb = le;
+        le += total;
+        level++;
+    }
+    dev_free(nch, st);
+    dev_free(coff, st);
+    stage_end(t, FMM_STAGE_OCTREE, st);
+    stage_begin(t, FMM_STAGE_SETUP, st);
+    t->ncell = le;
+    t->nlevel = level + 1;
+    for (int l = t->nlevel + 1; l <= FMM_MAX_LEVEL + 1; l++) t->level_start[l] = le;
+    // move the cell table into exactly sized, tree-owned arrays
+    const size_t nc = (size_t)t->ncell;
+    if ((rc = dev_alloc(&d.level, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.ckey, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.first, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.count, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.parent, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.child_first, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.child_count, nc, t, st))) return rc;
+    FMM_CUDA_TRY(cudaMemcpyAsync(d.level, lev, nc * 4, cudaMemcpyDeviceToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(d.ckey, ckey, nc * 8, cudaMemcpyDeviceToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(d.first, first, nc * 4, cudaMemcpyDeviceToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(d.count, count, nc * 4, cudaMemcpyDeviceToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(d.parent, par, nc * 4, cudaMemcpyDeviceToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(d.child_first, cf, nc * 4, cudaMemcpyDeviceToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(d.child_count, cc, nc * 4, cudaMemcpyDeviceToDevice, st));
+    dev_free(lev, st); dev_free(ckey, st); dev_free(first, st); dev_free(count, st);
+    dev_free(par, st); dev_free(cf, st); dev_free(cc, st);
+    if ((rc = dev_alloc(&d.centre, nc, t, st))) return rc;
+    k_centres<<<nblk(nc, 128), 128, 0, st>>>((int)nc, d.level, d.ckey, d.geom, d.centre);
+    count_launch(t);
+    // leaves
+    {
+        char* flag = nullptr;
+        int32_t *nsel = nullptr, *it = nullptr;
+        if ((rc = dev_alloc(&flag, nc, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&it, nc, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&nsel, 1, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&d.leaves, nc, t, st))) return rc;
+        k_leaf_flags<<<nblk(nc, 256), 256, 0, st>>>((int)nc, d.child_count, flag, it);
+        count_launch(t);
+        size_t sb = 0;
+        cub::DeviceSelect::Flagged(nullptr, sb, it, flag, d.leaves, nsel, (int)nc, st);
+        if ((rc = dev_alloc(&tmp, sb, nullptr, st))) return rc;
+        FMM_CUDA_TRY(cub::DeviceSelect::Flagged(tmp, sb, it, flag, d.leaves, nsel, (int)nc, st));
+        count_launch(t);
+        int32_t h = 0;
+        FMM_CUDA_TRY(cudaMemcpyAsync(&h, nsel, 4, cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+        t->nleaf = h;
+        dev_free(tmp, st); dev_free(flag, st); dev_free(nsel, st); dev_free(it, st);
+    }
+
+    stage_end(t, FMM_STAGE_SETUP, st);
+    // --- a3: breadth-first dual traversal from (root, root)
+    stage_begin(t, FMM_STAGE_LISTS, st);
+    size_t c_front = 1024, c_next = 1024, c_m = 1024, c_p = 1024;
+    int2 *front = nullptr, *next = nullptr, *m2l = nullptr, *p2p = nullptr;
+    if ((rc = grow(front, c_front = 0, 1024, 0, st))) return rc;
+    if ((rc = grow(next, c_next = 0, 1024, 0, st))) return rc;
+    if ((rc = grow(m2l, c_m = 0, 1024, 0, st))) return rc;
+    if ((rc = grow(p2p, c_p = 0, 1024, 0, st))) return rc;
+    TravCounters* ctr = nullptr;
+    if ((rc = dev_alloc(&ctr, 1, nullptr, st))) return rc;
+    FMM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(TravCounters), st));
+    {
+        int2 root = make_int2(0, 0);
+        FMM_CUDA_TRY(cudaMemcpyAsync(front, &root, sizeof(int2), cudaMemcpyHostToDevice, st));
+    }
+    int64_t nf = 1, nm = 0, npp = 0;
+    const double th2 = t->prm.theta * t->prm.theta;
+    while (nf > 0) {
+        if ((rc = grow(next, c_next, (size_t)nf * 8, 0, st))) return rc;
+        if ((rc = grow(m2l, c_m, (size_t)(nm + nf), (size_t)nm, st))) return rc;
+        if ((rc = grow(p2p, c_p, (size_t)(npp + nf), (size_t)npp, st))) return rc;
+        FMM_CUDA_TRY(cudaMemsetAsync(&ctr->nnext, 0, 8, st));
+        k_traverse<<<nblk(nf, 256), 256, 0, st>>>(front, nf, d.level, d.ckey, d.child_first, d.child_count, th2,
+                                                    m2l, p2p, next, ctr);
+        count_launch(t);
+        TravCounters h;
+        FMM_CUDA_TRY(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+        nm = (int64_t)h.nm2l;
+        npp = (int64_t)h.np2p;
+        nf = (int64_t)h.nnext;
+        std::swap(front, next);
+        std::swap(c_front, c_next);
+    }
+    dev_free(front, st); dev_free(next, st); dev_free(ctr, st);
+    t->nm2l = nm;
+    t->np2p = npp;
+    if ((rc = finish_list(t, m2l, nm, &d.m2l_start, &d.m2l_src, st))) return rc;
+    if ((rc = finish_list(t, p2p, npp, &d.p2p_start, &d.p2p_src, st))) return rc;
+    dev_free(m2l, st); dev_free(p2p, st);
+    stage_end(t, FMM_STAGE_LISTS, st);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+void free_tree_device(fmm_tree* t) {
+    TreeDev& d = t->d;
+    cudaStream_t st = 0;
+    dev_free(d.keys, st); dev_free(d.perm, st); dev_free(d.spos, st);
+    dev_free(d.level, st); dev_free(d.ckey, st); dev_free(d.first, st); dev_free(d.count, st);
+    dev_free(d.parent, st); dev_free(d.child_first, st); dev_free(d.child_count, st);
+    dev_free(d.centre, st); dev_free(d.leaves, st);
+    dev_free(d.m2l_start, st); dev_free(d.m2l_src, st); dev_free(d.p2p_start, st); dev_free(d.p2p_src, st);
+    dev_free(d.geom, st); dev_free(d.status, st);
+    dev_free(d.M, st); dev_free(d.L, st); dev_free(d.xq, st); dev_free(d.near, st);
+}
+
+}  // namespace fmm

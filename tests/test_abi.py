@@ -1,0 +1,73 @@
+"""The C-ABI library builds for sm_103a, loads, and exports what include/fmm.h declares.
+
+No compute call is made here (no GPU): only argument checks that the library
+rejects before touching the device.
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^\s*(?:int64_t|int|void|const char\s*\*)\s*(fmm_\w+)\s*\(", txt, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1203_0889_gb300 import _build
+    import paper_1203_0889_gb300 as fmm
+    _build.build()
+    return fmm.load()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ("fmm_build_tree", "fmm_evaluate", "fmm_tree_export", "fmm_tree_destroy", "fmm_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_argument_errors(lib):
+    import paper_1203_0889_gb300 as fmm
+    assert b"sm_103a" in lib.fmm_version()
+    out = C.c_void_p()
+    # NULL params
+    assert lib.fmm_build_tree(None, 10, None, 0, C.byref(out), None) == fmm.FMM_ERR_ARG
+    assert b"params" in lib.fmm_last_error()
+    bad = [fmm.Params(-1, 64, 0.5, 0, 0, 0), fmm.Params(4, 0, 0.5, 0, 0, 0), fmm.Params(4, 64, 1.5, 0, 0, 0),
+           fmm.Params(4, 64, 0.5, 9, 0, 0), fmm.Params(4, 64, 0.5, 0, 64, 0), fmm.Params(21, 64, 0.5, 0, 0, 0),
+           fmm.Params(4, 64, 0.0, 0, 0, 0), fmm.Params(4, 64, 0.5, 0, 0, -1)]
+    for prm in bad:
+        assert lib.fmm_build_tree(C.byref(prm), 10, C.c_void_p(8), 0, C.byref(out), None) == fmm.FMM_ERR_ARG
+        assert out.value is None
+    good = fmm.Params(4, 64, 0.5, 0, 0, 0)
+    assert lib.fmm_build_tree(C.byref(good), -5, C.c_void_p(8), 0, C.byref(out), None) == fmm.FMM_ERR_ARG
+    assert lib.fmm_build_tree(C.byref(good), 1 << 31, C.c_void_p(8), 0, C.byref(out), None) == fmm.FMM_ERR_ARG
+    assert lib.fmm_build_tree(C.byref(good), 10, None, 0, C.byref(out), None) == fmm.FMM_ERR_ARG
+    assert lib.fmm_build_tree(C.byref(good), 10, C.c_void_p(8), 7, C.byref(out), None) == fmm.FMM_ERR_ARG
+    assert lib.fmm_build_tree(C.byref(good), 10, C.c_void_p(8), 0, None, None) == fmm.FMM_ERR_ARG
+    assert lib.fmm_evaluate(None, None, None, None, 0, None) == fmm.FMM_ERR_ARG
+    assert lib.fmm_tree_get_info(None, None) == fmm.FMM_ERR_ARG
+    assert lib.fmm_status(None) == fmm.FMM_ERR_ARG
+    lib.fmm_tree_destroy(None)
+
+
+def test_binding_refuses_without_library(monkeypatch, tmp_path):
+    import paper_1203_0889_gb300 as fmm
+    monkeypatch.setattr(fmm, "_lib", None)
+    monkeypatch.setattr(fmm, "_LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        fmm.load()

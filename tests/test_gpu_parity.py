@@ -1,0 +1,101 @@
+"""CUDA FMM values against the oracle's FMM at equal p, theta, leaf size.
+
+Bars: the FP64 path within relative L2 1e-10 of the oracle (potentials and
+forces); paths with FP32 stages within 1e-4 (the stated error bar of the
+reduced-precision forms), with the measured error well below it asserted too.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.gpu_common import gpu_eval, gpu_tree, oracle_phi_force, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+@pytest.mark.parametrize("name,n,p,leaf,theta", [
+    ("uniform", 16384, 4, 64, 0.5),
+    ("plummer", 20000, 8, 64, 0.4),
+    ("clustered", 20000, 10, 64, 0.5),
+    ("uniform", 5000, 0, 16, 0.5),
+    ("plummer", 7000, 1, 8, 0.6),
+    ("clustered", 9000, 13, 32, 0.4),
+    ("uniform", 3000, 20, 16, 0.3),
+])
+def test_fp64_matches_oracle(name, n, p, leaf, theta):
+    import paper_1203_0889_gb300 as fmm
+    wl = W.make_workload(name, n=n)
+    ref_phi, ref_f, _ = oracle_phi_force(wl.pos, wl.q, p, leaf, theta)
+    t = gpu_tree(wl.pos, p=p, leaf_size=leaf, theta=theta, precision=fmm.PREC_FP64)
+    phi, f = gpu_eval(t, wl.q)
+    assert O.rel_l2(phi, ref_phi) <= FP64_TOL
+    assert O.rel_l2(f, ref_f) <= FP64_TOL
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("name,n,p,leaf,theta", [
+    ("uniform", 16384, 4, 64, 0.5),
+    ("plummer", 30000, 8, 64, 0.4),
+    ("clustered", 30000, 10, 64, 0.5),
+])
+def test_reduced_precision_within_bar(prec, name, n, p, leaf, theta):
+    wl = W.make_workload(name, n=n)
+    ref_phi, ref_f, _ = oracle_phi_force(wl.pos, wl.q, p, leaf, theta)
+    t = gpu_tree(wl.pos, p=p, leaf_size=leaf, theta=theta, precision=prec)
+    for dt in ("f64", "f32"):
+        torch, _ = torch_dev()
+        phi, f = gpu_eval(t, wl.q, dtype=torch.float64 if dt == "f64" else torch.float32)
+        assert O.rel_l2(phi, ref_phi) <= 1e-4
+        assert O.rel_l2(f, ref_f) <= 1e-4
+
+
+def test_no_far_field_equals_direct():
+    wl = W.make_workload("plummer", n=4000)
+    ref_phi, ref_grad = O.direct(wl.pos, wl.q)
+    t = gpu_tree(wl.pos, p=3, leaf_size=16, theta=1e-6)
+    assert t.info().nm2l == 0
+    phi, f = gpu_eval(t, wl.q)
+    assert O.rel_l2(phi, ref_phi) <= 1e-13
+    assert O.rel_l2(f, -wl.q[:, None] * ref_grad) <= 1e-13
+
+
+def test_field_flag_and_optional_outputs():
+    import paper_1203_0889_gb300 as fmm
+    torch, dev = torch_dev()
+    wl = W.make_workload("uniform", n=6000)
+    t1 = gpu_tree(wl.pos, p=5, leaf_size=32, theta=0.5)
+    t2 = gpu_tree(wl.pos, p=5, leaf_size=32, theta=0.5, flags=fmm.OUT_FIELD)
+    q = torch.tensor(wl.q, dtype=torch.float64, device=dev)
+    _, f = t1.evaluate(q)
+    _, e = t2.evaluate(q)
+    assert torch.allclose(f, q[:, None] * e, rtol=1e-14, atol=0)
+    phi, none = t1.evaluate(q, want_force=False)
+    assert none is None
+    phi2, _ = t1.evaluate(q)
+    assert torch.equal(phi, phi2)
+
+
+def test_repeat_evaluations_identical_and_charge_linearity():
+    torch, dev = torch_dev()
+    wl = W.make_workload("clustered", n=8000)
+    t = gpu_tree(wl.pos, p=6, leaf_size=32, theta=0.5)
+    q = torch.tensor(wl.q, dtype=torch.float64, device=dev)
+    a = t.evaluate(q)
+    b = t.evaluate(q)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    c = t.evaluate(2.0 * q)
+    assert torch.allclose(c[0], 2.0 * a[0], rtol=1e-14, atol=0)
+
+
+def test_duplicates_and_single_particle():
+    rng = np.random.default_rng(5)
+    pos = rng.random((3000, 3)); pos[100:400] = pos[7]
+    q = rng.uniform(-1, 1, 3000)
+    ref_phi, ref_f, _ = oracle_phi_force(pos, q, 6, 16, 0.5)
+    phi, f = gpu_eval(gpu_tree(pos, p=6, leaf_size=16, theta=0.5), q)
+    assert O.rel_l2(phi, ref_phi) <= FP64_TOL and O.rel_l2(f, ref_f) <= FP64_TOL
+    phi, f = gpu_eval(gpu_tree(np.array([[0.3, 0.3, 0.3]]), p=4), np.array([1.0]))
+    assert phi[0] == 0.0 and np.all(f == 0.0)
