@@ -184,6 +184,31 @@ int fmm_status(fmm_tree* tree);
 /* Free the tree and its device memory (synchronises the device). NULL is a no-op. */
 void fmm_tree_destroy(fmm_tree* tree);
 
+/*
+ * Allocation-free direct evaluation (no counterpart in the paper: it is an
+ * interface for callers that cannot allocate device memory, e.g. a plug-in of
+ * a framework that owns all device memory, or a real-time loop that must not
+ * wait on the allocator or risk running out of memory after start-up).
+ * Computes the same potentials and forces as fmm_evaluate with every pair
+ * handled by P2P (the exact direct sum), for n <= fmm_direct_noalloc_max_n()
+ * = 16384 particles; larger n is rejected with FMM_ERR_ARG.
+ *   pos    device, n x 3 of dtype;  q  device, n of dtype.
+ *   phi    device, n of dtype, may be NULL;  force  device, n x 3, may be NULL.
+ *   flags  0 or FMM_OUT_FIELD.
+ * Scratch: a static 1 MiB device array inside the library, held by every GPU
+ * that loads it until the process exits; no cudaMalloc/cudaFree is called.
+ * The first call on a device looks up the array's device address (once per
+ * device) -- make that first call before any stream capture.  Every call
+ * shares the one array (the accumulators are cleared at the start of each
+ * call), so calls that overlap on the GPU -- on different streams, or from
+ * different threads -- race and must be serialised by the caller.
+ */
+int fmm_direct_noalloc(int64_t n, const void* pos, const void* q, void* phi, void* force, int dtype,
+                       int32_t flags, void* stream);
+
+/* Largest n accepted by fmm_direct_noalloc. */
+int64_t fmm_direct_noalloc_max_n(void);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* fmm_last_error(void);
 

@@ -90,6 +90,10 @@ def load():
             lib.fmm_stage_name.restype = C.c_char_p
             lib.fmm_kernel_launches.argtypes = [_P, C.c_int32]
             lib.fmm_kernel_launches.restype = C.c_int64
+            lib.fmm_direct_noalloc.argtypes = [C.c_int64, _P, _P, _P, _P, C.c_int, C.c_int32, _P]
+            lib.fmm_direct_noalloc.restype = C.c_int
+            lib.fmm_direct_noalloc_max_n.argtypes = []
+            lib.fmm_direct_noalloc_max_n.restype = C.c_int64
             for name in ("fmm_build_tree", "fmm_evaluate", "fmm_build_tree_batched", "fmm_evaluate_batched",
                          "fmm_tree_get_info", "fmm_tree_export", "fmm_status"):
                 getattr(lib, name).restype = C.c_int
