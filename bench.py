@@ -135,7 +135,7 @@ def p2p_pairs(ex) -> int:
     return int((cnt[pl[:, 0]] * cnt[pl[:, 1]]).sum() - len(ex["keys"]))
 
 
-def roofline(stage_ms: dict, ex, prec: int, sm_clock_mhz: float, n_sm: int):
+def roofline(stage_ms: dict, ex, prec: int, sm_clock_mhz: float, n_sm: int, info=None):
     """Roofline object for the stage that dominates the evaluation."""
     pk, how = peaks()
     K = (P + 1) ** 2
@@ -146,6 +146,18 @@ def roofline(stage_ms: dict, ex, prec: int, sm_clock_mhz: float, n_sm: int):
     dom = max(cand, key=cand.get)
     t = cand[dom] * 1e-3
     nm2l = len(ex["m2l"])
+    if dom == "m2l" and prec == 3 and info is not None and info.tc_pairs > 0 and "m2l_tc" in stage_ms:
+        t_tc = stage_ms["m2l_tc"] * 1e-3
+        kp = ((P + 1) * (P + 2) + 15) // 16 * 16
+        useful = info.tc_pairs * 2.0 * K * K
+        issued = info.tc_items * 128 * 2.0 * kp * kp * 3
+        peak = pk["bf16_tflops"]
+        return {"kernel": "k_m2l_tc", "bound": "tensor", "achieved": useful / t_tc / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "frac": useful / t_tc / 1e12 / peak, "traffic": None,
+                "algorithmic": f"{info.tc_pairs} tensor-core M2L pairs x 2K^2 flops, K=(p+1)^2={K}",
+                "issued_frac": issued / t_tc / 1e12 / peak,
+                "peak_source": f"bf16 dense, {how} (MEASURED_PEAKS.json burst)",
+                "m2l_stage_ms": stage_ms["m2l"], "m2l_tc_ms": stage_ms["m2l_tc"]}
     if dom == "m2l":
         flops = nm2l * 2.0 * K * K
         peak = fp64_peak if prec in (0, 1) else fp32_peak
@@ -246,7 +258,7 @@ def run_ours(args):
     value = n * world * args.steps / total_s
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
     props = torch.cuda.get_device_properties(dev)
-    roof = roofline(stage_ms, ex, args.precision, clocks.get("sm_mhz"), props.multi_processor_count)
+    roof = roofline(stage_ms, ex, args.precision, clocks.get("sm_mhz"), props.multi_processor_count, info)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -295,7 +307,8 @@ def run_ours(args):
                        "step": "fmm_build_tree + fmm_evaluate (potentials and forces)",
                        "precision": PREC_NAMES[args.precision], "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"replicas x{world}", "ncell": info.ncell, "nleaf": info.nleaf,
-                       "nm2l": info.nm2l, "np2p": info.np2p,
+                       "nm2l": info.nm2l, "np2p": info.np2p, "tc_pairs": info.tc_pairs,
+                       "tc_classes": info.tc_classes,
                        "rel_l2_vs_fp64_gpu": {"phi": err_phi, "force": err_f},
                        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
                        "evaluate_ms": round(sum(v for k, v in stage_ms.items()

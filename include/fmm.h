@@ -70,7 +70,8 @@ extern "C" {
 #define FMM_STAGE_L2L       9
 #define FMM_STAGE_L2P      10   /* L2P + near field + output in input order */
 #define FMM_STAGE_QUEUE    11   /* persistent task-queue kernel (all evaluation stages) */
-#define FMM_NUM_STAGES     12
+#define FMM_STAGE_M2L_TC   12   /* tensor-core part of M2L (inside FMM_STAGE_M2L) */
+#define FMM_NUM_STAGES     13
 
 typedef struct fmm_tree fmm_tree;   /* opaque, library-owned */
 
@@ -98,6 +99,9 @@ typedef struct {
     double  origin[3];   /* corner of the root cube */
     double  side;        /* side of the root cube */
     int64_t device_bytes;/* device memory held by the tree */
+    int64_t tc_pairs;    /* M2L pairs handled by the tensor cores (FMM_PREC_MIXED_TC) */
+    int64_t tc_classes;  /* translation classes (one operator each) */
+    int64_t tc_items;    /* 128-pair work items */
 } fmm_tree_info;
 
 /*

@@ -31,7 +31,8 @@ FMM_OK, FMM_ERR_ARG, FMM_ERR_ALLOC, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, FMM_ERR_STATE
 F64, F32 = 0, 1
 PREC_FP64, PREC_FP32_P2P, PREC_FP32, PREC_MIXED_TC = 0, 1, 2, 3
 OUT_FIELD, STAGED, TIMING = 1, 2, 4
-STAGE_NAMES = ("keys", "octree", "lists", "setup", "prepare", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p", "queue")
+STAGE_NAMES = ("keys", "octree", "lists", "setup", "prepare", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p", "queue",
+               "m2l_tc")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")
@@ -53,7 +54,8 @@ class Params(C.Structure):
 class TreeInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("ncell", C.c_int32), ("nlevel", C.c_int32), ("nleaf", C.c_int32),
                 ("p", C.c_int32), ("nm2l", C.c_int64), ("np2p", C.c_int64), ("origin", C.c_double * 3),
-                ("side", C.c_double), ("device_bytes", C.c_int64)]
+                ("side", C.c_double), ("device_bytes", C.c_int64), ("tc_pairs", C.c_int64),
+                ("tc_classes", C.c_int64), ("tc_items", C.c_int64)]
 
 
 def library_path() -> str:

@@ -87,6 +87,10 @@ int fmm_build_tree(const fmm_params* params, int64_t n, const void* pos, int pos
         }
     }
     t->launch_ctr = &t->launches_build;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
     rc = fmm::build_tree_impl(t, pos, pos_dtype, st);
     if (!rc) rc = fmm::alloc_eval_workspace(t, st);
     if (!rc) {
@@ -145,6 +149,9 @@ int fmm_tree_get_info(const fmm_tree* t, fmm_tree_info* info) {
     for (int k = 0; k < 3; k++) info->origin[k] = t->origin[k];
     info->side = t->side;
     info->device_bytes = t->device_bytes;
+    info->tc_pairs = t->tc_npairs;
+    info->tc_classes = t->tc_nclass;
+    info->tc_items = t->tc_nitems;
     return FMM_OK;
 }
 
@@ -216,7 +223,7 @@ void fmm_tree_destroy(fmm_tree* t) {
 }
 
 static const char* k_stage_names[FMM_NUM_STAGES] = {"keys", "octree", "lists", "setup", "prepare", "p2p",
-                                                     "p2m", "m2m", "m2l", "l2l", "l2p", "queue"};
+                                                     "p2m", "m2m", "m2l", "l2l", "l2p", "queue", "m2l_tc"};
 
 const char* fmm_stage_name(int32_t i) { return (i >= 0 && i < FMM_NUM_STAGES) ? k_stage_names[i] : ""; }
 

@@ -34,17 +34,18 @@ __global__ void k_prepare64(const double* __restrict__ spos, const int32_t* __re
     xq[i] = make_double4_32a(spos[3 * i], spos[3 * i + 1], spos[3 * i + 2], (double)q[perm[i]]);
 }
 
-// FP32 copy, relative to the root-cube centre
+// FP32 copy relative to the centre of the particle's own leaf, so that the
+// rounding of a coordinate scales with the leaf size, not with the position.
 template <typename Q>
 __global__ void k_prepare32(const double* __restrict__ spos, const int32_t* __restrict__ perm,
-                            const Q* __restrict__ q, int64_t n, const Geometry* __restrict__ g,
-                            double4_32a* xq64, float4* xq32) {
+                            const Q* __restrict__ q, int64_t n, const int32_t* __restrict__ pleaf,
+                            const double4_32a* __restrict__ centre, double4_32a* xq64, float4* xq32) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double x = spos[3 * i], y = spos[3 * i + 1], z = spos[3 * i + 2], qq = (double)q[perm[i]];
     xq64[i] = make_double4_32a(x, y, z, qq);
-    xq32[i] = make_float4((float)(x - g->centre[0]), (float)(y - g->centre[1]), (float)(z - g->centre[2]),
-                          (float)qq);
+    double4_32a c = centre[pleaf[i]];
+    xq32[i] = make_float4((float)(x - c.x), (float)(y - c.y), (float)(z - c.z), (float)qq);
 }
 
 // R_k^l(d/h_P) for the eight child octants, d/h_P = (+-1/4, +-1/4, +-1/4);
@@ -72,7 +73,7 @@ __global__ void k_p2m(int p, int nleaf, const int32_t* __restrict__ leaves, cons
                       const int32_t* __restrict__ count, const double4_32a* __restrict__ centre,
                       const double4_32a* __restrict__ xq, cplx<T>* __restrict__ M) {
     extern __shared__ unsigned char smem_raw[];
-    const int K = ntri(p);
+    const int K = ntri(p), KS = kstride(p);
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     cplx<T>* acc = reinterpret_cast<cplx<T>*>(smem_raw) + warp * K;
     int li = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -112,7 +113,7 @@ __global__ void k_p2m(int p, int nleaf, const int32_t* __restrict__ leaves, cons
         }
     }
     __syncwarp();
-    for (int j = lane; j < K; j += 32) M[(int64_t)c * K + j] = acc[j];
+    for (int j = lane; j < K; j += 32) M[(int64_t)c * KS + j] = acc[j];
 }
 
 // ---------------------------------------------------------------------------
@@ -124,7 +125,7 @@ __global__ void k_m2m(int p, int lb, int le, const int32_t* __restrict__ child_f
                       const int32_t* __restrict__ child_count, const uint64_t* __restrict__ ckey,
                       const cplx<T>* __restrict__ Roct, cplx<T>* __restrict__ M) {
     extern __shared__ unsigned char smem_raw[];
-    const int K = ntri(p);
+    const int K = ntri(p), KS = kstride(p);
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     cplx<T>* Mc = reinterpret_cast<cplx<T>*>(smem_raw) + warp * 2 * K;
     cplx<T>* acc = Mc + K;
@@ -137,7 +138,7 @@ __global__ void k_m2m(int p, int lb, int le, const int32_t* __restrict__ child_f
     for (int ch = 0; ch < nc; ch++) {
         int cidx = cf + ch;
         __syncwarp();
-        for (int j = lane; j < K; j += 32) Mc[j] = M[(int64_t)cidx * K + j];
+        for (int j = lane; j < K; j += 32) Mc[j] = M[(int64_t)cidx * KS + j];
         __syncwarp();
         const cplx<T>* R = Roct + (int)(ckey[cidx] & 7) * K;
         for (int j = lane; j < K; j += 32) {
@@ -161,7 +162,7 @@ __global__ void k_m2m(int p, int lb, int le, const int32_t* __restrict__ child_f
         }
     }
     __syncwarp();
-    for (int j = lane; j < K; j += 32) M[(int64_t)c * K + j] = acc[j];
+    for (int j = lane; j < K; j += 32) M[(int64_t)c * KS + j] = acc[j];
 }
 
 // ---------------------------------------------------------------------------
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(128) k_m2l_generic(int p, int t0, int t1, cons
                                                      const double4_32a* __restrict__ centre,
                                                      const cplx<T>* __restrict__ M, cplx<T>* __restrict__ L) {
     extern __shared__ unsigned char smem_raw[];
-    const int K = ntri(p), KI = ntri(2 * p);
+    const int K = ntri(p), KI = ntri(2 * p), KS = kstride(p);
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     cplx<T>* base = reinterpret_cast<cplx<T>*>(smem_raw) + warp * 2 * (K + KI);
     cplx<T>* Ms = base + half * (K + KI);
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(128) k_m2l_generic(int p, int t0, int t1, cons
                 while (tri(n + 1, 0) <= j) n++;
                 T sc = T(1);
                 for (int i = 0; i < n; i++) sc *= rho;
-                Ms[j] = cscale(M[(int64_t)s * K + j], sc);
+                Ms[j] = cscale(M[(int64_t)s * KS + j], sc);
             }
             T dx = (T)((ct.x - cs.x) * invht), dy = (T)((ct.y - cs.y) * invht), dz = (T)((ct.z - cs.z) * invht);
             for (int m = hl; m <= 2 * p; m += 16) irregular_column<T>(2 * p, m, dx, dy, dz, Is);
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(128) k_m2l_generic(int p, int t0, int t1, cons
             int j = hl + 16 * r;
             if (j < K) {
                 T sg = (kk[r] & 1) ? T(-1) : T(1);
-                L[(int64_t)t * K + j] = cscale(acc[r], sg);
+                L[(int64_t)t * KS + j] = cscale(acc[r], sg);
             }
         }
     }
@@ -273,13 +274,13 @@ template <typename T>
 __global__ void k_l2l(int p, int lb, int le, const int32_t* __restrict__ parent, const uint64_t* __restrict__ ckey,
                       const cplx<T>* __restrict__ Roct, cplx<T>* __restrict__ L) {
     extern __shared__ unsigned char smem_raw[];
-    const int K = ntri(p);
+    const int K = ntri(p), KS = kstride(p);
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     cplx<T>* Lp = reinterpret_cast<cplx<T>*>(smem_raw) + warp * K;
     int c = lb + blockIdx.x * (blockDim.x >> 5) + warp;
     if (c >= le) return;
     int pc = parent[c];
-    for (int j = lane; j < K; j += 32) Lp[j] = L[(int64_t)pc * K + j];
+    for (int j = lane; j < K; j += 32) Lp[j] = L[(int64_t)pc * KS + j];
     __syncwarp();
     const cplx<T>* R = Roct + (int)(ckey[c] & 7) * K;
     for (int j = lane; j < K; j += 32) {
@@ -295,8 +296,8 @@ __global__ void k_l2l(int p, int lb, int le, const int32_t* __restrict__ parent,
             }
         T sc = T(1);
         for (int i = 0; i <= k; i++) sc *= T(0.5);
-        cplx<T> o = L[(int64_t)c * K + j];
-        L[(int64_t)c * K + j] = cadd(o, cscale(s, sc));
+        cplx<T> o = L[(int64_t)c * KS + j];
+        L[(int64_t)c * KS + j] = cadd(o, cscale(s, sc));
     }
 }
 
@@ -308,6 +309,16 @@ __global__ void k_l2l(int p, int lb, int le, const int32_t* __restrict__ parent,
 template <typename T> struct Vec4;
 template <> struct Vec4<double> { typedef double4_32a type; };
 template <> struct Vec4<float> { typedef float4 type; };
+
+// FP64 records hold absolute positions; FP32 records hold positions relative
+// to their own leaf centre, so a source is shifted by (c_s - c_t) when staged.
+// The offset c_s - c_t comes from the exact integer centres times side/2^22 in
+// FP32: no FP64 instruction per source (the FP64 pipe is narrow on this GPU).
+template <typename T> struct Offset3 { T x, y, z; };
+__device__ __forceinline__ double4_32a shift_src(double4_32a v, Offset3<double>) { return v; }
+__device__ __forceinline__ float4 shift_src(float4 v, Offset3<float> o) {
+    return make_float4(v.x + o.x, v.y + o.y, v.z + o.z, v.w);
+}
 
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
@@ -322,6 +333,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nleaf, const int32_t* _
                                                      const int64_t* __restrict__ start,
                                                      const int32_t* __restrict__ src,
                                                      const typename Vec4<T>::type* __restrict__ xq,
+                                                     const int4* __restrict__ icentre, float u2f,
                                                      double* __restrict__ near) {
     typedef typename Vec4<T>::type V;
     __shared__ V buf[P2P_BUF];
@@ -331,6 +343,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nleaf, const int32_t* _
     int c = leaves[li];
     int tf = first[c], nt = count[c];
     int64_t s0 = start[c], s1 = start[c + 1];
+    const int4 ict = icentre[c];
     for (int tb = 0; tb < nt; tb += P2P_THREADS) {
         int ntc = min(P2P_THREADS, nt - tb);
         int G = P2P_THREADS / ntc;
@@ -355,9 +368,15 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nleaf, const int32_t* _
         for (int64_t e = s0; e < s1; e++) {
             int sc = src[e];
             int rf = first[sc], rc = count[sc], off = 0;
+            const int4 ics = icentre[sc];
+            Offset3<T> o;
+            o.x = (T)((float)(ics.x - ict.x) * u2f);
+            o.y = (T)((float)(ics.y - ict.y) * u2f);
+            o.z = (T)((float)(ics.z - ict.z) * u2f);
             while (off < rc) {
                 int take = min(rc - off, P2P_BUF - fill);
-                for (int k = threadIdx.x; k < take; k += P2P_THREADS) buf[fill + k] = xq[rf + off + k];
+                for (int k = threadIdx.x; k < take; k += P2P_THREADS)
+                    buf[fill + k] = shift_src(xq[rf + off + k], o);
                 fill += take;
                 off += take;
                 if (fill == P2P_BUF) {
@@ -400,13 +419,13 @@ __global__ void k_l2p_finalize(int p, int nleaf, const int32_t* __restrict__ lea
                                const double* __restrict__ near, O* __restrict__ phi_out, O* __restrict__ force_out,
                                int field) {
     extern __shared__ unsigned char smem_raw[];
-    const int K = ntri(p);
+    const int K = ntri(p), KS = kstride(p);
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     cplx<T>* Ls = reinterpret_cast<cplx<T>*>(smem_raw) + warp * K;
     int li = blockIdx.x * (blockDim.x >> 5) + warp;
     if (li >= nleaf) return;
     int c = leaves[li];
-    for (int j = lane; j < K; j += 32) Ls[j] = L[(int64_t)c * K + j];
+    for (int j = lane; j < K; j += 32) Ls[j] = L[(int64_t)c * KS + j];
     __syncwarp();
     double4_32a cc = centre[c];
     double invh = 1.0 / cc.w;
@@ -479,7 +498,7 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st) {
     int rc;
     TreeDev& d = t->d;
     if (t->n == 0) return FMM_OK;
-    size_t K = (size_t)ntri(t->prm.p);
+    size_t K = (size_t)kstride(t->prm.p);
     size_t csz = exp_fp64(t) ? sizeof(cplx<double>) : sizeof(cplx<float>);
     char *M = nullptr, *L = nullptr, *xq = nullptr;
     if ((rc = dev_alloc(&M, (size_t)t->ncell * K * csz + 8 * K * csz, t, st))) return rc;
@@ -489,6 +508,11 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st) {
     if ((rc = dev_alloc(&xq, xb, t, st))) return rc;
     if ((rc = dev_alloc(&d.near, (size_t)t->n * 4, t, st))) return rc;
     d.M = M; d.L = L; d.xq = xq;
+    if (t->prm.precision == FMM_PREC_MIXED_TC && t->tc_nitems > 0) {
+        char* ms = nullptr;
+        if ((rc = dev_alloc(&ms, (size_t)t->ncell * 2 * tc_kpad(t->prm.p) * 2, t, st))) return rc;
+        d.tc_msplit = ms;
+    }
     // octant table after the multipoles
     if (exp_fp64(t))
         k_octant_table<double><<<1, 32, 0, st>>>(t->prm.p, (cplx<double>*)(M + (size_t)t->ncell * K * csz));
@@ -500,10 +524,10 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st) {
 }
 
 template <typename T>
-static int launch_m2l_generic(fmm_tree* t, int p, int t0, int t1, const TreeDev& d, const cplx<T>* M,
-                              cplx<T>* L, cudaStream_t st) {
+static int launch_m2l_generic(fmm_tree* t, int p, int t0, int t1, const int64_t* start, const int32_t* src,
+                              const TreeDev& d, const cplx<T>* M, cplx<T>* L, cudaStream_t st) {
     if (t1 <= t0) return FMM_OK;
-    const int K = ntri(p), KI = ntri(2 * p);
+    const int K = ntri(p), KI = ntri(2 * p), KS = kstride(p);
     size_t smem = (size_t)4 * 2 * (K + KI) * sizeof(cplx<T>);
     int rmax = (K + 15) / 16;
     unsigned grid = nblk(t1 - t0, 4);
@@ -512,7 +536,7 @@ static int launch_m2l_generic(fmm_tree* t, int p, int t0, int t1, const TreeDev&
         if (smem > 48 * 1024)                                                                         \
             FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_generic<T, R>,                                    \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        k_m2l_generic<T, R><<<grid, 128, smem, st>>>(p, t0, t1, d.m2l_start, d.m2l_src, d.centre, M, L); \
+        k_m2l_generic<T, R><<<grid, 128, smem, st>>>(p, t0, t1, start, src, d.centre, M, L);               \
         count_launch(t);                                                                              \
         return FMM_OK;                                                                                \
     }
@@ -531,23 +555,24 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     float4* xq32 = (float4*)((char*)d.xq + (size_t)n * sizeof(double4_32a));
     cplx<T>* M = (cplx<T>*)d.M;
     cplx<T>* L = (cplx<T>*)d.L;
-    const cplx<T>* Roct = M + (size_t)t->ncell * K;
+    const cplx<T>* Roct = M + (size_t)t->ncell * kstride(p);
     // particles in sorted order
     stage_begin(t, FMM_STAGE_PREPARE, st);
     if (p2p_fp64(t))
         k_prepare64<Q><<<nblk(n, 256), 256, 0, st>>>(d.spos, d.perm, q, n, xq64);
     else
-        k_prepare32<Q><<<nblk(n, 256), 256, 0, st>>>(d.spos, d.perm, q, n, d.geom, xq64, xq32);
+        k_prepare32<Q><<<nblk(n, 256), 256, 0, st>>>(d.spos, d.perm, q, n, d.pleaf, d.centre, xq64, xq32);
     count_launch(t);
     stage_end(t, FMM_STAGE_PREPARE, st);
     // P2P (near field)
     stage_begin(t, FMM_STAGE_P2P, st);
     if (p2p_fp64(t))
         k_p2p<double><<<t->nleaf, P2P_THREADS, 0, st>>>(t->nleaf, d.leaves, d.first, d.count, d.p2p_start,
-                                                          d.p2p_src, xq64, d.near);
+                                                          d.p2p_src, xq64, d.icentre, 0.f, d.near);
     else
         k_p2p<float><<<t->nleaf, P2P_THREADS, 0, st>>>(t->nleaf, d.leaves, d.first, d.count, d.p2p_start,
-                                                         d.p2p_src, xq32, d.near);
+                                                         d.p2p_src, xq32, d.icentre,
+                                                         (float)(t->side / 4194304.0), d.near);
     count_launch(t);
     stage_end(t, FMM_STAGE_P2P, st);
     // upward pass
@@ -567,7 +592,16 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     stage_end(t, FMM_STAGE_M2M, st);
     // M2L over every target's list (writes L of every cell)
     stage_begin(t, FMM_STAGE_M2L, st);
-    int rc = launch_m2l_generic<T>(t, p, 0, t->ncell, d, M, L, st);
+    int rc;
+    if (t->prm.precision == FMM_PREC_MIXED_TC && t->tc_nitems > 0) {
+        // class-less pairs on the CUDA cores (this also initialises every L), then
+        // the classes on the tensor cores, accumulated into L
+        rc = launch_m2l_generic<T>(t, p, 0, t->ncell, d.rem_start, d.tc_src + t->tc_npairs, d, M, L, st);
+        if (rc) return rc;
+        rc = m2l_tensor_cores(t, (const float*)M, (float*)L, st);
+    } else {
+        rc = launch_m2l_generic<T>(t, p, 0, t->ncell, d.m2l_start, d.m2l_src, d, M, L, st);
+    }
     if (rc) return rc;
     stage_end(t, FMM_STAGE_M2L, st);
     // downward pass

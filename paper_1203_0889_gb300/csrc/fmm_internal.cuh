@@ -24,6 +24,9 @@ namespace fmm {
 
 __host__ __device__ inline int tri(int n, int m) { return n * (n + 1) / 2 + m; }
 __host__ __device__ inline int ntri(int p) { return (p + 1) * (p + 2) / 2; }
+// row stride of expansion arrays (complex entries): rows start on 32-byte (FP32)
+// or 64-byte (FP64) boundaries, so FP32 rows can take 16-byte vector atomics
+__host__ __device__ inline int kstride(int p) { return (ntri(p) + 3) & ~3; }
 
 template <typename T>
 struct cplx {
@@ -136,12 +139,22 @@ struct TreeDev {
     int32_t* child_first = nullptr;
     int32_t* child_count = nullptr;
     double4_32a* centre = nullptr;    // (cx, cy, cz, h) in input coordinates
+    int4* icentre = nullptr;      // twice the centre in units side/2^21 (exact integers), level
     int32_t* leaves = nullptr;    // [nleaf]
+    int32_t* pleaf = nullptr;     // [n] leaf of each sorted particle
     // lists, CSR by target
     int64_t* m2l_start = nullptr; // [ncell+1]
     int32_t* m2l_src = nullptr;   // [nm2l]
     int64_t* p2p_start = nullptr;
     int32_t* p2p_src = nullptr;
+    int32_t* m2l_tgt = nullptr;   // [nm2l] target of each list entry (class build only)
+    // tensor-core M2L (FMM_PREC_MIXED_TC): pairs grouped by translation class
+    int4* tc_items = nullptr;     // [tc_nitems] (class, first pair, rows, -)
+    void* tc_ops = nullptr;       // [nclass][hi|lo][Kp x Kp] bf16 operators
+    int32_t* tc_tgt = nullptr;    // [nm2l] targets in class order (class-less pairs last)
+    int32_t* tc_src = nullptr;
+    int64_t* rem_start = nullptr; // CSR of the class-less pairs by target
+    void* tc_msplit = nullptr;    // [ncell][hi|lo][Kp] bf16 multipoles
     Geometry* geom = nullptr;
     int* status = nullptr;        // device status word(s)
     // evaluation workspace
@@ -168,6 +181,8 @@ struct fmm_tree {
     double origin[3] = {0, 0, 0}, side = 1.0;
     int64_t device_bytes = 0;
     int nsys = 1;
+    int num_sms = 148;
+    int64_t tc_nclass = 0, tc_nitems = 0, tc_npairs = 0, tc_nrem = 0;
     fmm::TreeDev d;
 };
 
@@ -198,6 +213,10 @@ inline void count_launch(fmm_tree* t, int k = 1) {
 int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st);
 int evaluate_impl(fmm_tree* t, const void* q, void* phi, void* force, int dtype, cudaStream_t st);
 int alloc_eval_workspace(fmm_tree* t, cudaStream_t st);
+int build_m2l_classes(fmm_tree* t, cudaStream_t st);
+int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st);
+int tc_kpad(int p);
+bool tc_supported(int p);
 void free_tree_device(fmm_tree* t);
 template <typename T>
 int dev_alloc(T** p, size_t count, fmm_tree* t, cudaStream_t st);

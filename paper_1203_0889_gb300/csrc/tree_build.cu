@@ -7,6 +7,7 @@
 // product, and the lists are put in canonical (target, source) order by a
 // radix sort.
 #include <cub/cub.cuh>
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <vector>
@@ -36,6 +37,10 @@ template int dev_alloc<int32_t>(int32_t**, size_t, fmm_tree*, cudaStream_t);
 template int dev_alloc<int64_t>(int64_t**, size_t, fmm_tree*, cudaStream_t);
 template int dev_alloc<double>(double**, size_t, fmm_tree*, cudaStream_t);
 template int dev_alloc<char>(char**, size_t, fmm_tree*, cudaStream_t);
+template int dev_alloc<int4>(int4**, size_t, fmm_tree*, cudaStream_t);
+template int dev_alloc<__nv_bfloat16>(__nv_bfloat16**, size_t, fmm_tree*, cudaStream_t);
+template int dev_alloc<int2>(int2**, size_t, fmm_tree*, cudaStream_t);
+template int dev_alloc<double4_32a>(double4_32a**, size_t, fmm_tree*, cudaStream_t);
 
 template <typename T>
 static void dev_free(T*& p, cudaStream_t st) {
@@ -96,13 +101,20 @@ __global__ void k_bbox_partial(const T* __restrict__ pos, int64_t n, double* par
 // Root cube (same operation sequence as the oracle): side = longest extent
 // (1 if zero), origin = (lo + hi) * 0.5 - side * 0.5, inv = 2^21 / side.
 __global__ void k_bbox_final(const double* part, int nb, Geometry* g) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    // one warp: lanes reduce strided partials, then a shuffle tree (min/max are exact)
+    int lane = threadIdx.x;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nb; b++)
+    for (int b = lane; b < nb; b += 32)
         for (int d = 0; d < 3; d++) {
             lo[d] = fmin(lo[d], part[b * 6 + d]);
             hi[d] = fmax(hi[d], part[b * 6 + 3 + d]);
         }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int d = 0; d < 3; d++) {
+            lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        }
+    if (lane != 0) return;
     double s = 0.0;
     for (int d = 0; d < 3; d++) s = fmax(s, __dsub_rn(hi[d], lo[d]));
     if (s == 0.0) s = 1.0;
@@ -226,7 +238,7 @@ __global__ void k_emit_children(int lb, int le, int level, int leaf_size, const 
 }
 
 __global__ void k_centres(int ncell, const int32_t* lev, const uint64_t* ckey, const Geometry* g,
-                          double4_32a* centre) {
+                          double4_32a* centre, int4* icentre) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     int l = lev[c];
@@ -234,11 +246,14 @@ __global__ void k_centres(int ncell, const int32_t* lev, const uint64_t* ckey, c
     uint64_t k = ckey[c];
     double u2 = __ddiv_rn(g->side, 4194304.0);  // side / 2^22: the unit of twice a centre
     double x[3];
+    int ic[3];
     for (int d = 0; d < 3; d++) {
         int64_t kc = compact3(k >> d);
         int64_t twoc = 2 * kc * s + s;
+        ic[d] = (int)twoc;
         x[d] = __dadd_rn(g->origin[d], __dmul_rn((double)twoc, u2));
     }
+    icentre[c] = make_int4(ic[0], ic[1], ic[2], l);
     centre[c] = make_double4_32a(x[0], x[1], x[2], __dmul_rn((double)s, __ddiv_rn(g->side, 2097152.0)));
 }
 
@@ -317,9 +332,11 @@ __global__ void k_pack_pairs(const int2* pr, int64_t np, uint64_t* key) {
     if (i < np) key[i] = ((uint64_t)(uint32_t)pr[i].x << 32) | (uint32_t)pr[i].y;
 }
 
-__global__ void k_unpack_sources(const uint64_t* key, int64_t np, int32_t* src) {
+__global__ void k_unpack_sources(const uint64_t* key, int64_t np, int32_t* src, int32_t* tgt) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < np) src[i] = (int32_t)(key[i] & 0xffffffffull);
+    if (i >= np) return;
+    src[i] = (int32_t)(key[i] & 0xffffffffull);
+    if (tgt) tgt[i] = (int32_t)(key[i] >> 32);
 }
 
 // start[c] = first list entry whose target is >= c, for c = 0..ncell
@@ -342,6 +359,15 @@ __global__ void k_leaf_flags(int ncell, const int32_t* child_count, char* flag, 
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// leaf index of every sorted particle (one warp per leaf)
+__global__ void k_particle_leaf(int nleaf, const int32_t* __restrict__ leaves, const int32_t* __restrict__ first,
+                                const int32_t* __restrict__ count, int32_t* pleaf) {
+    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= nleaf) return;
+    int c = leaves[w];
+    for (int i = first[c] + lane; i < first[c] + count[c]; i += 32) pleaf[i] = c;
+}
+
 static int bits_for(int64_t v) {
     int b = 1;
     while (((int64_t)1 << b) <= v && b < 63) b++;
@@ -350,7 +376,7 @@ static int bits_for(int64_t v) {
 
 // sort (target, source) pairs and build the CSR arrays
 static int finish_list(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, int32_t** src,
-                       cudaStream_t st) {
+                       int32_t** tgt, cudaStream_t st) {
     int rc;
     uint64_t *k0 = nullptr, *k1 = nullptr;
     if ((rc = dev_alloc(&k0, np, nullptr, st))) return rc;
@@ -364,7 +390,8 @@ static int finish_list(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, in
     if (np) { FMM_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tmp_bytes, k0, k1, (int64_t)np, 0, end_bit, st)); count_launch(t); }
     if ((rc = dev_alloc(src, np, t, st))) return rc;
     if ((rc = dev_alloc(start, (size_t)t->ncell + 1, t, st))) return rc;
-    if (np) { k_unpack_sources<<<nblk(np, 256), 256, 0, st>>>(k1, np, *src); count_launch(t); }
+    if (tgt && (rc = dev_alloc(tgt, np, t, st))) return rc;
+    if (np) { k_unpack_sources<<<nblk(np, 256), 256, 0, st>>>(k1, np, *src, tgt ? *tgt : nullptr); count_launch(t); }
     k_csr_start<<<nblk(t->ncell + 1, 256), 256, 0, st>>>(k1, np, t->ncell, *start);
     count_launch(t);
     dev_free(tmp, st);
@@ -523,7 +550,8 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     dev_free(lev, st); dev_free(ckey, st); dev_free(first, st); dev_free(count, st);
     dev_free(par, st); dev_free(cf, st); dev_free(cc, st);
     if ((rc = dev_alloc(&d.centre, nc, t, st))) return rc;
-    k_centres<<<nblk(nc, 128), 128, 0, st>>>((int)nc, d.level, d.ckey, d.geom, d.centre);
+    if ((rc = dev_alloc(&d.icentre, nc, t, st))) return rc;
+    k_centres<<<nblk(nc, 128), 128, 0, st>>>((int)nc, d.level, d.ckey, d.geom, d.centre, d.icentre);
     count_launch(t);
     // leaves
     {
@@ -545,6 +573,9 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         FMM_CUDA_TRY(cudaStreamSynchronize(st));
         t->nleaf = h;
         dev_free(tmp, st); dev_free(flag, st); dev_free(nsel, st); dev_free(it, st);
+        if ((rc = dev_alloc(&d.pleaf, (size_t)n, t, st))) return rc;
+        k_particle_leaf<<<nblk((int64_t)h * 32, 256), 256, 0, st>>>(h, d.leaves, d.first, d.count, d.pleaf);
+        count_launch(t);
     }
 
     stage_end(t, FMM_STAGE_SETUP, st);
@@ -585,9 +616,14 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     dev_free(front, st); dev_free(next, st); dev_free(ctr, st);
     t->nm2l = nm;
     t->np2p = npp;
-    if ((rc = finish_list(t, m2l, nm, &d.m2l_start, &d.m2l_src, st))) return rc;
-    if ((rc = finish_list(t, p2p, npp, &d.p2p_start, &d.p2p_src, st))) return rc;
+    const bool want_classes = t->prm.precision == FMM_PREC_MIXED_TC && tc_supported(t->prm.p);
+    if ((rc = finish_list(t, m2l, nm, &d.m2l_start, &d.m2l_src, want_classes ? &d.m2l_tgt : nullptr, st))) return rc;
+    if ((rc = finish_list(t, p2p, npp, &d.p2p_start, &d.p2p_src, nullptr, st))) return rc;
     dev_free(m2l, st); dev_free(p2p, st);
+    if (want_classes) {
+        if ((rc = build_m2l_classes(t, st))) return rc;
+        dev_free(d.m2l_tgt, st);
+    }
     stage_end(t, FMM_STAGE_LISTS, st);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
@@ -599,9 +635,14 @@ void free_tree_device(fmm_tree* t) {
     dev_free(d.keys, st); dev_free(d.perm, st); dev_free(d.spos, st);
     dev_free(d.level, st); dev_free(d.ckey, st); dev_free(d.first, st); dev_free(d.count, st);
     dev_free(d.parent, st); dev_free(d.child_first, st); dev_free(d.child_count, st);
-    dev_free(d.centre, st); dev_free(d.leaves, st);
+    dev_free(d.centre, st); dev_free(d.icentre, st); dev_free(d.leaves, st); dev_free(d.pleaf, st);
     dev_free(d.m2l_start, st); dev_free(d.m2l_src, st); dev_free(d.p2p_start, st); dev_free(d.p2p_src, st);
     dev_free(d.geom, st); dev_free(d.status, st);
+    dev_free(d.m2l_tgt, st); dev_free(d.tc_items, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
+    dev_free(d.rem_start, st);
+    if (d.tc_ops) cudaFreeAsync(d.tc_ops, st);
+    if (d.tc_msplit) cudaFreeAsync(d.tc_msplit, st);
+    d.tc_ops = nullptr; d.tc_msplit = nullptr;
     dev_free(d.M, st); dev_free(d.L, st); dev_free(d.xq, st); dev_free(d.near, st);
 }
 

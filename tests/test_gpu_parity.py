@@ -35,7 +35,7 @@ def test_fp64_matches_oracle(name, n, p, leaf, theta):
     assert O.rel_l2(f, ref_f) <= FP64_TOL
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3])
 @pytest.mark.parametrize("name,n,p,leaf,theta", [
     ("uniform", 16384, 4, 64, 0.5),
     ("plummer", 30000, 8, 64, 0.4),
@@ -50,6 +50,22 @@ def test_reduced_precision_within_bar(prec, name, n, p, leaf, theta):
         phi, f = gpu_eval(t, wl.q, dtype=torch.float64 if dt == "f64" else torch.float32)
         assert O.rel_l2(phi, ref_phi) <= 1e-4
         assert O.rel_l2(f, ref_f) <= 1e-4
+
+
+@pytest.mark.parametrize("name,n,p,theta", [("plummer", 60000, 8, 0.4), ("uniform", 40000, 4, 0.5),
+                                             ("clustered", 50000, 10, 0.5), ("plummer", 20000, 6, 0.6)])
+def test_tensor_core_m2l_matches_fp32(name, n, p, theta):
+    """The tensor-core M2L (split bf16 products, FP32 accumulation) against the
+    all-FP32 path on the same tree: the two differ only in M2L arithmetic."""
+    import paper_1203_0889_gb300 as fmm
+    wl = W.make_workload(name, n=n)
+    t32 = gpu_tree(wl.pos, p=p, leaf_size=64, theta=theta, precision=fmm.PREC_FP32)
+    ttc = gpu_tree(wl.pos, p=p, leaf_size=64, theta=theta, precision=fmm.PREC_MIXED_TC)
+    assert np.array_equal(t32.export()["m2l"], ttc.export()["m2l"])
+    phi32, f32 = gpu_eval(t32, wl.q)
+    phitc, ftc = gpu_eval(ttc, wl.q)
+    assert ttc.status() == fmm.FMM_OK
+    assert O.rel_l2(phitc, phi32) <= 2e-5 and O.rel_l2(ftc, f32) <= 2e-5
 
 
 def test_no_far_field_equals_direct():
