@@ -185,6 +185,17 @@ int64_t fmm_kernel_launches(const fmm_tree* tree, int32_t build);
  * FMM_ERR_TIMEOUT (a bounded wait in the task-queue kernel ran out). */
 int fmm_status(fmm_tree* tree);
 
+/*
+ * Failure injection for the task-queue evaluation (tests of the bounded waits).
+ * Adds `delta` to the initial dependency counter `counter` of cell `cell`:
+ * counter 0 = children still to finish M (M2M), 1 = M2L sources not final,
+ * 2 = L2L prerequisites, 3 = L2P prerequisites.  A counter raised by one
+ * leaves its task never ready: the evaluation then ends after the tree's
+ * timeout with FMM_ERR_TIMEOUT reported by fmm_status, without a hang.
+ * FMM_ERR_STATE if the tree does not use the task queue.  Synchronises.
+ */
+int fmm_inject_dependency(fmm_tree* tree, int32_t counter, int32_t cell, int32_t delta);
+
 /* Free the tree and its device memory (synchronises the device). NULL is a no-op. */
 void fmm_tree_destroy(fmm_tree* tree);
 

@@ -92,6 +92,8 @@ def load():
             lib.fmm_stage_name.restype = C.c_char_p
             lib.fmm_kernel_launches.argtypes = [_P, C.c_int32]
             lib.fmm_kernel_launches.restype = C.c_int64
+            lib.fmm_inject_dependency.argtypes = [_P, C.c_int32, C.c_int32, C.c_int32]
+            lib.fmm_inject_dependency.restype = C.c_int
             lib.fmm_direct_noalloc.argtypes = [C.c_int64, _P, _P, _P, _P, C.c_int, C.c_int32, _P]
             lib.fmm_direct_noalloc.restype = C.c_int
             lib.fmm_direct_noalloc_max_n.argtypes = []
@@ -171,6 +173,10 @@ class Tree:
 
     def status(self) -> int:
         return load().fmm_status(self._h)
+
+    def inject_dependency(self, counter: int, cell: int, delta: int = 1):
+        """Raise a task-queue dependency counter (failure-detection tests)."""
+        _check(load().fmm_inject_dependency(self._h, int(counter), int(cell), int(delta)))
 
     def stage_times(self) -> dict:
         """Per-stage device ms of the last build and evaluation (tree built with TIMING)."""

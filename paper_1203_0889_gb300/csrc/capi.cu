@@ -116,6 +116,10 @@ int fmm_evaluate(fmm_tree* tree, const void* q, void* phi, void* force, int dtyp
     if (tree->n > 0 && !q) { fmm_set_error("q is NULL"); return FMM_ERR_ARG; }
     tree->launches_eval = 0;
     tree->launch_ctr = &tree->launches_eval;
+    if (tree->d.status) {
+        cudaError_t e = cudaMemsetAsync(tree->d.status, 0, sizeof(int), (cudaStream_t)stream);
+        if (e != cudaSuccess) { fmm_set_error("evaluate: %s", cudaGetErrorString(e)); return FMM_ERR_CUDA; }
+    }
     for (int s = FMM_STAGE_PREPARE; s < FMM_NUM_STAGES; s++) tree->ev_used[s] = false;
     int rc = fmm::evaluate_impl(tree, q, phi, force, dtype, (cudaStream_t)stream);
     tree->launch_ctr = nullptr;
@@ -197,6 +201,19 @@ int fmm_tree_export(const fmm_tree* t, uint64_t* keys, int64_t* perm, int32_t* l
             for (int64_t k = st[c]; k < st[c + 1]; k++) { out[2 * k] = (int32_t)c; out[2 * k + 1] = src[k]; }
     }
 #undef CP
+    return FMM_OK;
+}
+
+int fmm_inject_dependency(fmm_tree* t, int32_t counter, int32_t cell, int32_t delta) {
+    if (!t) { fmm_set_error("tree is NULL"); return FMM_ERR_ARG; }
+    if (!t->d.q_cnt_init) { fmm_set_error("tree does not use the task queue"); return FMM_ERR_STATE; }
+    if (counter < 0 || counter > 3 || cell < 0 || cell >= t->ncell) { fmm_set_error("bad counter or cell"); return FMM_ERR_ARG; }
+    int32_t v = 0;
+    int32_t* p = t->d.q_cnt_init + (size_t)counter * t->ncell + cell;
+    cudaError_t e = cudaMemcpy(&v, p, 4, cudaMemcpyDeviceToHost);
+    v += delta;
+    if (e == cudaSuccess) e = cudaMemcpy(p, &v, 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { fmm_set_error("inject: %s", cudaGetErrorString(e)); return FMM_ERR_CUDA; }
     return FMM_OK;
 }
 

@@ -15,8 +15,10 @@
 // theorem takes the forms above.  Interaction is non-mutual (Section 4):
 // every kernel writes only its target cell or target particles.
 #include <algorithm>
+#include <type_traits>
 
 #include "fmm_internal.cuh"
+#include "stages.cuh"
 
 namespace fmm {
 
@@ -48,128 +50,89 @@ __global__ void k_prepare32(const double* __restrict__ spos, const int32_t* __re
     xq32[i] = make_float4((float)(x - c.x), (float)(y - c.y), (float)(z - c.z), (float)qq);
 }
 
-// R_k^l(d/h_P) for the eight child octants, d/h_P = (+-1/4, +-1/4, +-1/4);
-// bit 0 of the octant is x, bit 1 y, bit 2 z.
+// Dense real forms of the child <-> parent shifts, one per octant (the shift
+// d/h_P = (+-1/4, +-1/4, +-1/4) depends only on the octant).  For an input
+// coefficient X = Xt_{n'}^{m'} (m' >= 0) the shift adds a X + b conj(X) to an
+// output coefficient (b from the order -m' term), i.e. a real 2 x 2 block:
+//   re += (a.re + b.re) X.re + (b.im - a.im) X.im,  im += (a.im + b.im) X.re + (a.re - b.re) X.im
+//   M2M: out (n, m) <- in (n', m'):  a = R_{n-n'}^{m-m'} 2^-n',  b = (-1)^m' R_{n-n'}^{m+m'} 2^-n'
+//   L2L: out (k, l) <- in (n, m):    a = R_{n-k}^{m-l} 2^-(k+1), b = (-1)^m R_{n-k}^{-m-l} 2^-(k+1)
+// Stored input-major (row = input index) so that lanes reading consecutive
+// outputs read consecutive words.  ops[kind][octant][in][out], kind 0 = M2M, 1 = L2L.
 template <typename T>
-__global__ void k_octant_table(int p, cplx<T>* Roct) {
-    int o = threadIdx.x;
-    if (o >= 8) return;
-    T x = (o & 1) ? T(0.25) : T(-0.25), y = (o & 2) ? T(0.25) : T(-0.25), z = (o & 4) ? T(0.25) : T(-0.25);
-    regular_harmonics<T>(p, x, y, z, Roct + o * ntri(p));
+__global__ void k_shift_operators(int p, T* ops) {
+    extern __shared__ unsigned char smraw[];
+    cplx<double>* R = reinterpret_cast<cplx<double>*>(smraw);
+    const int kind = blockIdx.x >> 3, o = blockIdx.x & 7, K = ntri(p), K2 = 2 * K;
+    if (threadIdx.x == 0)
+        regular_harmonics<double>(p, (o & 1) ? 0.25 : -0.25, (o & 2) ? 0.25 : -0.25, (o & 4) ? 0.25 : -0.25, R);
+    __syncthreads();
+    T* out = ops + (size_t)blockIdx.x * K2 * K2;
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+        int jo = e / K, ji = e % K;   // output / input complex index
+        int no = 0, ni = 0;
+        while (tri(no + 1, 0) <= jo) no++;
+        while (tri(ni + 1, 0) <= ji) ni++;
+        int mo = jo - tri(no, 0), mi = ji - tri(ni, 0);
+        cplx<double> a = {0, 0}, b = {0, 0};
+        if (kind == 0 && ni <= no) {
+            double sc = ldexp(1.0, -ni);
+            a = get_sym(R, no - ni, mo - mi);
+            if (mi > 0) b = get_sym(R, no - ni, mo + mi);
+            if (mi & 1) { b.re = -b.re; b.im = -b.im; }
+            a.re *= sc; a.im *= sc; b.re *= sc; b.im *= sc;
+        } else if (kind == 1 && ni >= no) {
+            double sc = ldexp(1.0, -(no + 1));
+            a = get_sym(R, ni - no, mi - mo);
+            if (mi > 0) b = get_sym(R, ni - no, -mi - mo);
+            if (mi & 1) { b.re = -b.re; b.im = -b.im; }
+            a.re *= sc; a.im *= sc; b.re *= sc; b.im *= sc;
+        }
+        // rows: inputs (2 ji + re|im), columns: outputs (2 jo + re|im)
+        T* r0 = out + (size_t)(2 * ji) * K2 + 2 * jo;
+        T* r1 = r0 + K2;
+        r0[0] = (T)(a.re + b.re);
+        r0[1] = (T)(a.im + b.im);
+        r1[0] = mi > 0 ? (T)(b.im - a.im) : T(0);
+        r1[1] = mi > 0 ? (T)(a.re - b.re) : T(0);
+    }
 }
 
 // ---------------------------------------------------------------------------
-// P2M: one warp per leaf; each coefficient is reduced over the warp
+// stage-by-stage kernels (bodies in stages.cuh)
 // ---------------------------------------------------------------------------
 
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+// one warp per destination cell of one level
+template <typename T, int RQ>
+__global__ void __launch_bounds__(128) k_shift_dense(int p, int lb, int le, int kind,
+                                                     const int32_t* __restrict__ child_first,
+                                                     const int32_t* __restrict__ child_count,
+                                                     const int32_t* __restrict__ parent,
+                                                     const uint64_t* __restrict__ ckey, const T* __restrict__ ops,
+                                                     cplx<T>* __restrict__ E) {
+    extern __shared__ unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* xin = reinterpret_cast<T*>(smem_raw) + warp * 2 * ntri(p);
+    const int c = lb + blockIdx.x * (blockDim.x >> 5) + warp;
+    if (c >= le) return;
+    shift_cell<T, RQ, false>(p, c, kind, lane, child_first, child_count, parent, ckey, ops, E, xin);
 }
 
+// one warp per leaf
 template <typename T>
 __global__ void k_p2m(int p, int nleaf, const int32_t* __restrict__ leaves, const int32_t* __restrict__ first,
                       const int32_t* __restrict__ count, const double4_32a* __restrict__ centre,
                       const double4_32a* __restrict__ xq, cplx<T>* __restrict__ M) {
     extern __shared__ unsigned char smem_raw[];
-    const int K = ntri(p), KS = kstride(p);
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cplx<T>* acc = reinterpret_cast<cplx<T>*>(smem_raw) + warp * K;
-    int li = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cplx<T>* acc = reinterpret_cast<cplx<T>*>(smem_raw) + warp * ntri(p);
+    const int li = blockIdx.x * (blockDim.x >> 5) + warp;
     if (li >= nleaf) return;
-    int c = leaves[li];
-    for (int j = lane; j < K; j += 32) acc[j] = cmk<T>(0, 0);
-    __syncwarp();
-    double4_32a cc = centre[c];
-    double invh = 1.0 / cc.w;
-    int f = first[c], cnt = count[c];
-    for (int base = 0; base < cnt; base += 32) {
-        int i = base + lane;
-        T ux = 0, uy = 0, uz = 0, q = 0;
-        if (i < cnt) {
-            double4_32a a = xq[f + i];
-            ux = (T)((a.x - cc.x) * invh); uy = (T)((a.y - cc.y) * invh); uz = (T)((a.z - cc.z) * invh);
-            q = (T)a.w;
-        }
-        T r2 = ux * ux + uy * uy + uz * uz;
-        cplx<T> rmm = cmk<T>(q, 0);
-        for (int m = 0; m <= p; m++) {
-            if (m > 0) rmm = cscale(cmul(rmm, cmk<T>(ux, uy)), T(1) / T(2 * m));
-            cplx<T> a = rmm, b = cscale(rmm, uz);
-            for (int n = m; n <= p; n++) {
-                cplx<T> v;
-                if (n == m) v = a;
-                else if (n == m + 1) v = b;
-                else {
-                    T inv = T(1) / T((n + m) * (n - m));
-                    v = cmk<T>((T(2 * n - 1) * uz * b.re - r2 * a.re) * inv,
-                               (T(2 * n - 1) * uz * b.im - r2 * a.im) * inv);
-                    a = b; b = v;
-                }
-                T sr = warp_sum(v.re), si = warp_sum(v.im);
-                if (lane == 0) { acc[tri(n, m)].re += sr; acc[tri(n, m)].im += si; }
-            }
-        }
-    }
-    __syncwarp();
-    for (int j = lane; j < K; j += 32) M[(int64_t)c * KS + j] = acc[j];
+    p2m_leaf<T>(p, leaves[li], lane, first, count, centre, xq, M, acc);
 }
 
-// ---------------------------------------------------------------------------
-// M2M: one warp per parent cell of one level
-// ---------------------------------------------------------------------------
-
-template <typename T>
-__global__ void k_m2m(int p, int lb, int le, const int32_t* __restrict__ child_first,
-                      const int32_t* __restrict__ child_count, const uint64_t* __restrict__ ckey,
-                      const cplx<T>* __restrict__ Roct, cplx<T>* __restrict__ M) {
-    extern __shared__ unsigned char smem_raw[];
-    const int K = ntri(p), KS = kstride(p);
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cplx<T>* Mc = reinterpret_cast<cplx<T>*>(smem_raw) + warp * 2 * K;
-    cplx<T>* acc = Mc + K;
-    int c = lb + blockIdx.x * (blockDim.x >> 5) + warp;
-    if (c >= le) return;
-    int nc = child_count[c];
-    if (nc == 0) return;
-    for (int j = lane; j < K; j += 32) acc[j] = cmk<T>(0, 0);
-    int cf = child_first[c];
-    for (int ch = 0; ch < nc; ch++) {
-        int cidx = cf + ch;
-        __syncwarp();
-        for (int j = lane; j < K; j += 32) Mc[j] = M[(int64_t)cidx * KS + j];
-        __syncwarp();
-        const cplx<T>* R = Roct + (int)(ckey[cidx] & 7) * K;
-        for (int j = lane; j < K; j += 32) {
-            int n = 0;
-            while (tri(n + 1, 0) <= j) n++;
-            int m = j - tri(n, 0);
-            cplx<T> s = cmk<T>(0, 0);
-            T scale = T(1);
-            for (int k = n; k >= 0; k--) {      // source degree n-k, scale 2^{-(n-k)}
-                int js = n - k;
-                for (int l = -k; l <= k; l++) {
-                    int ms = m - l;
-                    if (ms > js || -ms > js) continue;
-                    cplx<T> r = get_sym(R, k, l), mv = get_sym(Mc, js, ms);
-                    cplx<T> t = cmul(r, mv);
-                    s.re += scale * t.re; s.im += scale * t.im;
-                }
-                scale *= T(0.5);
-            }
-            acc[j] = cadd(acc[j], s);
-        }
-    }
-    __syncwarp();
-    for (int j = lane; j < K; j += 32) M[(int64_t)c * KS + j] = acc[j];
-}
-
-// ---------------------------------------------------------------------------
-// M2L (any pair of cells): one warp per target, each half-warp one source.
-// Lane (h, i) accumulates the outputs j = i, i+16, ... < ntri(p).
-// ---------------------------------------------------------------------------
-
+// M2L (any pair of cells): one warp per target, each half-warp one source
+// at a time; lane (h, i) accumulates the outputs j = i, i + 16, ...
 template <typename T, int RMAX>
 __global__ void __launch_bounds__(128) k_m2l_generic(int p, int t0, int t1, const int64_t* __restrict__ start,
                                                      const int32_t* __restrict__ src,
@@ -177,78 +140,17 @@ __global__ void __launch_bounds__(128) k_m2l_generic(int p, int t0, int t1, cons
                                                      const cplx<T>* __restrict__ M, cplx<T>* __restrict__ L) {
     extern __shared__ unsigned char smem_raw[];
     const int K = ntri(p), KI = ntri(2 * p), KS = kstride(p);
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
-    cplx<T>* base = reinterpret_cast<cplx<T>*>(smem_raw) + warp * 2 * (K + KI);
-    cplx<T>* Ms = base + half * (K + KI);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    cplx<T>* Ms = reinterpret_cast<cplx<T>*>(smem_raw) + (warp * 2 + half) * (K + KI);
     cplx<T>* Is = Ms + K;
-    int t = t0 + blockIdx.x * (blockDim.x >> 5) + warp;
+    const int t = t0 + blockIdx.x * (blockDim.x >> 5) + warp;
     if (t >= t1) return;
     int kk[RMAX], ll[RMAX];
     cplx<T> acc[RMAX];
+    m2l_output_index<RMAX>(p, hl, kk, ll);
 #pragma unroll
-    for (int r = 0; r < RMAX; r++) {
-        int j = hl + 16 * r, n = 0;
-        if (j < K) { while (tri(n + 1, 0) <= j) n++; }
-        kk[r] = n;
-        ll[r] = j < K ? j - tri(n, 0) : 0;
-        acc[r] = cmk<T>(0, 0);
-    }
-    int64_t s0 = start[t], s1 = start[t + 1];
-    double4_32a ct = centre[t];
-    double invht = 1.0 / ct.w;
-    for (int64_t e = s0; e < s1; e += 2) {
-        int64_t my = e + half;
-        bool valid = my < s1;
-        if (valid) {
-            int s = src[my];
-            double4_32a cs = centre[s];
-            T rho = (T)(cs.w * invht);
-            // stage rho^n Mt_n^m(s)
-            for (int j = hl; j < K; j += 16) {
-                int n = 0;
-                while (tri(n + 1, 0) <= j) n++;
-                T sc = T(1);
-                for (int i = 0; i < n; i++) sc *= rho;
-                Ms[j] = cscale(M[(int64_t)s * KS + j], sc);
-            }
-            T dx = (T)((ct.x - cs.x) * invht), dy = (T)((ct.y - cs.y) * invht), dz = (T)((ct.z - cs.z) * invht);
-            for (int m = hl; m <= 2 * p; m += 16) irregular_column<T>(2 * p, m, dx, dy, dz, Is);
-        }
-        __syncwarp();
-        if (valid) {
-#pragma unroll
-            for (int r = 0; r < RMAX; r++) {
-                if (hl + 16 * r >= K) break;
-                int k = kk[r], l = ll[r];
-                cplx<T> a = acc[r];
-                for (int n = 0; n <= p; n++) {
-                    const cplx<T>* Ij = Is + tri(n + k, 0);
-                    const cplx<T>* Mn = Ms + tri(n, 0);
-                    // m = 0: Mt_n^0 real
-                    {
-                        T mr = Mn[0].re;
-                        cplx<T> x = Ij[l];
-                        a.re += mr * x.re;
-                        a.im -= mr * x.im;
-                    }
-                    for (int m = 1; m <= n; m++) {
-                        cplx<T> mv = Mn[m];
-                        cfma_cj(a, mv, Ij[m + l]);                       // M conj(I^{m+l})
-                        // negative order -m:  (-1)^m conj(M) conj(I^{l-m})
-                        bool ge = l >= m;
-                        cplx<T> x = Ij[ge ? l - m : m - l];
-                        T sgn = ((ge ? m : l) & 1) ? T(-1) : T(1);
-                        // conj(M) * (ge ? conj(x) : x) * sgn
-                        T xi = ge ? -x.im : x.im;
-                        a.re += sgn * (mv.re * x.re + mv.im * xi);
-                        a.im += sgn * (mv.re * xi - mv.im * x.re);
-                    }
-                }
-                acc[r] = a;
-            }
-        }
-        __syncwarp();
-    }
+    for (int r = 0; r < RMAX; r++) acc[r] = cmk<T>(0, 0);
+    m2l_slot<T, RMAX, false>(p, t, half, 2, hl, start, src, centre, M, Ms, Is, kk, ll, acc);
 #pragma unroll
     for (int r = 0; r < RMAX; r++) {
         acc[r].re += __shfl_xor_sync(0xffffffffu, acc[r].re, 16);
@@ -257,160 +159,29 @@ __global__ void __launch_bounds__(128) k_m2l_generic(int p, int t0, int t1, cons
     if (half == 0) {
 #pragma unroll
         for (int r = 0; r < RMAX; r++) {
-            int j = hl + 16 * r;
-            if (j < K) {
-                T sg = (kk[r] & 1) ? T(-1) : T(1);
-                L[(int64_t)t * KS + j] = cscale(acc[r], sg);
-            }
+            const int j = hl + 16 * r;
+            if (j < K) L[(int64_t)t * KS + j] = cscale(acc[r], (kk[r] & 1) ? T(-1) : T(1));
         }
     }
 }
 
-// ---------------------------------------------------------------------------
-// L2L: one warp per child cell of one level
-// ---------------------------------------------------------------------------
-
-template <typename T>
-__global__ void k_l2l(int p, int lb, int le, const int32_t* __restrict__ parent, const uint64_t* __restrict__ ckey,
-                      const cplx<T>* __restrict__ Roct, cplx<T>* __restrict__ L) {
-    extern __shared__ unsigned char smem_raw[];
-    const int K = ntri(p), KS = kstride(p);
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cplx<T>* Lp = reinterpret_cast<cplx<T>*>(smem_raw) + warp * K;
-    int c = lb + blockIdx.x * (blockDim.x >> 5) + warp;
-    if (c >= le) return;
-    int pc = parent[c];
-    for (int j = lane; j < K; j += 32) Lp[j] = L[(int64_t)pc * KS + j];
-    __syncwarp();
-    const cplx<T>* R = Roct + (int)(ckey[c] & 7) * K;
-    for (int j = lane; j < K; j += 32) {
-        int k = 0;
-        while (tri(k + 1, 0) <= j) k++;
-        int l = j - tri(k, 0);
-        cplx<T> s = cmk<T>(0, 0);
-        for (int n = k; n <= p; n++)
-            for (int m = -n; m <= n; m++) {
-                int mr = m - l;
-                if (mr > n - k || -mr > n - k) continue;
-                cfma(s, get_sym(Lp, n, m), get_sym(R, n - k, mr));
-            }
-        T sc = T(1);
-        for (int i = 0; i <= k; i++) sc *= T(0.5);
-        cplx<T> o = L[(int64_t)c * KS + j];
-        L[(int64_t)c * KS + j] = cadd(o, cscale(s, sc));
-    }
-}
-
-// ---------------------------------------------------------------------------
-// P2P: one block per target leaf; sources staged in shared memory.
-// Thread t works on target (t mod nt) and source stream (t / nt).
-// ---------------------------------------------------------------------------
-
-template <typename T> struct Vec4;
-template <> struct Vec4<double> { typedef double4_32a type; };
-template <> struct Vec4<float> { typedef float4 type; };
-
-// FP64 records hold absolute positions; FP32 records hold positions relative
-// to their own leaf centre, so a source is shifted by (c_s - c_t) when staged.
-// The offset c_s - c_t comes from the exact integer centres times side/2^22 in
-// FP32: no FP64 instruction per source (the FP64 pipe is narrow on this GPU).
-template <typename T> struct Offset3 { T x, y, z; };
-__device__ __forceinline__ double4_32a shift_src(double4_32a v, Offset3<double>) { return v; }
-__device__ __forceinline__ float4 shift_src(float4 v, Offset3<float> o) {
-    return make_float4(v.x + o.x, v.y + o.y, v.z + o.z, v.w);
-}
-
-__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
-__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
-
-constexpr int P2P_THREADS = 128;
-constexpr int P2P_BUF = 512;
-
+// one block per target leaf
 template <typename T>
 __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nleaf, const int32_t* __restrict__ leaves,
                                                      const int32_t* __restrict__ first,
                                                      const int32_t* __restrict__ count,
                                                      const int64_t* __restrict__ start,
-                                                     const int32_t* __restrict__ src,
+                                                     const int4* __restrict__ rec,
                                                      const typename Vec4<T>::type* __restrict__ xq,
                                                      const int4* __restrict__ icentre, float u2f,
                                                      double* __restrict__ near) {
-    typedef typename Vec4<T>::type V;
-    __shared__ V buf[P2P_BUF];
+    __shared__ typename Vec4<T>::type buf[P2P_BUF];
     __shared__ T part[P2P_THREADS][4];
-    int li = blockIdx.x;
-    if (li >= nleaf) return;
-    int c = leaves[li];
-    int tf = first[c], nt = count[c];
-    int64_t s0 = start[c], s1 = start[c + 1];
-    const int4 ict = icentre[c];
-    for (int tb = 0; tb < nt; tb += P2P_THREADS) {
-        int ntc = min(P2P_THREADS, nt - tb);
-        int G = P2P_THREADS / ntc;
-        int ti = threadIdx.x % ntc, sub = threadIdx.x / ntc;
-        bool active = sub < G;
-        V me = xq[tf + tb + ti];
-        T phi = 0, gx = 0, gy = 0, gz = 0;
-        int fill = 0;
-        auto compute = [&](int nfill) {
-            if (!active) return;
-            for (int j = sub; j < nfill; j += G) {
-                V s = buf[j];
-                T dx = me.x - s.x, dy = me.y - s.y, dz = me.z - s.z;
-                T r2 = dx * dx + dy * dy + dz * dz;
-                T rinv = r2 > T(0) ? rsqrt_t(r2) : T(0);
-                T qr = s.w * rinv;
-                phi += qr;
-                T qr3 = qr * rinv * rinv;
-                gx -= qr3 * dx; gy -= qr3 * dy; gz -= qr3 * dz;
-            }
-        };
-        for (int64_t e = s0; e < s1; e++) {
-            int sc = src[e];
-            int rf = first[sc], rc = count[sc], off = 0;
-            const int4 ics = icentre[sc];
-            Offset3<T> o;
-            o.x = (T)((float)(ics.x - ict.x) * u2f);
-            o.y = (T)((float)(ics.y - ict.y) * u2f);
-            o.z = (T)((float)(ics.z - ict.z) * u2f);
-            while (off < rc) {
-                int take = min(rc - off, P2P_BUF - fill);
-                for (int k = threadIdx.x; k < take; k += P2P_THREADS)
-                    buf[fill + k] = shift_src(xq[rf + off + k], o);
-                fill += take;
-                off += take;
-                if (fill == P2P_BUF) {
-                    __syncthreads();
-                    compute(fill);
-                    __syncthreads();
-                    fill = 0;
-                }
-            }
-        }
-        if (fill) {
-            __syncthreads();
-            compute(fill);
-            __syncthreads();
-        }
-        part[threadIdx.x][0] = phi; part[threadIdx.x][1] = gx; part[threadIdx.x][2] = gy; part[threadIdx.x][3] = gz;
-        __syncthreads();
-        if (threadIdx.x < ntc) {
-            double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-            for (int s = 0; s < G; s++) {
-                int k = s * ntc + threadIdx.x;
-                a0 += part[k][0]; a1 += part[k][1]; a2 += part[k][2]; a3 += part[k][3];
-            }
-            int64_t i = tf + tb + threadIdx.x;
-            near[4 * i] = a0; near[4 * i + 1] = a1; near[4 * i + 2] = a2; near[4 * i + 3] = a3;
-        }
-        __syncthreads();
-    }
+    if (blockIdx.x >= nleaf) return;
+    p2p_leaf<T>(leaves[blockIdx.x], first, count, start, rec, xq, icentre, u2f, near, buf, part);
 }
 
-// ---------------------------------------------------------------------------
-// L2P + near field + output in input order: one warp per leaf, one particle per lane
-// ---------------------------------------------------------------------------
-
+// one warp per leaf: L2P + near field + output in input order
 template <typename T, typename O>
 __global__ void k_l2p_finalize(int p, int nleaf, const int32_t* __restrict__ leaves,
                                const int32_t* __restrict__ first, const int32_t* __restrict__ count,
@@ -420,69 +191,14 @@ __global__ void k_l2p_finalize(int p, int nleaf, const int32_t* __restrict__ lea
                                int field) {
     extern __shared__ unsigned char smem_raw[];
     const int K = ntri(p), KS = kstride(p);
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     cplx<T>* Ls = reinterpret_cast<cplx<T>*>(smem_raw) + warp * K;
-    int li = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int li = blockIdx.x * (blockDim.x >> 5) + warp;
     if (li >= nleaf) return;
-    int c = leaves[li];
+    const int c = leaves[li];
     for (int j = lane; j < K; j += 32) Ls[j] = L[(int64_t)c * KS + j];
     __syncwarp();
-    double4_32a cc = centre[c];
-    double invh = 1.0 / cc.w;
-    int f = first[c], cnt = count[c];
-    for (int i = lane; i < cnt; i += 32) {
-        double4_32a a = xq[f + i];
-        T ux = (T)((a.x - cc.x) * invh), uy = (T)((a.y - cc.y) * invh), uz = (T)((a.z - cc.z) * invh);
-        T r2 = ux * ux + uy * uy + uz * uz;
-        T fp = 0, gx = 0, gy = 0, gz = 0;
-        cplx<T> rmm = cmk<T>(1, 0);
-        for (int m = 0; m <= p; m++) {
-            if (m > 0) rmm = cscale(cmul(rmm, cmk<T>(ux, uy)), T(1) / T(2 * m));
-            cplx<T> a0 = rmm, b0 = cscale(rmm, uz);
-            T w = m == 0 ? T(1) : T(2);
-            for (int n = m; n <= p; n++) {
-                cplx<T> S;
-                if (n == m) S = a0;
-                else if (n == m + 1) S = b0;
-                else {
-                    T inv = T(1) / T((n + m) * (n - m));
-                    S = cmk<T>((T(2 * n - 1) * uz * b0.re - r2 * a0.re) * inv,
-                               (T(2 * n - 1) * uz * b0.im - r2 * a0.im) * inv);
-                    a0 = b0; b0 = S;
-                }
-                cplx<T> Lnm = Ls[tri(n, m)];
-                fp += w * (Lnm.re * S.re - Lnm.im * S.im);
-                if (n + 1 <= p) {
-                    const cplx<T>* L1 = Ls + tri(n + 1, 0);
-                    cplx<T> lz = L1[m];
-                    gz += w * (lz.re * S.re - lz.im * S.im);
-                    if (m == 0) {
-                        gx += L1[1].re * S.re;
-                        gy -= L1[1].im * S.re;
-                    } else {
-                        cplx<T> up = L1[m + 1], dn = L1[m - 1];
-                        cplx<T> A = csub(up, dn), B = cadd(up, dn);
-                        gx += A.re * S.re - A.im * S.im;
-                        gy += -(B.im * S.re + B.re * S.im);  // Re(i B S)
-                    }
-                }
-            }
-        }
-        int64_t gi = f + i;
-        double ph = (double)fp * invh + near[4 * gi];
-        double ih2 = invh * invh;
-        double ex = -((double)gx * ih2 + near[4 * gi + 1]);
-        double ey = -((double)gy * ih2 + near[4 * gi + 2]);
-        double ez = -((double)gz * ih2 + near[4 * gi + 3]);
-        int64_t o = perm[gi];
-        if (phi_out) phi_out[o] = (O)ph;
-        if (force_out) {
-            double s = field ? 1.0 : a.w;
-            force_out[3 * o] = (O)(s * ex);
-            force_out[3 * o + 1] = (O)(s * ey);
-            force_out[3 * o + 2] = (O)(s * ez);
-        }
-    }
+    l2p_particles<T, O, false>(p, c, lane, 32, Ls, first, count, centre, xq, perm, near, phi_out, force_out, field);
 }
 
 // ---------------------------------------------------------------------------
@@ -501,26 +217,55 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st) {
     size_t K = (size_t)kstride(t->prm.p);
     size_t csz = exp_fp64(t) ? sizeof(cplx<double>) : sizeof(cplx<float>);
     char *M = nullptr, *L = nullptr, *xq = nullptr;
-    if ((rc = dev_alloc(&M, (size_t)t->ncell * K * csz + 8 * K * csz, t, st))) return rc;
+    if ((rc = dev_alloc(&M, (size_t)t->ncell * K * csz, t, st))) return rc;
     if ((rc = dev_alloc(&L, (size_t)t->ncell * K * csz, t, st))) return rc;
     // double4_32a copy always (P2M/L2P positions), plus float4 for FP32 P2P
     size_t xb = (size_t)t->n * sizeof(double4_32a) + (p2p_fp64(t) ? 0 : (size_t)t->n * sizeof(float4));
     if ((rc = dev_alloc(&xq, xb, t, st))) return rc;
     if ((rc = dev_alloc(&d.near, (size_t)t->n * 4, t, st))) return rc;
     d.M = M; d.L = L; d.xq = xq;
+    {
+        const int K2 = 2 * ntri(t->prm.p);
+        size_t tsz = exp_fp64(t) ? sizeof(double) : sizeof(float);
+        char* ops = nullptr;
+        if ((rc = dev_alloc(&ops, (size_t)16 * K2 * K2 * tsz, t, st))) return rc;
+        d.shift_ops = ops;
+        size_t smem = (size_t)ntri(t->prm.p) * sizeof(cplx<double>);
+        if (exp_fp64(t))
+            k_shift_operators<double><<<16, 256, smem, st>>>(t->prm.p, (double*)ops);
+        else
+            k_shift_operators<float><<<16, 256, smem, st>>>(t->prm.p, (float*)ops);
+        count_launch(t);
+    }
     if (t->prm.precision == FMM_PREC_MIXED_TC && t->tc_nitems > 0) {
         char* ms = nullptr;
         if ((rc = dev_alloc(&ms, (size_t)t->ncell * 2 * tc_kpad(t->prm.p) * 2, t, st))) return rc;
         d.tc_msplit = ms;
     }
-    // octant table after the multipoles
-    if (exp_fp64(t))
-        k_octant_table<double><<<1, 32, 0, st>>>(t->prm.p, (cplx<double>*)(M + (size_t)t->ncell * K * csz));
-    else
-        k_octant_table<float><<<1, 32, 0, st>>>(t->prm.p, (cplx<float>*)(M + (size_t)t->ncell * K * csz));
-    count_launch(t);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
+}
+
+template <typename T>
+static int launch_shift(fmm_tree* t, int kind, int lb, int le, cplx<T>* E, cudaStream_t st) {
+    const int p = t->prm.p, K2 = 2 * ntri(p), W = 4;
+    if (le <= lb) return FMM_OK;
+    const TreeDev& d = t->d;
+    const T* ops = (const T*)d.shift_ops;
+    size_t smem = (size_t)W * K2 * sizeof(T);
+    unsigned grid = nblk(le - lb, W);
+    int rq = (K2 + 31) / 32;
+#define SHIFT_CASE(R)                                                                                         \
+    if (rq <= R) {                                                                                            \
+        k_shift_dense<T, R><<<grid, 32 * W, smem, st>>>(p, lb, le, kind, d.child_first, d.child_count, d.parent, \
+                                                        d.ckey, ops, E);                                      \
+        count_launch(t);                                                                                      \
+        return FMM_OK;                                                                                        \
+    }
+    SHIFT_CASE(1) SHIFT_CASE(2) SHIFT_CASE(3) SHIFT_CASE(5) SHIFT_CASE(8) SHIFT_CASE(12) SHIFT_CASE(15)
+#undef SHIFT_CASE
+    fmm_set_error("order too high for the shift kernel");
+    return FMM_ERR_ARG;
 }
 
 template <typename T>
@@ -555,7 +300,6 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     float4* xq32 = (float4*)((char*)d.xq + (size_t)n * sizeof(double4_32a));
     cplx<T>* M = (cplx<T>*)d.M;
     cplx<T>* L = (cplx<T>*)d.L;
-    const cplx<T>* Roct = M + (size_t)t->ncell * kstride(p);
     // particles in sorted order
     stage_begin(t, FMM_STAGE_PREPARE, st);
     if (p2p_fp64(t))
@@ -564,14 +308,21 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
         k_prepare32<Q><<<nblk(n, 256), 256, 0, st>>>(d.spos, d.perm, q, n, d.pleaf, d.centre, xq64, xq32);
     count_launch(t);
     stage_end(t, FMM_STAGE_PREPARE, st);
+    if (queue_supported(t)) {
+        // one persistent launch runs the whole task graph
+        if constexpr (std::is_same<T, double>::value) {
+            if (p2p_fp64(t)) return evaluate_queue<T, double, O>(t, xq64, xq64, phi, force, st);
+        }
+        return evaluate_queue<T, float, O>(t, xq64, xq32, phi, force, st);
+    }
     // P2P (near field)
     stage_begin(t, FMM_STAGE_P2P, st);
     if (p2p_fp64(t))
         k_p2p<double><<<t->nleaf, P2P_THREADS, 0, st>>>(t->nleaf, d.leaves, d.first, d.count, d.p2p_start,
-                                                          d.p2p_src, xq64, d.icentre, 0.f, d.near);
+                                                          d.p2p_rec, xq64, d.icentre, 0.f, d.near);
     else
         k_p2p<float><<<t->nleaf, P2P_THREADS, 0, st>>>(t->nleaf, d.leaves, d.first, d.count, d.p2p_start,
-                                                         d.p2p_src, xq32, d.icentre,
+                                                         d.p2p_rec, xq32, d.icentre,
                                                          (float)(t->side / 4194304.0), d.near);
     count_launch(t);
     stage_end(t, FMM_STAGE_P2P, st);
@@ -584,10 +335,8 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     stage_end(t, FMM_STAGE_P2M, st);
     stage_begin(t, FMM_STAGE_M2M, st);
     for (int l = t->nlevel - 2; l >= 0; l--) {
-        int lb = t->level_start[l], le = t->level_start[l + 1];
-        k_m2m<T><<<nblk(le - lb, W), 32 * W, W * 2 * K * sizeof(cplx<T>), st>>>(p, lb, le, d.child_first,
-                                                                                 d.child_count, d.ckey, Roct, M);
-        count_launch(t);
+        int rc0 = launch_shift<T>(t, 0, t->level_start[l], t->level_start[l + 1], M, st);
+        if (rc0) return rc0;
     }
     stage_end(t, FMM_STAGE_M2M, st);
     // M2L over every target's list (writes L of every cell)
@@ -607,9 +356,8 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     // downward pass
     stage_begin(t, FMM_STAGE_L2L, st);
     for (int l = 1; l < t->nlevel; l++) {
-        int lb = t->level_start[l], le = t->level_start[l + 1];
-        k_l2l<T><<<nblk(le - lb, W), 32 * W, W * K * sizeof(cplx<T>), st>>>(p, lb, le, d.parent, d.ckey, Roct, L);
-        count_launch(t);
+        rc = launch_shift<T>(t, 1, t->level_start[l], t->level_start[l + 1], L, st);
+        if (rc) return rc;
     }
     stage_end(t, FMM_STAGE_L2L, st);
     stage_begin(t, FMM_STAGE_L2P, st);

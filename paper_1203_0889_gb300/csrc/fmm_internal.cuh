@@ -148,6 +148,7 @@ struct TreeDev {
     int64_t* p2p_start = nullptr;
     int32_t* p2p_src = nullptr;
     int32_t* m2l_tgt = nullptr;   // [nm2l] target of each list entry (class build only)
+    int4* p2p_rec = nullptr;      // [np2p] (first, count, particle offset within the target's sources, source)
     // tensor-core M2L (FMM_PREC_MIXED_TC): pairs grouped by translation class
     int4* tc_items = nullptr;     // [tc_nitems] (class, first pair, rows, -)
     void* tc_ops = nullptr;       // [nclass][hi|lo][Kp x Kp] bf16 operators
@@ -162,6 +163,15 @@ struct TreeDev {
     void* L = nullptr;
     void* xq = nullptr;           // sorted (x, y, z, q): double4_32a or float4
     double* near = nullptr;       // [n*4] sorted near-field (phi, gx, gy, gz)
+    void* shift_ops = nullptr;    // [2][8][K2][K2] dense M2M / L2L operators per octant
+    // persistent task queue (queue.cu)
+    int64_t* tr_start = nullptr;  // transposed M2L list: source -> targets (CSR)
+    int32_t* tr_tgt = nullptr;
+    int32_t* q_cnt_init = nullptr;  // [4][ncell] initial dependency counters
+    int32_t* q_cnt = nullptr;
+    int32_t* q_init = nullptr;    // initial high-priority queue
+    int32_t* q_work = nullptr;
+    char* q_ctr = nullptr;        // queue heads / tails / done
 };
 
 }  // namespace fmm
@@ -183,6 +193,7 @@ struct fmm_tree {
     int nsys = 1;
     int num_sms = 148;
     int64_t tc_nclass = 0, tc_nitems = 0, tc_npairs = 0, tc_nrem = 0;
+    int64_t q_n_hi = 0, q_n0 = 0, q_n_tasks = 0;
     fmm::TreeDev d;
 };
 
@@ -216,6 +227,10 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st);
 int build_m2l_classes(fmm_tree* t, cudaStream_t st);
 int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st);
 int tc_kpad(int p);
+bool queue_supported(const fmm_tree* t);
+int build_queue(fmm_tree* t, cudaStream_t st);
+template <typename T, typename TP, typename O>
+int evaluate_queue(fmm_tree* t, const double4_32a* xq64, const void* xqp, O* phi, O* force, cudaStream_t st);
 bool tc_supported(int p);
 void free_tree_device(fmm_tree* t);
 template <typename T>

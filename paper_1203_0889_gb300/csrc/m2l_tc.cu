@@ -1,6 +1,6 @@
 // m2l_tc.cu -- M2L on the tensor cores (tcgen05), grouped by translation class.
 //
-// Every M2L pair (t, s) whose cells are at most two levels apart belongs to a
+// Every M2L pair (t, s) whose cells are at most ten levels apart belongs to a
 // translation class (dl = level_t - level_s, V = (2c_t - 2c_s) / min(side_t, side_s)),
 // an integer vector.  With per-level scaled expansions the translation is one
 // real matrix per class:
@@ -15,7 +15,7 @@
 // accumulated in FP32 in tensor memory as A_hi T_hi + A_hi T_lo + A_lo T_hi
 // (about 16 significant bits per product).  Each result row is added into the
 // target's local expansion with 16-byte vector atomics; pairs of rarer classes
-// (level gap above two) go through the CUDA-core kernel first, which also
+// (level gap above ten) go through the CUDA-core kernel first, which also
 // initialises every local expansion.
 #include <cub/cub.cuh>
 #include <cuda_bf16.h>
@@ -29,7 +29,7 @@ namespace fmm {
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-constexpr int TC_MAX_DL = 2;
+constexpr int TC_MAX_DL = 10;
 constexpr int TC_ROWS = 128;                 // MMA M: pairs per work item
 constexpr uint64_t NOT_TC = ~0ull;
 
@@ -98,9 +98,13 @@ __global__ void k_csr_from_targets(const int32_t* tgt, int64_t np, int ncell, in
 // rows = output coefficients (k, l, re|im), columns = input (n, m, re|im).
 __global__ void k_class_operators(int p, int Kp, const uint64_t* __restrict__ ukeys,
                                   __nv_bfloat16* __restrict__ ops) {
+    // harmonics in FP64 (one column per thread), entries assembled in FP32
+    // (each entry is rounded to FP32 and split to bf16 anyway)
     extern __shared__ unsigned char smraw[];
     cplx<double>* I = reinterpret_cast<cplx<double>*>(smraw);
-    int8_t* tk = reinterpret_cast<int8_t*>(I + ntri(2 * p));   // tri index -> (n, m)
+    cplx<float>* If = reinterpret_cast<cplx<float>*>(I + ntri(2 * p));
+    float* rpow = reinterpret_cast<float*>(If + ntri(2 * p));   // (-1)^k-free rho^n, n <= p
+    int8_t* tk = reinterpret_cast<int8_t*>(rpow + 32);            // tri index -> (n, m)
     int8_t* tm = tk + 256;
     const int c = blockIdx.x;
     const uint64_t key = ukeys[c];
@@ -113,33 +117,35 @@ __global__ void k_class_operators(int p, int Kp, const uint64_t* __restrict__ uk
     for (int m = threadIdx.x; m <= 2 * p; m += blockDim.x) irregular_column<double>(2 * p, m, dx, dy, dz, I);
     for (int n = 0; n <= p; n++)
         for (int m = threadIdx.x; m <= n; m += blockDim.x) { tk[tri(n, m)] = (int8_t)n; tm[tri(n, m)] = (int8_t)m; }
+    if (threadIdx.x <= p) rpow[threadIdx.x] = (float)pow(rho, (double)threadIdx.x);
+    __syncthreads();
+    for (int e = threadIdx.x; e < ntri(2 * p); e += blockDim.x) If[e] = cmk<float>((float)I[e].re, (float)I[e].im);
     __syncthreads();
     const int K2 = 2 * ntri(p);
     __nv_bfloat16* hi = ops + (size_t)c * 2 * Kp * Kp;
     __nv_bfloat16* lo = hi + (size_t)Kp * Kp;
     for (int e = threadIdx.x; e < Kp * Kp; e += blockDim.x) {
         int o = e / Kp, i = e % Kp;
-        double v = 0.0;
+        float v = 0.f;
         if (o < K2 && i < K2) {
             int k = tk[o >> 1], l = tm[o >> 1], pa = o & 1;
             int n = tk[i >> 1], m = tm[i >> 1], pb = i & 1;
             int j = n + k;
-            double s = (k & 1) ? -1.0 : 1.0;
-            for (int q = 0; q < n; q++) s *= rho;
-            const cplx<double>* Ij = I + tri(j, 0);
+            float s = (k & 1) ? -rpow[n] : rpow[n];
+            const cplx<float>* Ij = If + tri(j, 0);
             if (m == 0) {
-                cplx<double> x = Ij[l];
-                v = pb ? 0.0 : (pa ? -s * x.im : s * x.re);
+                cplx<float> x = Ij[l];
+                v = pb ? 0.f : (pa ? -s * x.im : s * x.re);
             } else {
-                cplx<double> xa = Ij[m + l];
-                double Ar = xa.re, Ai = -xa.im, Br, Bi;
+                cplx<float> xa = Ij[m + l];
+                float Ar = xa.re, Ai = -xa.im, Br, Bi;
                 if (l >= m) {
-                    cplx<double> xb = Ij[l - m];
-                    double sg = (m & 1) ? -1.0 : 1.0;
+                    cplx<float> xb = Ij[l - m];
+                    float sg = (m & 1) ? -1.f : 1.f;
                     Br = sg * xb.re; Bi = -sg * xb.im;
                 } else {
-                    cplx<double> xb = Ij[m - l];
-                    double sg = (l & 1) ? -1.0 : 1.0;
+                    cplx<float> xb = Ij[m - l];
+                    float sg = (l & 1) ? -1.f : 1.f;
                     Br = sg * xb.re; Bi = sg * xb.im;
                 }
                 if (!pa && !pb) v = s * (Ar + Br);
@@ -148,7 +154,7 @@ __global__ void k_class_operators(int p, int Kp, const uint64_t* __restrict__ uk
                 else v = s * (Ar - Br);
             }
         }
-        float f = (float)v;
+        float f = v;
         __nv_bfloat16 h = __float2bfloat16_rn(f);
         __nv_bfloat16 r = __float2bfloat16_rn(f - __bfloat162float(h));
         uint32_t off = tc::core_offset(o, i, Kp) >> 1;
@@ -230,7 +236,7 @@ int build_m2l_classes(fmm_tree* t, cudaStream_t st) {
         __nv_bfloat16* ops = nullptr;
         if ((rc = dev_alloc(&ops, ob, t, st))) return rc;
         d.tc_ops = ops;
-        size_t smem = ntri(2 * p) * sizeof(cplx<double>) + 512;
+        size_t smem = ntri(2 * p) * (sizeof(cplx<double>) + sizeof(cplx<float>)) + 32 * 4 + 512;
         k_class_operators<<<nclass, 256, smem, st>>>(p, Kp, ukeys, ops);
         count_launch(t);
     }

@@ -1,0 +1,400 @@
+// stages.cuh -- the FMM stages (paper Section 2.1) as device functions, shared
+// by the stage-by-stage kernels (evaluate.cu) and the persistent task-queue
+// kernel (queue.cu).
+//
+// Expansions are per-level scaled (see fmm_internal.cuh):
+//   P2M  Mt_n^m = sum_j q_j R_n^m((x_j - c)/h)
+//   M2M  Mt(P) = sum_children S_o Mt(C)         (dense real operator per octant o)
+//   M2L  Lt_k^l(t) += (-1)^k sum_{n,m} rho^n Mt_n^m(s) conj(I_{n+k}^{m+l}(D/h_t)), rho = h_s/h_t, D = c_t - c_s
+//   L2L  Lt(C) += S'_o Lt(P)                      (dense real operator per octant o)
+//   L2P  phi = (1/h) sum Lt_k^l R_k^l(u), grad phi = (1/h^2) sum Lt grad R(u), u = (x - c)/h
+//   P2P  phi_i += q_j / r_ij,  grad phi_i -= q_j (x_i - x_j) / r_ij^3  (r_ij > 0)
+// Interaction is non-mutual (Section 4): each function writes only its target.
+//
+// Load policy: the persistent kernel reads expansions that other blocks wrote
+// during the same launch, so it reads them through L2 (COH = true, __ldcg);
+// the staged kernels use the ordinary cached path.
+#pragma once
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+template <bool COH, typename X>
+__device__ __forceinline__ X ldx(const X* p) {
+    if (COH) return __ldcg(p);
+    return *p;
+}
+template <bool COH, typename T>
+__device__ __forceinline__ cplx<T> ldc(const cplx<T>* p) {
+    if (COH) {
+        const T* f = reinterpret_cast<const T*>(p);
+        return cmk<T>(__ldcg(f), __ldcg(f + 1));
+    }
+    return *p;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------- P2M
+// One warp, one leaf c; acc: the warp's shared scratch of ntri(p) entries.
+template <typename T>
+__device__ void p2m_leaf(int p, int c, int lane, const int32_t* __restrict__ first, const int32_t* __restrict__ count,
+                         const double4_32a* __restrict__ centre, const double4_32a* __restrict__ xq,
+                         cplx<T>* __restrict__ M, cplx<T>* acc) {
+    const int K = ntri(p), KS = kstride(p);
+    for (int j = lane; j < K; j += 32) acc[j] = cmk<T>(0, 0);
+    __syncwarp();
+    const double4_32a cc = centre[c];
+    const double invh = 1.0 / cc.w;
+    const int f = first[c], cnt = count[c];
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        T ux = 0, uy = 0, uz = 0, q = 0;
+        if (i < cnt) {
+            const double4_32a a = xq[f + i];
+            ux = (T)((a.x - cc.x) * invh); uy = (T)((a.y - cc.y) * invh); uz = (T)((a.z - cc.z) * invh);
+            q = (T)a.w;
+        }
+        const T r2 = ux * ux + uy * uy + uz * uz;
+        cplx<T> rmm = cmk<T>(q, 0);
+        for (int m = 0; m <= p; m++) {
+            if (m > 0) rmm = cscale(cmul(rmm, cmk<T>(ux, uy)), T(1) / T(2 * m));
+            cplx<T> a = rmm, b = cscale(rmm, uz);
+            for (int n = m; n <= p; n++) {
+                cplx<T> v;
+                if (n == m) v = a;
+                else if (n == m + 1) v = b;
+                else {
+                    const T inv = T(1) / T((n + m) * (n - m));
+                    v = cmk<T>((T(2 * n - 1) * uz * b.re - r2 * a.re) * inv, (T(2 * n - 1) * uz * b.im - r2 * a.im) * inv);
+                    a = b; b = v;
+                }
+                const T sr = warp_sum(v.re), si = warp_sum(v.im);
+                if (lane == 0) { acc[tri(n, m)].re += sr; acc[tri(n, m)].im += si; }
+            }
+        }
+    }
+    __syncwarp();
+    for (int j = lane; j < K; j += 32) M[(int64_t)c * KS + j] = acc[j];
+}
+
+// ---------------------------------------------------------------- M2M / L2L
+// One warp, destination cell c.  kind 0 (M2M): inputs are c's children, the
+// result is stored in E[c]; kind 1 (L2L): input is c's parent, the result is
+// added to E[c].  ops[kind][octant] is stored input-major (row = input).
+template <typename T, int RQ, bool COH>
+__device__ void shift_cell(int p, int c, int kind, int lane, const int32_t* __restrict__ child_first,
+                           const int32_t* __restrict__ child_count, const int32_t* __restrict__ parent,
+                           const uint64_t* __restrict__ ckey, const T* __restrict__ ops, cplx<T>* E, T* xin) {
+    const int K2 = 2 * ntri(p), ld = 2 * kstride(p);
+    T* Ef = reinterpret_cast<T*>(E);
+    T acc[RQ];
+#pragma unroll
+    for (int q = 0; q < RQ; q++) acc[q] = T(0);
+    int nin = 1, src0 = 0;
+    if (kind == 0) {
+        nin = child_count[c];
+        src0 = child_first[c];
+        if (nin == 0) return;
+    } else {
+        src0 = parent[c];
+#pragma unroll
+        for (int q = 0; q < RQ; q++) {
+            const int j = lane + 32 * q;
+            if (j < K2) acc[q] = ldx<COH>(Ef + (size_t)c * ld + j);
+        }
+    }
+    for (int k = 0; k < nin; k++) {
+        const int s = src0 + k;
+        const int oct = (int)(ckey[kind == 0 ? s : c] & 7);
+        const T* op = ops + (size_t)(kind * 8 + oct) * K2 * K2;
+        __syncwarp();
+        for (int j = lane; j < K2; j += 32) xin[j] = ldx<COH>(Ef + (size_t)s * ld + j);
+        __syncwarp();
+        // eight operator rows in flight per step (the top levels have few cells)
+        for (int i0 = 0; i0 < K2; i0 += 8) {
+            T w[8][RQ];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const T* row = op + (size_t)min(i0 + u, K2 - 1) * K2;
+#pragma unroll
+                for (int q = 0; q < RQ; q++) {
+                    const int j = lane + 32 * q;
+                    w[u][q] = j < K2 ? __ldg(row + j) : T(0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const T x = (i0 + u < K2) ? xin[i0 + u] : T(0);
+#pragma unroll
+                for (int q = 0; q < RQ; q++) acc[q] = fma(w[u][q], x, acc[q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RQ; q++) {
+        const int j = lane + 32 * q;
+        if (j < K2) Ef[(size_t)c * ld + j] = acc[q];
+    }
+}
+
+// ---------------------------------------------------------------- M2L
+// One source slot (a half-warp) accumulates, into acc[r], the outputs
+// j = hl + 16 r of target t over the sources e = s0 + slot, s0 + slot + nslot, ...
+// Ms / Is: the slot's shared scratch (ntri(p) and ntri(2p) entries).
+// The caller combines the slots and applies the (-1)^k sign.
+template <typename T, int RMAX, bool COH>
+__device__ void m2l_slot(int p, int t, int slot, int nslot, int hl, const int64_t* __restrict__ start,
+                         const int32_t* __restrict__ src, const double4_32a* __restrict__ centre,
+                         const cplx<T>* __restrict__ M, cplx<T>* Ms, cplx<T>* Is, const int* kk, const int* ll,
+                         cplx<T>* acc) {
+    const int K = ntri(p), KS = kstride(p);
+    const int64_t s0 = start[t], s1 = start[t + 1];
+    const double4_32a ct = centre[t];
+    const double invht = 1.0 / ct.w;
+    // every slot of the warp runs the same number of rounds (warp-synchronous scratch)
+    const int64_t rounds = (s1 - s0 + nslot - 1) / nslot;
+    for (int64_t rr = 0; rr < rounds; rr++) {
+        const int64_t my = s0 + rr * nslot + slot;
+        const bool valid = my < s1;
+        if (valid) {
+            const int s = src[my];
+            const double4_32a cs = centre[s];
+            const T rho = (T)(cs.w * invht);
+            for (int j = hl; j < K; j += 16) {
+                int n = 0;
+                while (tri(n + 1, 0) <= j) n++;
+                T sc = T(1);
+                for (int i = 0; i < n; i++) sc *= rho;
+                Ms[j] = cscale(ldc<COH>(M + (int64_t)s * KS + j), sc);
+            }
+            const T dx = (T)((ct.x - cs.x) * invht), dy = (T)((ct.y - cs.y) * invht), dz = (T)((ct.z - cs.z) * invht);
+            for (int m = hl; m <= 2 * p; m += 16) irregular_column<T>(2 * p, m, dx, dy, dz, Is);
+        }
+        __syncwarp();
+        if (valid) {
+#pragma unroll
+            for (int r = 0; r < RMAX; r++) {
+                if (hl + 16 * r >= K) break;
+                const int k = kk[r], l = ll[r];
+                cplx<T> a = acc[r];
+                for (int n = 0; n <= p; n++) {
+                    const cplx<T>* Ij = Is + tri(n + k, 0);
+                    const cplx<T>* Mn = Ms + tri(n, 0);
+                    {   // m = 0: Mt_n^0 is real
+                        const T mr = Mn[0].re;
+                        const cplx<T> x = Ij[l];
+                        a.re += mr * x.re;
+                        a.im -= mr * x.im;
+                    }
+                    for (int m = 1; m <= n; m++) {
+                        const cplx<T> mv = Mn[m];
+                        cfma_cj(a, mv, Ij[m + l]);  // M conj(I^{m+l})
+                        // order -m: (-1)^m conj(M) conj(I^{l-m}), I^{l-m} by symmetry when l < m
+                        const bool ge = l >= m;
+                        const cplx<T> x = Ij[ge ? l - m : m - l];
+                        const T sgn = ((ge ? m : l) & 1) ? T(-1) : T(1);
+                        const T xi = ge ? -x.im : x.im;
+                        a.re += sgn * (mv.re * x.re + mv.im * xi);
+                        a.im += sgn * (mv.re * xi - mv.im * x.re);
+                    }
+                }
+                acc[r] = a;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int RMAX>
+__device__ __forceinline__ void m2l_output_index(int p, int hl, int* kk, int* ll) {
+    const int K = ntri(p);
+#pragma unroll
+    for (int r = 0; r < RMAX; r++) {
+        const int j = hl + 16 * r;
+        int n = 0;
+        if (j < K) { while (tri(n + 1, 0) <= j) n++; }
+        kk[r] = n;
+        ll[r] = j < K ? j - tri(n, 0) : 0;
+    }
+}
+
+// ---------------------------------------------------------------- P2P
+template <typename T> struct Vec4;
+template <> struct Vec4<double> { typedef double4_32a type; };
+template <> struct Vec4<float> { typedef float4 type; };
+
+// FP32 records are relative to their own leaf centre; a source is shifted by
+// c_s - c_t when staged.  The offset comes from the exact integer centres
+// times side/2^22 in FP32 (no FP64 instruction per source: the FP64 pipe is
+// narrow on this GPU).
+template <typename T> struct Offset3 { T x, y, z; };
+__device__ __forceinline__ double4_32a shift_src(double4_32a v, Offset3<double>) { return v; }
+__device__ __forceinline__ float4 shift_src(float4 v, Offset3<float> o) {
+    return make_float4(v.x + o.x, v.y + o.y, v.z + o.z, v.w);
+}
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+
+constexpr int P2P_THREADS = 128;
+constexpr int P2P_BUF = 1024;
+
+template <typename T>
+__device__ __forceinline__ void p2p_pair(const typename Vec4<T>::type& me, const typename Vec4<T>::type& s, T& phi,
+                                         T& gx, T& gy, T& gz) {
+    const T dx = me.x - s.x, dy = me.y - s.y, dz = me.z - s.z;
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    const T rinv = r2 > T(0) ? rsqrt_t(r2) : T(0);
+    const T qr = s.w * rinv;
+    phi += qr;
+    const T qr3 = qr * rinv * rinv;
+    gx -= qr3 * dx; gy -= qr3 * dy; gz -= qr3 * dz;
+}
+
+// One block of P2P_THREADS threads, target leaf c.  The target's sources are
+// one concatenated particle stream (each P2P record gives a source leaf's
+// offset in it), staged P2P_BUF at a time, the four warps copying different
+// source leaves.  Thread t works on target (t mod nt) over the staged sources
+// j = (t / nt) (mod G), G = 128 / nt streams, so small leaves fill the block.
+template <typename T>
+__device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t* __restrict__ count,
+                         const int64_t* __restrict__ start, const int4* __restrict__ rec,
+                         const typename Vec4<T>::type* __restrict__ xq, const int4* __restrict__ icentre, float u2f,
+                         double* __restrict__ near, typename Vec4<T>::type* buf, T (*part)[4]) {
+    typedef typename Vec4<T>::type V;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tf = first[c], nt = count[c];
+    const int64_t s0 = start[c], s1 = start[c + 1];
+    int total = 0;
+    if (s1 > s0) { const int4 r = rec[s1 - 1]; total = r.z + r.y; }
+    const int4 ict = icentre[c];
+    for (int tb = 0; tb < nt; tb += P2P_THREADS) {
+        const int ntc = min(P2P_THREADS, nt - tb);
+        const int G = P2P_THREADS / ntc;
+        const int ti = threadIdx.x % ntc, sub = threadIdx.x / ntc;
+        const bool active = sub < G;
+        const V me = xq[tf + tb + ti];
+        T phi = 0, gx = 0, gy = 0, gz = 0;
+        int64_t e_lo = s0;
+        for (int base = 0; base < total; base += P2P_BUF) {
+            const int lim = min(P2P_BUF, total - base);
+            for (int64_t e = e_lo + warp; e < s1; e += P2P_THREADS / 32) {
+                const int4 r = rec[e];
+                if (r.z >= base + P2P_BUF) break;
+                const int k0 = max(0, base - r.z), k1 = min(r.y, base + P2P_BUF - r.z);
+                if (k1 <= k0) continue;
+                Offset3<T> o = {T(0), T(0), T(0)};
+                if (sizeof(T) == 4) {
+                    const int4 ics = icentre[r.w];
+                    o.x = (T)((float)(ics.x - ict.x) * u2f);
+                    o.y = (T)((float)(ics.y - ict.y) * u2f);
+                    o.z = (T)((float)(ics.z - ict.z) * u2f);
+                }
+                for (int k = k0 + lane; k < k1; k += 32) buf[r.z + k - base] = shift_src(xq[r.x + k], o);
+            }
+            __syncthreads();
+            if (active) {
+                int j = sub;
+                for (; j + 3 * G < lim; j += 4 * G) {
+                    const V a = buf[j], b = buf[j + G], cc = buf[j + 2 * G], d = buf[j + 3 * G];
+                    p2p_pair<T>(me, a, phi, gx, gy, gz);
+                    p2p_pair<T>(me, b, phi, gx, gy, gz);
+                    p2p_pair<T>(me, cc, phi, gx, gy, gz);
+                    p2p_pair<T>(me, d, phi, gx, gy, gz);
+                }
+                for (; j < lim; j += G) p2p_pair<T>(me, buf[j], phi, gx, gy, gz);
+            }
+            __syncthreads();
+            while (e_lo < s1) {
+                const int4 r = rec[e_lo];
+                if (r.z + r.y > base + P2P_BUF) break;
+                e_lo++;
+            }
+        }
+        part[threadIdx.x][0] = phi; part[threadIdx.x][1] = gx; part[threadIdx.x][2] = gy; part[threadIdx.x][3] = gz;
+        __syncthreads();
+        if (threadIdx.x < ntc) {
+            T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+            for (int q = 0; q < G; q++) {
+                const int k = q * ntc + threadIdx.x;
+                a0 += part[k][0]; a1 += part[k][1]; a2 += part[k][2]; a3 += part[k][3];
+            }
+            const int64_t i = tf + tb + threadIdx.x;
+            near[4 * i] = (double)a0; near[4 * i + 1] = (double)a1; near[4 * i + 2] = (double)a2;
+            near[4 * i + 3] = (double)a3;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- L2P
+// Particles tid, tid + nthr, ... of leaf c, with Lt(c) already in Ls; adds the
+// near field and writes the outputs in input order.
+template <typename T, typename O, bool COH>
+__device__ void l2p_particles(int p, int c, int tid, int nthr, const cplx<T>* Ls, const int32_t* __restrict__ first,
+                              const int32_t* __restrict__ count, const double4_32a* __restrict__ centre,
+                              const double4_32a* __restrict__ xq, const int32_t* __restrict__ perm,
+                              const double* __restrict__ near, O* __restrict__ phi_out, O* __restrict__ force_out,
+                              int field) {
+    const double4_32a cc = centre[c];
+    const double invh = 1.0 / cc.w;
+    const int f = first[c], cnt = count[c];
+    for (int i = tid; i < cnt; i += nthr) {
+        const double4_32a a = xq[f + i];
+        const T ux = (T)((a.x - cc.x) * invh), uy = (T)((a.y - cc.y) * invh), uz = (T)((a.z - cc.z) * invh);
+        const T r2 = ux * ux + uy * uy + uz * uz;
+        T fp = 0, gx = 0, gy = 0, gz = 0;
+        cplx<T> rmm = cmk<T>(1, 0);
+        for (int m = 0; m <= p; m++) {
+            if (m > 0) rmm = cscale(cmul(rmm, cmk<T>(ux, uy)), T(1) / T(2 * m));
+            cplx<T> a0 = rmm, b0 = cscale(rmm, uz);
+            const T w = m == 0 ? T(1) : T(2);
+            for (int n = m; n <= p; n++) {
+                cplx<T> S;
+                if (n == m) S = a0;
+                else if (n == m + 1) S = b0;
+                else {
+                    const T inv = T(1) / T((n + m) * (n - m));
+                    S = cmk<T>((T(2 * n - 1) * uz * b0.re - r2 * a0.re) * inv, (T(2 * n - 1) * uz * b0.im - r2 * a0.im) * inv);
+                    a0 = b0; b0 = S;
+                }
+                const cplx<T> Lnm = Ls[tri(n, m)];
+                fp += w * (Lnm.re * S.re - Lnm.im * S.im);
+                if (n + 1 <= p) {
+                    const cplx<T>* L1 = Ls + tri(n + 1, 0);
+                    const cplx<T> lz = L1[m];
+                    gz += w * (lz.re * S.re - lz.im * S.im);
+                    if (m == 0) {
+                        gx += L1[1].re * S.re;
+                        gy -= L1[1].im * S.re;
+                    } else {
+                        const cplx<T> up = L1[m + 1], dn = L1[m - 1];
+                        const cplx<T> A = csub(up, dn), B = cadd(up, dn);
+                        gx += A.re * S.re - A.im * S.im;
+                        gy += -(B.im * S.re + B.re * S.im);  // Re(i B S)
+                    }
+                }
+            }
+        }
+        const int64_t gi = f + i;
+        const double ph = (double)fp * invh + ldx<COH>(near + 4 * gi);
+        const double ih2 = invh * invh;
+        const double ex = -((double)gx * ih2 + ldx<COH>(near + 4 * gi + 1));
+        const double ey = -((double)gy * ih2 + ldx<COH>(near + 4 * gi + 2));
+        const double ez = -((double)gz * ih2 + ldx<COH>(near + 4 * gi + 3));
+        const int64_t o = perm[gi];
+        if (phi_out) phi_out[o] = (O)ph;
+        if (force_out) {
+            const double s = field ? 1.0 : a.w;
+            force_out[3 * o] = (O)(s * ex);
+            force_out[3 * o + 1] = (O)(s * ey);
+            force_out[3 * o + 2] = (O)(s * ez);
+        }
+    }
+}
+
+}  // namespace fmm

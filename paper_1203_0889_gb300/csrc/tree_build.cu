@@ -181,60 +181,62 @@ __global__ void k_gather_pos(const T* __restrict__ pos, const int32_t* __restric
 // ---------------------------------------------------------------------------
 
 // Children of cell c are the distinct values of key >> shift within its
-// particle range; found by one binary search per octant.
-__device__ __forceinline__ int child_bounds(const uint64_t* keys, int f, int e, uint64_t base, int shift,
-                                            int* bnd) {
-    int lo = f, nc = 0;
-    bnd[0] = f;
-    for (int o = 0; o < 8; o++) {
-        int a = lo, b = e;
-        uint64_t lim = base + (uint64_t)o;
-        while (a < b) {
-            int mid = (a + b) >> 1;
-            if ((keys[mid] >> shift) <= lim) a = mid + 1; else b = mid;
-        }
-        bnd[o + 1] = a;
-        if (a > lo) nc++;
-        lo = a;
+// particle range.  Eight lanes serve one cell: lane o finds the end of octant
+// o (first particle whose prefix exceeds base + o) by binary search, so the
+// eight searches run side by side; octant o spans [end(o-1), end(o)).
+__device__ __forceinline__ int octant_end(const uint64_t* keys, int f, int e, uint64_t lim, int shift) {
+    int a = f, b = e;
+    while (a < b) {
+        int mid = (a + b) >> 1;
+        if ((keys[mid] >> shift) <= lim) a = mid + 1; else b = mid;
     }
-    return nc;
+    return a;
 }
 
 __global__ void k_count_children(int lb, int le, int level, int leaf_size, const int32_t* first,
                                  const int32_t* count, const uint64_t* ckey, const uint64_t* keys,
                                  int32_t* nchild) {
-    int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= le) return;
-    int cnt = count[c];
-    if (!(cnt > leaf_size && level < FMM_MAX_LEVEL)) { nchild[c - lb] = 0; return; }
-    int bnd[9];
-    nchild[c - lb] = child_bounds(keys, first[c], first[c] + cnt, ckey[c] << 3,
-                                  3 * (FMM_MAX_LEVEL - (level + 1)), bnd);
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = lb + (g >> 3), o = g & 7;
+    bool valid = c < le;
+    int cnt = valid ? count[c] : 0;
+    bool split = valid && cnt > leaf_size && level < FMM_MAX_LEVEL;
+    int f = valid ? first[c] : 0;
+    int end = split ? octant_end(keys, f, f + cnt, (ckey[c] << 3) + (uint64_t)o, 3 * (FMM_MAX_LEVEL - (level + 1))) : 0;
+    int beg = __shfl_up_sync(0xffffffffu, end, 1, 8);
+    if (o == 0) beg = f;
+    unsigned nonempty = __ballot_sync(0xffffffffu, split && end > beg);
+    if (valid && o == 0) nchild[c - lb] = __popc((nonempty >> (threadIdx.x & 24)) & 0xffu);
 }
 
 __global__ void k_emit_children(int lb, int le, int level, int leaf_size, const uint64_t* keys,
                                 const int32_t* nchild, const int32_t* coff, int next_base,
                                 int32_t* lev, uint64_t* ckey, int32_t* first, int32_t* count,
                                 int32_t* parent, int32_t* child_first, int32_t* child_count) {
-    int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= le) return;
-    int nc = nchild[c - lb];
-    if (nc == 0) { child_first[c] = 0; child_count[c] = 0; return; }
-    int bnd[9];
-    uint64_t base = ckey[c] << 3;
-    child_bounds(keys, first[c], first[c] + count[c], base, 3 * (FMM_MAX_LEVEL - (level + 1)), bnd);
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = lb + (g >> 3), o = g & 7;
+    bool valid = c < le;
+    int nc = valid ? nchild[c - lb] : 0;
+    int f = valid ? first[c] : 0;
+    uint64_t base = valid ? (ckey[c] << 3) : 0;
+    int end = nc ? octant_end(keys, f, f + count[c], base + (uint64_t)o, 3 * (FMM_MAX_LEVEL - (level + 1))) : 0;
+    int beg = __shfl_up_sync(0xffffffffu, end, 1, 8);
+    if (o == 0) beg = f;
+    bool ne = nc && end > beg;
+    unsigned m8 = (__ballot_sync(0xffffffffu, ne) >> (threadIdx.x & 24)) & 0xffu;
+    if (!valid) return;
     int w = next_base + coff[c - lb];
-    child_first[c] = w;
-    child_count[c] = nc;
-    for (int o = 0; o < 8; o++) {
-        if (bnd[o + 1] == bnd[o]) continue;
-        lev[w] = level + 1;
-        ckey[w] = base + (uint64_t)o;
-        first[w] = bnd[o];
-        count[w] = bnd[o + 1] - bnd[o];
-        parent[w] = c;
-        w++;
+    if (o == 0) {
+        child_first[c] = nc ? w : 0;
+        child_count[c] = nc;
     }
+    if (!ne) return;
+    w += __popc(m8 & ((1u << o) - 1u));
+    lev[w] = level + 1;
+    ckey[w] = base + (uint64_t)o;
+    first[w] = beg;
+    count[w] = end - beg;
+    parent[w] = c;
 }
 
 __global__ void k_centres(int ncell, const int32_t* lev, const uint64_t* ckey, const Geometry* g,
@@ -350,6 +352,20 @@ __global__ void k_csr_start(const uint64_t* key, int64_t np, int ncell, int64_t*
         if (key[mid] < lim) a = mid + 1; else b = mid;
     }
     start[c] = a;
+}
+
+// P2P records: source range and where its particles start in the target's
+// concatenated source stream (exclusive prefix of counts within the target)
+__global__ void k_p2p_counts(int64_t np, const int32_t* src, const int32_t* count, int64_t* cnt) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < np) cnt[e] = count[src[e]];
+}
+__global__ void k_p2p_records(int64_t np, const int32_t* src, const int32_t* tgt, const int64_t* start,
+                              const int32_t* first, const int32_t* count, const int64_t* gcum, int4* rec) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= np) return;
+    int s = src[e];
+    rec[e] = make_int4(first[s], count[s], (int)(gcum[e] - gcum[start[tgt[e]]]), s);
 }
 
 __global__ void k_leaf_flags(int ncell, const int32_t* child_count, char* flag, int32_t* iota) {
@@ -498,7 +514,7 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         int width = le - lb;
         if ((rc = grow(nch, c_nch, width, 0, st))) return rc;
         if ((rc = grow(coff, c_coff, width, 0, st))) return rc;
-        k_count_children<<<nblk(width, 128), 128, 0, st>>>(lb, le, level, t->prm.leaf_size, first, count,
+        k_count_children<<<nblk((int64_t)width * 8, 128), 128, 0, st>>>(lb, le, level, t->prm.leaf_size, first, count,
                                                              ckey, d.keys, nch);
         count_launch(t);
         size_t sb = 0;
@@ -515,7 +531,7 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         if ((size_t)le + total > c_lev) {
             if ((rc = grow_all((size_t)le + total, (size_t)le))) return rc;
         }
-        k_emit_children<<<nblk(width, 128), 128, 0, st>>>(lb, le, level, t->prm.leaf_size, d.keys, nch, coff, le,
+        k_emit_children<<<nblk((int64_t)width * 8, 128), 128, 0, st>>>(lb, le, level, t->prm.leaf_size, d.keys, nch, coff, le,
                                                             lev, ckey, first, count, par, cf, cc);
         count_launch(t);
         t->level_start[level + 1] = le;
@@ -618,12 +634,32 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     t->np2p = npp;
     const bool want_classes = t->prm.precision == FMM_PREC_MIXED_TC && tc_supported(t->prm.p);
     if ((rc = finish_list(t, m2l, nm, &d.m2l_start, &d.m2l_src, want_classes ? &d.m2l_tgt : nullptr, st))) return rc;
-    if ((rc = finish_list(t, p2p, npp, &d.p2p_start, &d.p2p_src, nullptr, st))) return rc;
+    int32_t* p2p_tgt = nullptr;
+    if ((rc = finish_list(t, p2p, npp, &d.p2p_start, &d.p2p_src, &p2p_tgt, st))) return rc;
+    {
+        int64_t *cnt = nullptr, *gcum = nullptr;
+        if ((rc = dev_alloc(&cnt, (size_t)npp, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&gcum, (size_t)npp, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&d.p2p_rec, (size_t)npp, t, st))) return rc;
+        if (npp) {
+            k_p2p_counts<<<nblk(npp, 256), 256, 0, st>>>(npp, d.p2p_src, d.count, cnt);
+            size_t sb = 0;
+            cub::DeviceScan::ExclusiveSum(nullptr, sb, cnt, gcum, npp, st);
+            if ((rc = dev_alloc(&tmp, sb, nullptr, st))) return rc;
+            FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, cnt, gcum, npp, st));
+            dev_free(tmp, st);
+            k_p2p_records<<<nblk(npp, 256), 256, 0, st>>>(npp, d.p2p_src, p2p_tgt, d.p2p_start, d.first, d.count,
+                                                            gcum, d.p2p_rec);
+            count_launch(t, 3);
+        }
+        dev_free(cnt, st); dev_free(gcum, st); dev_free(p2p_tgt, st);
+    }
     dev_free(m2l, st); dev_free(p2p, st);
     if (want_classes) {
         if ((rc = build_m2l_classes(t, st))) return rc;
         dev_free(d.m2l_tgt, st);
     }
+    if (queue_supported(t) && (rc = build_queue(t, st))) return rc;
     stage_end(t, FMM_STAGE_LISTS, st);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
@@ -638,12 +674,16 @@ void free_tree_device(fmm_tree* t) {
     dev_free(d.centre, st); dev_free(d.icentre, st); dev_free(d.leaves, st); dev_free(d.pleaf, st);
     dev_free(d.m2l_start, st); dev_free(d.m2l_src, st); dev_free(d.p2p_start, st); dev_free(d.p2p_src, st);
     dev_free(d.geom, st); dev_free(d.status, st);
-    dev_free(d.m2l_tgt, st); dev_free(d.tc_items, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
+    dev_free(d.m2l_tgt, st); dev_free(d.p2p_rec, st); dev_free(d.tc_items, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
     dev_free(d.rem_start, st);
+    dev_free(d.tr_start, st); dev_free(d.tr_tgt, st); dev_free(d.q_cnt_init, st); dev_free(d.q_cnt, st);
+    dev_free(d.q_init, st); dev_free(d.q_work, st); dev_free(d.q_ctr, st);
     if (d.tc_ops) cudaFreeAsync(d.tc_ops, st);
     if (d.tc_msplit) cudaFreeAsync(d.tc_msplit, st);
     d.tc_ops = nullptr; d.tc_msplit = nullptr;
     dev_free(d.M, st); dev_free(d.L, st); dev_free(d.xq, st); dev_free(d.near, st);
+    if (d.shift_ops) cudaFreeAsync(d.shift_ops, st);
+    d.shift_ops = nullptr;
 }
 
 }  // namespace fmm
