@@ -136,6 +136,30 @@ int fmm_build_tree(const fmm_params* params, int64_t n, const void* pos, int pos
 int fmm_evaluate(fmm_tree* tree, const void* q, void* phi, void* force, int dtype, void* stream);
 
 /*
+ * Replace the positions of a built tree without rebuilding it: the cells, their
+ * centres and the interaction lists stay, and particle i stays in its cell.
+ * (Used to differentiate with the tree held fixed; for large moves rebuild.)
+ *   pos  device, n x 3 of pos_dtype.  Queued on `stream`.
+ */
+int fmm_tree_set_positions(fmm_tree* tree, const void* pos, int pos_dtype, void* stream);
+
+/*
+ * Gradient of L = sum_i w_i phi_i (phi from charges q on this tree).  The
+ * Laplace kernel is symmetric, so one more FMM pass with the weights as
+ * charges gives everything:
+ *   dq_j = sum_{i != j} w_i / r_ij = phi^(w)_j
+ *   dx_k = w_k grad phi^(q)(x_k) + q_k grad phi^(w)(x_k)
+ *   q, w      device, n of dtype.
+ *   field_q   device, n x 3: E^(q) = -grad phi^(q), the forward's `force` output
+ *             on a tree built with FMM_OUT_FIELD.
+ *   dq        device, n (may be NULL);  dx  device, n x 3 (may be NULL).
+ * The tree must have been built with FMM_OUT_FIELD (else FMM_ERR_STATE).
+ * Queued on `stream`; the first call allocates an n x 3 work array in the tree.
+ */
+int fmm_backward(fmm_tree* tree, const void* q, const void* w, const void* field_q, void* dq, void* dx,
+                 int dtype, void* stream);
+
+/*
  * Build one tree holding nsys independent systems (a batch).
  *   offsets  host, nsys + 1 ascending particle offsets into pos (offsets[0] = 0).
  *   pos      device, offsets[nsys] x 3 of pos_dtype.

@@ -92,6 +92,10 @@ def load():
             lib.fmm_stage_name.restype = C.c_char_p
             lib.fmm_kernel_launches.argtypes = [_P, C.c_int32]
             lib.fmm_kernel_launches.restype = C.c_int64
+            lib.fmm_tree_set_positions.argtypes = [_P, _P, C.c_int, _P]
+            lib.fmm_tree_set_positions.restype = C.c_int
+            lib.fmm_backward.argtypes = [_P, _P, _P, _P, _P, _P, C.c_int, _P]
+            lib.fmm_backward.restype = C.c_int
             lib.fmm_inject_dependency.argtypes = [_P, C.c_int32, C.c_int32, C.c_int32]
             lib.fmm_inject_dependency.restype = C.c_int
             lib.fmm_direct_noalloc.argtypes = [C.c_int64, _P, _P, _P, _P, C.c_int, C.c_int32, _P]
@@ -241,3 +245,67 @@ def evaluate(tree: Tree, q, **kw):
 
 def version() -> str:
     return load().fmm_version().decode()
+
+
+def _set_positions(self, pos, stream=None):
+    """Move the particles without rebuilding the tree (cells and lists stay)."""
+    torch = _torch()
+    if not (pos.is_cuda and pos.shape == (self.n, 3)):
+        raise ValueError("pos must be a CUDA tensor of shape (n, 3)")
+    pos = pos.contiguous()
+    with torch.cuda.device(pos.device):
+        _check(load().fmm_tree_set_positions(self._h, C.c_void_p(pos.data_ptr()), _dtype_code(pos),
+                                             _stream_ptr(stream)))
+
+
+def _backward(self, q, w, field_q, stream=None):
+    """(dL/dq, dL/dx) of L = sum w_i phi_i, from one adjoint FMM pass (tree built with OUT_FIELD)."""
+    torch = _torch()
+    q, w, field_q = q.contiguous(), w.contiguous(), field_q.contiguous()
+    dq = torch.empty_like(q)
+    dx = torch.empty((self.n, 3), dtype=q.dtype, device=q.device)
+    with torch.cuda.device(q.device):
+        _check(load().fmm_backward(self._h, C.c_void_p(q.data_ptr()), C.c_void_p(w.data_ptr()),
+                                   C.c_void_p(field_q.data_ptr()), C.c_void_p(dq.data_ptr()),
+                                   C.c_void_p(dx.data_ptr()), _dtype_code(q), _stream_ptr(stream)))
+    return dq, dx
+
+
+Tree.set_positions = _set_positions
+Tree.backward = _backward
+
+
+def _fmm_function():
+    import torch
+
+    class FMMFunction(torch.autograd.Function):
+        """phi = FMM(pos, q) as an autograd node.
+
+        ``tree`` must be built on ``pos`` with OUT_FIELD (the forward keeps the
+        field for the backward).  The backward runs one more FMM pass with the
+        upstream gradient as charges (the kernel is symmetric) and returns
+        dL/dpos and dL/dq; the tree is held fixed, so positions are treated as
+        moving inside their cells."""
+
+        @staticmethod
+        def forward(ctx, pos, q, tree):
+            if not (tree.params.flags & OUT_FIELD):
+                raise ValueError("FMMFunction needs a tree built with flags=OUT_FIELD")
+            phi, field = tree.evaluate(q)
+            ctx.tree = tree
+            ctx.save_for_backward(q, field)
+            return phi
+
+        @staticmethod
+        def backward(ctx, w):
+            q, field = ctx.saved_tensors
+            dq, dx = ctx.tree.backward(q, w.contiguous().to(q.dtype), field)
+            return dx, dq, None
+
+    return FMMFunction
+
+
+def __getattr__(name):
+    if name == "FMMFunction":
+        return _fmm_function()
+    raise AttributeError(name)

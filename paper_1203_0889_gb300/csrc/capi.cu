@@ -126,6 +126,35 @@ int fmm_evaluate(fmm_tree* tree, const void* q, void* phi, void* force, int dtyp
     return rc;
 }
 
+int fmm_tree_set_positions(fmm_tree* tree, const void* pos, int pos_dtype, void* stream) {
+    g_err[0] = 0;
+    if (!tree) { fmm_set_error("tree is NULL"); return FMM_ERR_ARG; }
+    if (tree->n > 0 && !pos) { fmm_set_error("pos is NULL"); return FMM_ERR_ARG; }
+    if (pos_dtype != FMM_F64 && pos_dtype != FMM_F32) { fmm_set_error("pos_dtype must be FMM_F64 or FMM_F32"); return FMM_ERR_ARG; }
+    return fmm::set_positions_impl(tree, pos, pos_dtype, (cudaStream_t)stream);
+}
+
+int fmm_backward(fmm_tree* tree, const void* q, const void* w, const void* field_q, void* dq, void* dx, int dtype,
+                 void* stream) {
+    g_err[0] = 0;
+    if (!tree) { fmm_set_error("tree is NULL"); return FMM_ERR_ARG; }
+    if (!(tree->prm.flags & FMM_OUT_FIELD)) { fmm_set_error("fmm_backward needs a tree built with FMM_OUT_FIELD"); return FMM_ERR_STATE; }
+    if (dtype != FMM_F64 && dtype != FMM_F32) { fmm_set_error("dtype must be FMM_F64 or FMM_F32"); return FMM_ERR_ARG; }
+    if (tree->n == 0) return FMM_OK;
+    if (!q || !w || (dx && !field_q)) { fmm_set_error("q, w (and field_q when dx is wanted) must not be NULL"); return FMM_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t esz = dtype == FMM_F64 ? 8 : 4;
+    if (!tree->d.grad_tmp) {
+        cudaError_t e = cudaMallocAsync(&tree->d.grad_tmp, (size_t)tree->n * 3 * 8, st);
+        if (e != cudaSuccess) { fmm_set_error("backward: %s", cudaGetErrorString(e)); return FMM_ERR_ALLOC; }
+        tree->device_bytes += (int64_t)tree->n * 3 * 8;
+    }
+    (void)esz;
+    int rc = fmm_evaluate(tree, w, dq, dx ? tree->d.grad_tmp : nullptr, dtype, stream);
+    if (rc) return rc;
+    return fmm::grad_combine(tree, q, w, field_q, tree->d.grad_tmp, dx, dtype, st);
+}
+
 int fmm_build_tree_batched(const fmm_params* params, int32_t nsys, const int64_t* offsets, const void* pos,
                            int pos_dtype, fmm_tree** out, void* stream) {
     (void)params; (void)nsys; (void)offsets; (void)pos; (void)pos_dtype; (void)stream;

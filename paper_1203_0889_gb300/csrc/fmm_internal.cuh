@@ -172,6 +172,7 @@ struct TreeDev {
     int32_t* q_init = nullptr;    // initial high-priority queue
     int32_t* q_work = nullptr;
     char* q_ctr = nullptr;        // queue heads / tails / done
+    void* grad_tmp = nullptr;     // [n*3] field of the adjoint pass (fmm_backward)
 };
 
 }  // namespace fmm
@@ -224,6 +225,9 @@ inline void count_launch(fmm_tree* t, int k = 1) {
 int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st);
 int evaluate_impl(fmm_tree* t, const void* q, void* phi, void* force, int dtype, cudaStream_t st);
 int alloc_eval_workspace(fmm_tree* t, cudaStream_t st);
+int set_positions_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st);
+int grad_combine(fmm_tree* t, const void* q, const void* w, const void* eq, const void* ew, void* dx, int dtype,
+                 cudaStream_t st);
 int build_m2l_classes(fmm_tree* t, cudaStream_t st);
 int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st);
 int tc_kpad(int p);

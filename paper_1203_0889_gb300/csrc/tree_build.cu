@@ -665,6 +665,37 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     return FMM_OK;
 }
 
+int set_positions_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st) {
+    if (t->n == 0) return FMM_OK;
+    if (pos_dtype == FMM_F64)
+        k_gather_pos<double><<<nblk(t->n, 256), 256, 0, st>>>((const double*)pos, t->d.perm, t->n, t->d.spos);
+    else
+        k_gather_pos<float><<<nblk(t->n, 256), 256, 0, st>>>((const float*)pos, t->d.perm, t->n, t->d.spos);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+template <typename T>
+__global__ void k_grad_combine(int64_t n, const T* __restrict__ q, const T* __restrict__ w, const T* __restrict__ eq,
+                               const T* __restrict__ ew, T* __restrict__ dx) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int d = 0; d < 3; d++) dx[3 * i + d] = -(w[i] * eq[3 * i + d] + q[i] * ew[3 * i + d]);
+}
+
+int grad_combine(fmm_tree* t, const void* q, const void* w, const void* eq, const void* ew, void* dx, int dtype,
+                 cudaStream_t st) {
+    if (t->n == 0 || !dx) return FMM_OK;
+    if (dtype == FMM_F64)
+        k_grad_combine<double><<<nblk(t->n, 256), 256, 0, st>>>(t->n, (const double*)q, (const double*)w,
+                                                                 (const double*)eq, (const double*)ew, (double*)dx);
+    else
+        k_grad_combine<float><<<nblk(t->n, 256), 256, 0, st>>>(t->n, (const float*)q, (const float*)w,
+                                                                (const float*)eq, (const float*)ew, (float*)dx);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
 void free_tree_device(fmm_tree* t) {
     TreeDev& d = t->d;
     cudaStream_t st = 0;
@@ -674,6 +705,8 @@ void free_tree_device(fmm_tree* t) {
     dev_free(d.centre, st); dev_free(d.icentre, st); dev_free(d.leaves, st); dev_free(d.pleaf, st);
     dev_free(d.m2l_start, st); dev_free(d.m2l_src, st); dev_free(d.p2p_start, st); dev_free(d.p2p_src, st);
     dev_free(d.geom, st); dev_free(d.status, st);
+    if (d.grad_tmp) cudaFreeAsync(d.grad_tmp, st);
+    d.grad_tmp = nullptr;
     dev_free(d.m2l_tgt, st); dev_free(d.p2p_rec, st); dev_free(d.tc_items, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
     dev_free(d.rem_start, st);
     dev_free(d.tr_start, st); dev_free(d.tr_tgt, st); dev_free(d.q_cnt_init, st); dev_free(d.q_cnt, st);

@@ -355,3 +355,60 @@ ALL_PINS = [
     pin_scaling_invariance, pin_fmm_equals_direct_without_far_field, pin_fmm_error_decays_with_p,
     pin_fmm_high_order_matches_direct, pin_fmm_net_force, pin_fmm_sampled_matches_full,
 ]
+
+
+# ---------------------------------------------------------------- gradients (O9)
+
+def pin_direct_gradient_formulas():
+    """For L = sum_i w_i phi_i: dL/dq_j = phi^(w)_j and
+    dL/dx_k = w_k grad phi^(q)(x_k) + q_k grad phi^(w)(x_k), against central
+    differences of L computed by the direct sum."""
+    rng = _rng(8)
+    n = 40
+    pos = rng.random((n, 3))
+    q = rng.normal(size=n)
+    w = rng.normal(size=n)
+
+    def loss(x, qq):
+        return float(np.dot(w, O.direct(x, qq)[0]))
+
+    phi_w, g_w = O.direct(pos, w)
+    _, g_q = O.direct(pos, q)
+    dq = phi_w
+    dx = w[:, None] * g_q + q[:, None] * g_w
+    h = 1e-6
+    for j in (0, 7, 39):
+        e = np.zeros(n); e[j] = h
+        fd = (loss(pos, q + e) - loss(pos, q - e)) / (2 * h)
+        assert abs(fd - dq[j]) <= 1e-7 * (1 + abs(dq[j]))
+        for d in range(3):
+            xp, xm = pos.copy(), pos.copy()
+            xp[j, d] += h; xm[j, d] -= h
+            fd = (loss(xp, q) - loss(xm, q)) / (2 * h)
+            assert abs(fd - dx[j, d]) <= 1e-6 * (1 + abs(dx[j, d]))
+
+
+def pin_fmm_gradient_fixed_tree():
+    """With the tree held fixed (cells and centres from the unperturbed
+    positions), the FMM loss is smooth in x; at high order its central
+    difference matches w grad phi^(q) + q grad phi^(w) from two FMM passes."""
+    wl = W.make_workload("gradient", n=1500)
+    pos, q, w = wl.pos, wl.q, wl.extra["w"]
+    T = O.build_tree(pos, 32, 0.5)
+    p = 16
+    phi_q, g_q = T.evaluate(p, q, nthreads=4)
+    phi_w, g_w = T.evaluate(p, w, nthreads=4)
+    dx = w[:, None] * g_q + q[:, None] * g_w
+
+    def loss(x):
+        T.pos = np.ascontiguousarray(x)
+        return float(np.dot(w, T.evaluate(p, q, nthreads=4)[0]))
+
+    h = 1e-6
+    for j in (3, 500, 1499):
+        for d in range(3):
+            xp, xm = pos.copy(), pos.copy()
+            xp[j, d] += h; xm[j, d] -= h
+            fd = (loss(xp) - loss(xm)) / (2 * h)
+            assert abs(fd - dx[j, d]) <= 1e-5 * np.abs(dx).max()
+    T.pos = pos

@@ -13,7 +13,7 @@ from tests import oracle_pins as P
     P.pin_m2l_single_charge, P.pin_m2l_order_zero, P.pin_l2p_gradient_fd,
     P.pin_scaling_invariance, P.pin_fmm_equals_direct_without_far_field,
     P.pin_fmm_error_decays_with_p, P.pin_fmm_high_order_matches_direct, P.pin_fmm_net_force,
-    P.pin_fmm_sampled_matches_full,
+    P.pin_fmm_sampled_matches_full, P.pin_direct_gradient_formulas, P.pin_fmm_gradient_fixed_tree,
 ], ids=lambda f: f.__name__)
 def test_pin(pin):
     pin()
