@@ -102,6 +102,7 @@ typedef struct {
     int64_t tc_pairs;    /* M2L pairs handled by the tensor cores (FMM_PREC_MIXED_TC) */
     int64_t tc_classes;  /* translation classes (one operator each) */
     int64_t tc_items;    /* 128-pair work items */
+    int64_t nsys;        /* independent systems in the tree (1 unless built batched) */
 } fmm_tree_info;
 
 /*
@@ -161,17 +162,30 @@ int fmm_backward(fmm_tree* tree, const void* q, const void* w, const void* field
 
 /*
  * Build one tree holding nsys independent systems (a batch).
- *   offsets  host, nsys + 1 ascending particle offsets into pos (offsets[0] = 0).
+ *   offsets  host, nsys + 1 strictly ascending particle offsets into pos
+ *            (offsets[0] = 0; every system holds at least one particle).
  *   pos      device, offsets[nsys] x 3 of pos_dtype.
- * Each system gets its own root cube and octree; their cells and lists are
- * concatenated, so one fmm_evaluate_batched call runs every system.
+ * Each system gets its own root cube and octree (the rules of fmm_build_tree,
+ * applied per system); the systems' roots are cells 0..nsys-1, cells are
+ * ordered by (level, system, key) and no pair of cells crosses systems, so one
+ * evaluation runs every system in the same launches.
  */
 int fmm_build_tree_batched(const fmm_params* params, int32_t nsys, const int64_t* offsets,
                            const void* pos, int pos_dtype, fmm_tree** out, void* stream);
 
-/* Evaluate every system of a batched tree; arrays are concatenated like pos. */
+/* Evaluate every system of a batched tree; arrays are concatenated like pos.
+ * (fmm_evaluate does the same on any tree; this name documents the intent.) */
 int fmm_evaluate_batched(fmm_tree* tree, const void* q, void* phi, void* force, int dtype,
                          void* stream);
+
+/*
+ * Per-system geometry of a (batched) tree, host arrays, each may be NULL:
+ *   origins[3*nsys], sides[nsys]  root cube of each system;
+ *   cell_system[ncell]            system of each cell (cells are ordered by
+ *                                 level, then system, then key).
+ * Synchronises the device.
+ */
+int fmm_tree_export_systems(const fmm_tree* tree, double* origins, double* sides, int32_t* cell_system);
 
 /* Sizes and geometry of a tree (host struct filled). */
 int fmm_tree_get_info(const fmm_tree* tree, fmm_tree_info* info);

@@ -24,7 +24,8 @@ import numpy as np
 __all__ = [
     "FMM_OK", "FMM_ERR_ARG", "FMM_ERR_ALLOC", "FMM_ERR_CUDA", "FMM_ERR_TIMEOUT", "FMM_ERR_STATE",
     "PREC_FP64", "PREC_FP32_P2P", "PREC_FP32", "PREC_MIXED_TC", "OUT_FIELD", "STAGED", "TIMING",
-    "FMMError", "Params", "TreeInfo", "Tree", "build_tree", "evaluate", "library_path", "load",
+    "FMMError", "Params", "TreeInfo", "Tree", "build_tree", "build_tree_batched", "evaluate", "library_path", "load",
+    "capture_graph", "autotune_leaf_size",
 ]
 
 FMM_OK, FMM_ERR_ARG, FMM_ERR_ALLOC, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, FMM_ERR_STATE = 0, -1, -2, -3, -4, -5
@@ -55,7 +56,7 @@ class TreeInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("ncell", C.c_int32), ("nlevel", C.c_int32), ("nleaf", C.c_int32),
                 ("p", C.c_int32), ("nm2l", C.c_int64), ("np2p", C.c_int64), ("origin", C.c_double * 3),
                 ("side", C.c_double), ("device_bytes", C.c_int64), ("tc_pairs", C.c_int64),
-                ("tc_classes", C.c_int64), ("tc_items", C.c_int64)]
+                ("tc_classes", C.c_int64), ("tc_items", C.c_int64), ("nsys", C.c_int64)]
 
 
 def library_path() -> str:
@@ -92,6 +93,8 @@ def load():
             lib.fmm_stage_name.restype = C.c_char_p
             lib.fmm_kernel_launches.argtypes = [_P, C.c_int32]
             lib.fmm_kernel_launches.restype = C.c_int64
+            lib.fmm_tree_export_systems.argtypes = [_P, _P, _P, _P]
+            lib.fmm_tree_export_systems.restype = C.c_int
             lib.fmm_tree_set_positions.argtypes = [_P, _P, C.c_int, _P]
             lib.fmm_tree_set_positions.restype = C.c_int
             lib.fmm_backward.argtypes = [_P, _P, _P, _P, _P, _P, C.c_int, _P]
@@ -139,7 +142,7 @@ class Tree:
     """A built octree with interaction lists, owned by the library."""
 
     def __init__(self, pos, p: int = 4, leaf_size: int = 64, theta: float = 0.5,
-                 precision: int = PREC_FP64, flags: int = 0, timeout_ns: int = 0, stream=None):
+                 precision: int = PREC_FP64, flags: int = 0, timeout_ns: int = 0, stream=None, offsets=None):
         torch = _torch()
         lib = load()
         if not (pos.is_cuda and pos.dim() == 2 and pos.shape[1] == 3):
@@ -150,8 +153,18 @@ class Tree:
         self.device = pos.device
         h = _P()
         with torch.cuda.device(pos.device):
-            _check(lib.fmm_build_tree(C.byref(self.params), self.n, C.c_void_p(pos.data_ptr()), _dtype_code(pos),
-                                      C.byref(h), _stream_ptr(stream)))
+            if offsets is None:
+                _check(lib.fmm_build_tree(C.byref(self.params), self.n, C.c_void_p(pos.data_ptr()),
+                                          _dtype_code(pos), C.byref(h), _stream_ptr(stream)))
+                self.offsets = np.array([0, self.n], dtype=np.int64)
+            else:
+                off = np.ascontiguousarray(offsets, dtype=np.int64)
+                if off.ndim != 1 or off[-1] != self.n:
+                    raise ValueError("offsets must be 1-D and end at n")
+                _check(lib.fmm_build_tree_batched(C.byref(self.params), len(off) - 1, off.ctypes.data_as(_P),
+                                                  C.c_void_p(pos.data_ptr()), _dtype_code(pos), C.byref(h),
+                                                  _stream_ptr(stream)))
+                self.offsets = off
         self._h = h
 
     # -- evaluation -------------------------------------------------------
@@ -197,6 +210,15 @@ class Tree:
         _check(load().fmm_tree_get_info(self._h, C.byref(i)))
         return i
 
+    def export_systems(self):
+        """(origins [nsys,3], sides [nsys], cell_system [ncell]) of a batched tree."""
+        i = self.info()
+        ns = int(i.nsys)
+        org, sd, cs = np.zeros((ns, 3)), np.zeros(ns), np.zeros(i.ncell, np.int32)
+        _check(load().fmm_tree_export_systems(self._h, org.ctypes.data_as(_P), sd.ctypes.data_as(_P),
+                                              cs.ctypes.data_as(_P)))
+        return org, sd, cs
+
     def export(self) -> dict:
         """Host copies of keys, permutation, cell table and the sorted lists."""
         i = self.info()
@@ -237,6 +259,53 @@ class Tree:
 
 def build_tree(pos, **params) -> Tree:
     return Tree(pos, **params)
+
+
+def build_tree_batched(pos, offsets, **params) -> Tree:
+    """One tree holding independent systems; pos holds them back to back, system s
+    being rows offsets[s]..offsets[s+1]-1.  Evaluate it like any tree."""
+    return Tree(pos, offsets=offsets, **params)
+
+
+def capture_graph(tree, q, phi, force):
+    """Capture tree.evaluate(q) into a CUDA graph writing phi and force; returns
+    the torch.cuda.CUDAGraph (replay() re-runs the evaluation, which allocates
+    nothing and never synchronises)."""
+    torch = _torch()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        tree.evaluate(q, phi=phi, force=force)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        tree.evaluate(q, phi=phi, force=force)
+    return g
+
+
+def autotune_leaf_size(pos, q, offsets=None, candidates=(24, 32, 48, 64, 96, 128), repeats: int = 3, **params):
+    """Time build + evaluate for each leaf size and return (best, {leaf: ms}).
+
+    The cost balance between P2P (grows with the leaf size) and M2L (grows
+    with the number of cells) depends on the distribution and the order, so
+    the leaf size is chosen by measurement on the actual input."""
+    torch = _torch()
+    times = {}
+    for leaf in candidates:
+        kw = dict(params, leaf_size=int(leaf))
+        best = float("inf")
+        for r in range(repeats + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            t = Tree(pos, offsets=offsets, **kw)
+            t.evaluate(q)
+            e1.record()
+            torch.cuda.synchronize()
+            t.close()
+            if r > 0:
+                best = min(best, e0.elapsed_time(e1))
+        times[int(leaf)] = best
+    return min(times, key=times.get), times
 
 
 def evaluate(tree: Tree, q, **kw):

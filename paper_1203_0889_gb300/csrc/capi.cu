@@ -3,6 +3,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -57,8 +58,16 @@ const char* fmm_last_error(void) { return g_err; }
 
 const char* fmm_version(void) { return "paper_1203_0889_gb300 0.1 (sm_103a)"; }
 
+static int build_common(const fmm_params* params, int64_t n, const void* pos, int pos_dtype, fmm_tree** out,
+                        void* stream, const std::vector<int64_t>* offsets);
+
 int fmm_build_tree(const fmm_params* params, int64_t n, const void* pos, int pos_dtype, fmm_tree** out,
                    void* stream) {
+    return build_common(params, n, pos, pos_dtype, out, stream, nullptr);
+}
+
+static int build_common(const fmm_params* params, int64_t n, const void* pos, int pos_dtype, fmm_tree** out,
+                        void* stream, const std::vector<int64_t>* offsets) {
     g_err[0] = 0;
     if (!out) { fmm_set_error("out is NULL"); return FMM_ERR_ARG; }
     *out = nullptr;
@@ -70,9 +79,12 @@ int fmm_build_tree(const fmm_params* params, int64_t n, const void* pos, int pos
     setup_pool_once();
     fmm_tree* t = new (std::nothrow) fmm_tree();
     if (!t) { fmm_set_error("host allocation failed"); return FMM_ERR_ALLOC; }
+    if (offsets) t->h_sys_off = *offsets;
     t->prm = *params;
     if (t->prm.timeout_ns == 0) t->prm.timeout_ns = 2000000000LL;
     t->n = n;
+    if (t->h_sys_off.empty()) t->h_sys_off = {0, n};
+    t->nsys = (int)t->h_sys_off.size() - 1;
     cudaStream_t st = (cudaStream_t)stream;
     if (t->prm.flags & FMM_TIMING) {
         t->timing = true;
@@ -157,16 +169,39 @@ int fmm_backward(fmm_tree* tree, const void* q, const void* w, const void* field
 
 int fmm_build_tree_batched(const fmm_params* params, int32_t nsys, const int64_t* offsets, const void* pos,
                            int pos_dtype, fmm_tree** out, void* stream) {
-    (void)params; (void)nsys; (void)offsets; (void)pos; (void)pos_dtype; (void)stream;
+    g_err[0] = 0;
     if (out) *out = nullptr;
-    fmm_set_error("fmm_build_tree_batched: not available in this build");
-    return FMM_ERR_STATE;
+    if (nsys < 1 || !offsets) { fmm_set_error("fmm_build_tree_batched: nsys >= 1 and offsets are required"); return FMM_ERR_ARG; }
+    if (offsets[0] != 0) { fmm_set_error("fmm_build_tree_batched: offsets[0] must be 0"); return FMM_ERR_ARG; }
+    std::vector<int64_t> off(offsets, offsets + nsys + 1);
+    for (int s = 0; s < nsys; s++)
+        if (off[s + 1] <= off[s]) { fmm_set_error("fmm_build_tree_batched: system %d is empty or offsets descend", s); return FMM_ERR_ARG; }
+    return build_common(params, off[nsys], pos, pos_dtype, out, stream, &off);
 }
 
 int fmm_evaluate_batched(fmm_tree* tree, const void* q, void* phi, void* force, int dtype, void* stream) {
-    (void)tree; (void)q; (void)phi; (void)force; (void)dtype; (void)stream;
-    fmm_set_error("fmm_evaluate_batched: not available in this build");
-    return FMM_ERR_STATE;
+    return fmm_evaluate(tree, q, phi, force, dtype, stream);
+}
+
+int fmm_tree_export_systems(const fmm_tree* t, double* origins, double* sides, int32_t* cell_system) {
+    if (!t) { fmm_set_error("tree is NULL"); return FMM_ERR_ARG; }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { fmm_set_error("export: %s", cudaGetErrorString(e)); return FMM_ERR_CUDA; }
+    for (int s = 0; s < t->nsys && !t->h_geom.empty(); s++) {
+        if (origins) for (int k = 0; k < 3; k++) origins[3 * s + k] = t->h_geom[4 * s + k];
+        if (sides) sides[s] = t->h_geom[4 * s + 3];
+    }
+    if (cell_system && t->ncell) {
+        std::vector<int32_t> first(t->ncell);
+        e = cudaMemcpy(first.data(), t->d.first, 4 * (size_t)t->ncell, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { fmm_set_error("export: %s", cudaGetErrorString(e)); return FMM_ERR_CUDA; }
+        for (int c = 0; c < t->ncell; c++) {
+            int s = (int)(std::upper_bound(t->h_sys_off.begin(), t->h_sys_off.end(), (int64_t)first[c]) -
+                          t->h_sys_off.begin()) - 1;
+            cell_system[c] = s;
+        }
+    }
+    return FMM_OK;
 }
 
 int fmm_tree_get_info(const fmm_tree* t, fmm_tree_info* info) {
@@ -185,6 +220,7 @@ int fmm_tree_get_info(const fmm_tree* t, fmm_tree_info* info) {
     info->tc_pairs = t->tc_npairs;
     info->tc_classes = t->tc_nclass;
     info->tc_items = t->tc_nitems;
+    info->nsys = t->nsys;
     return FMM_OK;
 }
 

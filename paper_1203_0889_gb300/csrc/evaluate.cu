@@ -173,12 +173,12 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nleaf, const int32_t* _
                                                      const int64_t* __restrict__ start,
                                                      const int4* __restrict__ rec,
                                                      const typename Vec4<T>::type* __restrict__ xq,
-                                                     const int4* __restrict__ icentre, float u2f,
+                                                     const int4* __restrict__ icentre, const float* __restrict__ cu2f,
                                                      double* __restrict__ near) {
     __shared__ typename Vec4<T>::type buf[P2P_BUF];
     __shared__ T part[P2P_THREADS][4];
     if (blockIdx.x >= nleaf) return;
-    p2p_leaf<T>(leaves[blockIdx.x], first, count, start, rec, xq, icentre, u2f, near, buf, part);
+    p2p_leaf<T>(leaves[blockIdx.x], first, count, start, rec, xq, icentre, cu2f, near, buf, part);
 }
 
 // one warp per leaf: L2P + near field + output in input order
@@ -319,11 +319,10 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     stage_begin(t, FMM_STAGE_P2P, st);
     if (p2p_fp64(t))
         k_p2p<double><<<t->nleaf, P2P_THREADS, 0, st>>>(t->nleaf, d.leaves, d.first, d.count, d.p2p_start,
-                                                          d.p2p_rec, xq64, d.icentre, 0.f, d.near);
+                                                          d.p2p_rec, xq64, d.icentre, d.cu2f, d.near);
     else
         k_p2p<float><<<t->nleaf, P2P_THREADS, 0, st>>>(t->nleaf, d.leaves, d.first, d.count, d.p2p_start,
-                                                         d.p2p_rec, xq32, d.icentre,
-                                                         (float)(t->side / 4194304.0), d.near);
+                                                         d.p2p_rec, xq32, d.icentre, d.cu2f, d.near);
     count_launch(t);
     stage_end(t, FMM_STAGE_P2P, st);
     // upward pass

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "fmm.h"
 
 #define FMM_MAX_P 20
@@ -156,7 +158,9 @@ struct TreeDev {
     int32_t* tc_src = nullptr;
     int64_t* rem_start = nullptr; // CSR of the class-less pairs by target
     void* tc_msplit = nullptr;    // [ncell][hi|lo][Kp] bf16 multipoles
-    Geometry* geom = nullptr;
+    Geometry* geom = nullptr;     // [nsys] root cube of each system
+    int64_t* sys_off = nullptr;   // [nsys+1] particle offsets of the systems
+    float* cu2f = nullptr;        // [ncell] side/2^22 of the cell's system (FP32 P2P offsets)
     int* status = nullptr;        // device status word(s)
     // evaluation workspace
     void* M = nullptr;            // [ncell * ntri(p)] cplx<T>
@@ -192,6 +196,8 @@ struct fmm_tree {
     double origin[3] = {0, 0, 0}, side = 1.0;
     int64_t device_bytes = 0;
     int nsys = 1;
+    std::vector<int64_t> h_sys_off;   // host copy of the system offsets
+    std::vector<double> h_geom;       // per system: origin x, y, z, side
     int num_sms = 148;
     int64_t tc_nclass = 0, tc_nitems = 0, tc_npairs = 0, tc_nrem = 0;
     int64_t q_n_hi = 0, q_n0 = 0, q_n_tasks = 0;

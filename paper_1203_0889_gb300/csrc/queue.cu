@@ -52,7 +52,7 @@ struct QueueArgs {
     int p, ncell, nleaf, field;
     unsigned n_hi, n_lo, n_tasks;
     long long budget_cycles;
-    float u2f;
+    const float* cu2f;
     const int32_t* leaves;
     const int32_t* first;
     const int32_t* count;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(QUEUE_THREADS) k_queue(QueueArgs a) {
         } else {  // TK_P2P
             VP* buf = reinterpret_cast<VP*>(sm);
             TP(*part)[4] = reinterpret_cast<TP(*)[4]>(sm + P2P_BUF * sizeof(VP));
-            p2p_leaf<TP>(a.leaves[idx], a.first, a.count, a.p2p_start, a.p2p_rec, (const VP*)a.xqp, a.icentre, a.u2f,
+            p2p_leaf<TP>(a.leaves[idx], a.first, a.count, a.p2p_start, a.p2p_rec, (const VP*)a.xqp, a.icentre, a.cu2f,
                          a.near, buf, part);
         }
         // publish this task's writes, then release its successors
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(QUEUE_THREADS) k_queue(QueueArgs a) {
             } else if (kind == TK_M2M) {
                 on_m_final(a, idx, lane);
             } else if (kind == TK_M2L) {
-                if (idx == 0) on_l_final(a, 0, lane);
+                if (a.parent[idx] < 0) on_l_final(a, idx, lane);   // a root: its local is final
                 else if (lane == 0 && atomicSub(&a.dcnt[idx], 1) == 1) push(a, TK_L2L, idx);
             } else if (kind == TK_L2L) {
                 on_l_final(a, idx, lane);
@@ -261,14 +261,14 @@ __global__ void k_transpose_scatter(int ncell, const int64_t* start, const int32
         tr_tgt[tr_start[s] + k] = t;
     }
 }
-__global__ void k_queue_init_counters(int ncell, const int32_t* child_count, const int64_t* m2l_start, int32_t* cnt,
-                                      char* empty_m2l) {
+__global__ void k_queue_init_counters(int ncell, const int32_t* child_count, const int32_t* parent,
+                                      const int64_t* m2l_start, int32_t* cnt, char* empty_m2l) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     int nl = (int)(m2l_start[c + 1] - m2l_start[c]);
     cnt[c] = child_count[c];                     // mcnt
     cnt[ncell + c] = nl;                         // lcnt
-    cnt[2 * ncell + c] = c == 0 ? 0 : 2;         // dcnt
+    cnt[2 * ncell + c] = parent[c] < 0 ? 0 : 2;  // dcnt (roots have no L2L)
     cnt[3 * ncell + c] = child_count[c] == 0 ? 2 : 0;  // pcnt
     empty_m2l[c] = nl == 0;
 }
@@ -277,6 +277,14 @@ __global__ void k_queue_seed(int ngroups, int nempty, const int32_t* empty_cells
     if (i < ngroups) q[i] = (TK_P2M << TK_SHIFT) | i;
     else if (i < ngroups + nempty) q[i] = (TK_M2L << TK_SHIFT) | empty_cells[i - ngroups];
 }
+// queue heads and tails for a new evaluation (a kernel, so that an evaluation
+// captured in a CUDA graph replays it)
+__global__ void k_queue_reset(QueueCounters* c, unsigned n0) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c->head_hi = 0u; c->tail_hi = n0; c->head_lo = 0u; c->done = 0u; c->avail = (int)n0;
+    }
+}
+
 __global__ void k_iota(int n, int32_t* v) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) v[i] = i;
@@ -322,7 +330,8 @@ int build_queue(fmm_tree* t, cudaStream_t st) {
     if ((rc = dev_alloc(&cells, (size_t)nc, nullptr, st))) return rc;
     if ((rc = dev_alloc(&empty_cells, (size_t)nc, nullptr, st))) return rc;
     if ((rc = dev_alloc(&nsel, 1, nullptr, st))) return rc;
-    k_queue_init_counters<<<nblk(nc, 256), 256, 0, st>>>(nc, d.child_count, d.m2l_start, d.q_cnt_init, empty);
+    k_queue_init_counters<<<nblk(nc, 256), 256, 0, st>>>(nc, d.child_count, d.parent, d.m2l_start, d.q_cnt_init,
+                                                          empty);
     k_iota<<<nblk(nc, 256), 256, 0, st>>>(nc, cells);
     {
         size_t sb = 0;
@@ -337,7 +346,7 @@ int build_queue(fmm_tree* t, cudaStream_t st) {
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
     const int ngroups = (t->nleaf + P2M_GROUP - 1) / P2M_GROUP;
     const int ninternal = nc - t->nleaf;
-    t->q_n_hi = (int64_t)ngroups + ninternal + nc + (nc - 1) + t->nleaf;
+    t->q_n_hi = (int64_t)ngroups + ninternal + nc + (nc - t->nsys) + t->nleaf;   // L2L for every non-root cell
     t->q_n0 = ngroups + nempty;
     t->q_n_tasks = t->q_n_hi + t->nleaf;
     if ((rc = dev_alloc(&d.q_init, (size_t)t->q_n_hi, t, st))) return rc;
@@ -374,13 +383,13 @@ int evaluate_queue(fmm_tree* t, const double4_32a* xq64, const void* xqp, O* phi
     const int nc = t->ncell;
     FMM_CUDA_TRY(cudaMemcpyAsync(d.q_cnt, d.q_cnt_init, (size_t)4 * nc * 4, cudaMemcpyDeviceToDevice, st));
     FMM_CUDA_TRY(cudaMemcpyAsync(d.q_work, d.q_init, (size_t)t->q_n_hi * 4, cudaMemcpyDeviceToDevice, st));
-    QueueCounters h0 = {0u, (unsigned)t->q_n0, 0u, 0u, (int)t->q_n0};
-    FMM_CUDA_TRY(cudaMemcpyAsync(d.q_ctr, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+    k_queue_reset<<<1, 32, 0, st>>>((QueueCounters*)d.q_ctr, (unsigned)t->q_n0);
+    count_launch(t);
     QueueArgs a;
     a.p = p; a.ncell = nc; a.nleaf = t->nleaf; a.field = (t->prm.flags & FMM_OUT_FIELD) ? 1 : 0;
     a.n_hi = (unsigned)t->q_n_hi; a.n_lo = (unsigned)t->nleaf; a.n_tasks = (unsigned)t->q_n_tasks;
     a.budget_cycles = (long long)(t->prm.timeout_ns * 2);  // clock64 runs near 2 GHz
-    a.u2f = (float)(t->side / 4194304.0);
+    a.cu2f = d.cu2f;
     a.leaves = d.leaves; a.first = d.first; a.count = d.count; a.parent = d.parent;
     a.child_first = d.child_first; a.child_count = d.child_count; a.ckey = d.ckey; a.centre = d.centre;
     a.icentre = d.icentre; a.perm = d.perm; a.m2l_start = d.m2l_start; a.m2l_src = d.m2l_src;

@@ -263,8 +263,9 @@ __device__ __forceinline__ void p2p_pair(const typename Vec4<T>::type& me, const
 template <typename T>
 __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t* __restrict__ count,
                          const int64_t* __restrict__ start, const int4* __restrict__ rec,
-                         const typename Vec4<T>::type* __restrict__ xq, const int4* __restrict__ icentre, float u2f,
-                         double* __restrict__ near, typename Vec4<T>::type* buf, T (*part)[4]) {
+                         const typename Vec4<T>::type* __restrict__ xq, const int4* __restrict__ icentre,
+                         const float* __restrict__ cu2f, double* __restrict__ near, typename Vec4<T>::type* buf,
+                         T (*part)[4]) {
     typedef typename Vec4<T>::type V;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tf = first[c], nt = count[c];
@@ -272,6 +273,7 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
     int total = 0;
     if (s1 > s0) { const int4 r = rec[s1 - 1]; total = r.z + r.y; }
     const int4 ict = icentre[c];
+    const float u2f = cu2f[c];   // side/2^22 of the target's system (sources share it)
     for (int tb = 0; tb < nt; tb += P2P_THREADS) {
         const int ntc = min(P2P_THREADS, nt - tb);
         const int G = P2P_THREADS / ntc;

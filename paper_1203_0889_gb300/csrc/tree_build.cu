@@ -69,12 +69,13 @@ static int grow(T*& p, size_t& cap, size_t need, size_t keep, cudaStream_t st) {
 
 constexpr int BB_THREADS = 256;
 
+// Block b reduces particles [blk[2b], blk[2b+1]) (one system's share).
 template <typename T>
-__global__ void k_bbox_partial(const T* __restrict__ pos, int64_t n, double* part, Geometry* g) {
+__global__ void k_bbox_partial(const T* __restrict__ pos, const int64_t* __restrict__ blk, double* part, Geometry* g) {
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     int bad = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = blk[2 * blockIdx.x], i1 = blk[2 * blockIdx.x + 1];
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         for (int d = 0; d < 3; d++) {
             double v = (double)pos[3 * i + d];
             if (!isfinite(v)) bad = 1;
@@ -98,17 +99,22 @@ __global__ void k_bbox_partial(const T* __restrict__ pos, int64_t n, double* par
         for (int k = 0; k < 6; k++) part[blockIdx.x * 6 + k] = s[k][0];
 }
 
-// Root cube (same operation sequence as the oracle): side = longest extent
-// (1 if zero), origin = (lo + hi) * 0.5 - side * 0.5, inv = 2^21 / side.
-__global__ void k_bbox_final(const double* part, int nb, Geometry* g) {
-    // one warp: lanes reduce strided partials, then a shuffle tree (min/max are exact)
-    int lane = threadIdx.x;
+// Root cube of system s (same operation sequence as the oracle): side = longest
+// extent (1 if zero), origin = (lo + hi) * 0.5 - side * 0.5, inv = 2^21 / side.
+// One warp per system reduces the partials of the system's blocks
+// [sblk[s], sblk[s+1]); min/max are exact, so the order does not matter.
+__global__ void k_bbox_final(const double* part, const int32_t* sblk, int nsys, Geometry* gs) {
+    const int sy = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (sy >= nsys) return;
+    Geometry* g = gs + sy;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = lane; b < nb; b += 32)
+    for (int b = sblk[sy] + lane; b < sblk[sy + 1]; b += 32)
         for (int d = 0; d < 3; d++) {
             lo[d] = fmin(lo[d], part[b * 6 + d]);
             hi[d] = fmax(hi[d], part[b * 6 + 3 + d]);
         }
+    if (lane == 0 && gs[0].bad) g->bad = 1;
     for (int o = 16; o > 0; o >>= 1)
         for (int d = 0; d < 3; d++) {
             lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
@@ -153,11 +159,21 @@ __device__ __forceinline__ uint64_t quantise(double x, double o, double inv) {
     return (uint64_t)v;
 }
 
+__device__ __forceinline__ int system_of(int64_t i, const int64_t* off, int nsys) {
+    int a = 0, b = nsys;   // last s with off[s] <= i
+    while (b - a > 1) {
+        int mid = (a + b) >> 1;
+        if (off[mid] <= i) a = mid; else b = mid;
+    }
+    return a;
+}
+
 template <typename T>
-__global__ void k_keys(const T* __restrict__ pos, int64_t n, const Geometry* __restrict__ g,
-                       uint64_t* keys, int32_t* idx) {
+__global__ void k_keys(const T* __restrict__ pos, int64_t n, const int64_t* __restrict__ off, int nsys,
+                       const Geometry* __restrict__ gs, uint64_t* keys, int32_t* idx) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const Geometry* g = gs + system_of(i, off, nsys);
     uint64_t kx = quantise((double)pos[3 * i], g->origin[0], g->inv);
     uint64_t ky = quantise((double)pos[3 * i + 1], g->origin[1], g->inv);
     uint64_t kz = quantise((double)pos[3 * i + 2], g->origin[2], g->inv);
@@ -239,10 +255,13 @@ __global__ void k_emit_children(int lb, int le, int level, int leaf_size, const 
     parent[w] = c;
 }
 
-__global__ void k_centres(int ncell, const int32_t* lev, const uint64_t* ckey, const Geometry* g,
-                          double4_32a* centre, int4* icentre) {
+__global__ void k_centres(int ncell, const int32_t* lev, const uint64_t* ckey, const int32_t* first,
+                          const int64_t* off, int nsys, const Geometry* gs, double4_32a* centre, int4* icentre,
+                          float* cu2f) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
+    const Geometry* g = gs + system_of(first[c], off, nsys);
+    cu2f[c] = (float)__ddiv_rn(g->side, 4194304.0);
     int l = lev[c];
     int64_t s = (int64_t)1 << (FMM_MAX_LEVEL - l);
     uint64_t k = ckey[c];
@@ -262,6 +281,18 @@ __global__ void k_centres(int ncell, const int32_t* lev, const uint64_t* ckey, c
 // ---------------------------------------------------------------------------
 // breadth-first dual tree traversal
 // ---------------------------------------------------------------------------
+
+__global__ void k_init_roots(int nsys, const int64_t* off, int32_t* lev, uint64_t* ckey, int32_t* first,
+                             int32_t* count, int32_t* parent) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    lev[s] = 0; ckey[s] = 0; first[s] = (int32_t)off[s]; count[s] = (int32_t)(off[s + 1] - off[s]); parent[s] = -1;
+}
+
+__global__ void k_init_frontier(int nsys, int2* front) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsys) front[s] = make_int2(s, s);
+}
 
 struct TravCounters {
     unsigned long long nm2l, np2p, nnext;
@@ -421,24 +452,47 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     int rc;
     const int64_t n = t->n;
     TreeDev& d = t->d;
-    if ((rc = dev_alloc(&d.geom, 1, t, st))) return rc;
-    FMM_CUDA_TRY(cudaMemsetAsync(d.geom, 0, sizeof(Geometry), st));
+    const int nsys = t->nsys;
+    if ((rc = dev_alloc(&d.geom, (size_t)nsys, t, st))) return rc;
+    FMM_CUDA_TRY(cudaMemsetAsync(d.geom, 0, sizeof(Geometry) * nsys, st));
     if ((rc = dev_alloc(&d.status, 4, t, st))) return rc;
     FMM_CUDA_TRY(cudaMemsetAsync(d.status, 0, 4 * sizeof(int), st));
     if (n == 0) {
         t->ncell = 0; t->nlevel = 0; t->nleaf = 0;
         return FMM_OK;
     }
+    if ((rc = dev_alloc(&d.sys_off, (size_t)nsys + 1, t, st))) return rc;
+    FMM_CUDA_TRY(cudaMemcpyAsync(d.sys_off, t->h_sys_off.data(), sizeof(int64_t) * (nsys + 1), cudaMemcpyHostToDevice, st));
     stage_begin(t, FMM_STAGE_KEYS, st);
-    // --- a1: root cube, keys
-    int nb = (int)std::min<int64_t>(1024, (n + BB_THREADS - 1) / BB_THREADS);
+    // --- a1: root cube of every system, keys.  Blocks of the bounding-box
+    // reduction are dealt to the systems in proportion to their size.
+    std::vector<int64_t> hblk;
+    std::vector<int32_t> hsblk(nsys + 1, 0);
+    {
+        const int64_t chunk = std::max<int64_t>(BB_THREADS * 8, (n + 1023) / 1024);
+        for (int s = 0; s < nsys; s++) {
+            hsblk[s] = (int32_t)(hblk.size() / 2);
+            for (int64_t a = t->h_sys_off[s]; a < t->h_sys_off[s + 1]; a += chunk) {
+                hblk.push_back(a);
+                hblk.push_back(std::min(t->h_sys_off[s + 1], a + chunk));
+            }
+        }
+        hsblk[nsys] = (int32_t)(hblk.size() / 2);
+    }
+    const int nb = hsblk[nsys];
     double* part = nullptr;
+    int64_t* dblk = nullptr;
+    int32_t* dsblk = nullptr;
     if ((rc = dev_alloc(&part, (size_t)nb * 6, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&dblk, hblk.size(), nullptr, st))) return rc;
+    if ((rc = dev_alloc(&dsblk, (size_t)nsys + 1, nullptr, st))) return rc;
+    FMM_CUDA_TRY(cudaMemcpyAsync(dblk, hblk.data(), sizeof(int64_t) * hblk.size(), cudaMemcpyHostToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(dsblk, hsblk.data(), sizeof(int32_t) * (nsys + 1), cudaMemcpyHostToDevice, st));
     if (pos_dtype == FMM_F64)
-        k_bbox_partial<double><<<nb, BB_THREADS, 0, st>>>((const double*)pos, n, part, d.geom);
+        k_bbox_partial<double><<<nb, BB_THREADS, 0, st>>>((const double*)pos, dblk, part, d.geom);
     else
-        k_bbox_partial<float><<<nb, BB_THREADS, 0, st>>>((const float*)pos, n, part, d.geom);
-    k_bbox_final<<<1, 32, 0, st>>>(part, nb, d.geom);
+        k_bbox_partial<float><<<nb, BB_THREADS, 0, st>>>((const float*)pos, dblk, part, d.geom);
+    k_bbox_final<<<nblk((int64_t)nsys * 32, 128), 128, 0, st>>>(part, dsblk, nsys, d.geom);
     count_launch(t, 2);
     uint64_t* keys_in = nullptr;
     int32_t* idx_in = nullptr;
@@ -447,21 +501,31 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     if ((rc = dev_alloc(&d.keys, n, t, st))) return rc;
     if ((rc = dev_alloc(&d.perm, n, t, st))) return rc;
     if (pos_dtype == FMM_F64)
-        k_keys<double><<<nblk(n, 256), 256, 0, st>>>((const double*)pos, n, d.geom, keys_in, idx_in);
+        k_keys<double><<<nblk(n, 256), 256, 0, st>>>((const double*)pos, n, d.sys_off, nsys, d.geom, keys_in, idx_in);
     else
-        k_keys<float><<<nblk(n, 256), 256, 0, st>>>((const float*)pos, n, d.geom, keys_in, idx_in);
+        k_keys<float><<<nblk(n, 256), 256, 0, st>>>((const float*)pos, n, d.sys_off, nsys, d.geom, keys_in, idx_in);
     count_launch(t);
-    // --- a2: stable sort of (key, input index)
+    // --- a2: stable sort of (key, input index), within each system
     size_t tmp_bytes = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, d.keys, idx_in, d.perm, n, 0, 63, st);
     char* tmp = nullptr;
-    if ((rc = dev_alloc(&tmp, tmp_bytes, nullptr, st))) return rc;
-    FMM_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys_in, d.keys, idx_in, d.perm, n, 0, 63, st));
+    if (nsys == 1) {
+        cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, d.keys, idx_in, d.perm, n, 0, 63, st);
+        if ((rc = dev_alloc(&tmp, tmp_bytes, nullptr, st))) return rc;
+        FMM_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys_in, d.keys, idx_in, d.perm, n, 0, 63, st));
+    } else {
+        cub::DeviceSegmentedRadixSort::SortPairs(nullptr, tmp_bytes, keys_in, d.keys, idx_in, d.perm, n, nsys,
+                                                 d.sys_off, d.sys_off + 1, 0, 63, st);
+        if ((rc = dev_alloc(&tmp, tmp_bytes, nullptr, st))) return rc;
+        FMM_CUDA_TRY(cub::DeviceSegmentedRadixSort::SortPairs(tmp, tmp_bytes, keys_in, d.keys, idx_in, d.perm, n,
+                                                              nsys, d.sys_off, d.sys_off + 1, 0, 63, st));
+    }
     count_launch(t);
     dev_free(tmp, st);
     dev_free(keys_in, st);
     dev_free(idx_in, st);
     dev_free(part, st);
+    dev_free(dblk, st);
+    dev_free(dsblk, st);
     if ((rc = dev_alloc(&d.spos, (size_t)n * 3, t, st))) return rc;
     if (pos_dtype == FMM_F64)
         k_gather_pos<double><<<nblk(n, 256), 256, 0, st>>>((const double*)pos, d.perm, n, d.spos);
@@ -469,15 +533,20 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         k_gather_pos<float><<<nblk(n, 256), 256, 0, st>>>((const float*)pos, d.perm, n, d.spos);
     count_launch(t);
     stage_end(t, FMM_STAGE_KEYS, st);
-    Geometry hg;
-    FMM_CUDA_TRY(cudaMemcpyAsync(&hg, d.geom, sizeof(Geometry), cudaMemcpyDeviceToHost, st));
+    std::vector<Geometry> hg(nsys);
+    FMM_CUDA_TRY(cudaMemcpyAsync(hg.data(), d.geom, sizeof(Geometry) * nsys, cudaMemcpyDeviceToHost, st));
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    if (hg.bad) {
-        fmm_set_error("fmm_build_tree: positions contain a non-finite value");
-        return FMM_ERR_ARG;
+    t->h_geom.assign((size_t)nsys * 4, 0.0);
+    for (int s = 0; s < nsys; s++) {
+        if (hg[s].bad) {
+            fmm_set_error("fmm_build_tree: positions contain a non-finite value");
+            return FMM_ERR_ARG;
+        }
+        for (int k = 0; k < 3; k++) t->h_geom[4 * s + k] = hg[s].origin[k];
+        t->h_geom[4 * s + 3] = hg[s].side;
     }
-    for (int k = 0; k < 3; k++) t->origin[k] = hg.origin[k];
-    t->side = hg.side;
+    for (int k = 0; k < 3; k++) t->origin[k] = hg[0].origin[k];
+    t->side = hg[0].side;
 
     // --- a2: octree, level by level
     stage_begin(t, FMM_STAGE_OCTREE, st);
@@ -496,19 +565,12 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         if ((r = grow(cc, c_cc, need, keep, st))) return r;
         return FMM_OK;
     };
-    if ((rc = grow_all(cap, 0))) return rc;
-    {
-        int32_t zero = 0, n32 = (int32_t)n, m1 = -1;
-        uint64_t k0 = 0;
-        FMM_CUDA_TRY(cudaMemcpyAsync(lev, &zero, 4, cudaMemcpyHostToDevice, st));
-        FMM_CUDA_TRY(cudaMemcpyAsync(ckey, &k0, 8, cudaMemcpyHostToDevice, st));
-        FMM_CUDA_TRY(cudaMemcpyAsync(first, &zero, 4, cudaMemcpyHostToDevice, st));
-        FMM_CUDA_TRY(cudaMemcpyAsync(count, &n32, 4, cudaMemcpyHostToDevice, st));
-        FMM_CUDA_TRY(cudaMemcpyAsync(par, &m1, 4, cudaMemcpyHostToDevice, st));
-    }
+    if ((rc = grow_all(std::max(cap, (size_t)nsys + 64), 0))) return rc;
+    k_init_roots<<<nblk(nsys, 128), 128, 0, st>>>(nsys, d.sys_off, lev, ckey, first, count, par);
+    count_launch(t);
     int32_t *nch = nullptr, *coff = nullptr;
     size_t c_nch = 0, c_coff = 0;
-    int lb = 0, le = 1, level = 0;
+    int lb = 0, le = nsys, level = 0;
     t->level_start[0] = 0;
     while (true) {
         int width = le - lb;
@@ -567,7 +629,9 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     dev_free(par, st); dev_free(cf, st); dev_free(cc, st);
     if ((rc = dev_alloc(&d.centre, nc, t, st))) return rc;
     if ((rc = dev_alloc(&d.icentre, nc, t, st))) return rc;
-    k_centres<<<nblk(nc, 128), 128, 0, st>>>((int)nc, d.level, d.ckey, d.geom, d.centre, d.icentre);
+    if ((rc = dev_alloc(&d.cu2f, nc, t, st))) return rc;
+    k_centres<<<nblk(nc, 128), 128, 0, st>>>((int)nc, d.level, d.ckey, d.first, d.sys_off, nsys, d.geom, d.centre,
+                                              d.icentre, d.cu2f);
     count_launch(t);
     // leaves
     {
@@ -599,18 +663,16 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     stage_begin(t, FMM_STAGE_LISTS, st);
     size_t c_front = 1024, c_next = 1024, c_m = 1024, c_p = 1024;
     int2 *front = nullptr, *next = nullptr, *m2l = nullptr, *p2p = nullptr;
-    if ((rc = grow(front, c_front = 0, 1024, 0, st))) return rc;
+    if ((rc = grow(front, c_front = 0, std::max<size_t>(1024, nsys), 0, st))) return rc;
     if ((rc = grow(next, c_next = 0, 1024, 0, st))) return rc;
     if ((rc = grow(m2l, c_m = 0, 1024, 0, st))) return rc;
     if ((rc = grow(p2p, c_p = 0, 1024, 0, st))) return rc;
     TravCounters* ctr = nullptr;
     if ((rc = dev_alloc(&ctr, 1, nullptr, st))) return rc;
     FMM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(TravCounters), st));
-    {
-        int2 root = make_int2(0, 0);
-        FMM_CUDA_TRY(cudaMemcpyAsync(front, &root, sizeof(int2), cudaMemcpyHostToDevice, st));
-    }
-    int64_t nf = 1, nm = 0, npp = 0;
+    k_init_frontier<<<nblk(nsys, 128), 128, 0, st>>>(nsys, front);
+    count_launch(t);
+    int64_t nf = nsys, nm = 0, npp = 0;
     const double th2 = t->prm.theta * t->prm.theta;
     while (nf > 0) {
         if ((rc = grow(next, c_next, (size_t)nf * 8, 0, st))) return rc;
@@ -702,7 +764,7 @@ void free_tree_device(fmm_tree* t) {
     dev_free(d.keys, st); dev_free(d.perm, st); dev_free(d.spos, st);
     dev_free(d.level, st); dev_free(d.ckey, st); dev_free(d.first, st); dev_free(d.count, st);
     dev_free(d.parent, st); dev_free(d.child_first, st); dev_free(d.child_count, st);
-    dev_free(d.centre, st); dev_free(d.icentre, st); dev_free(d.leaves, st); dev_free(d.pleaf, st);
+    dev_free(d.centre, st); dev_free(d.icentre, st); dev_free(d.sys_off, st); dev_free(d.cu2f, st); dev_free(d.leaves, st); dev_free(d.pleaf, st);
     dev_free(d.m2l_start, st); dev_free(d.m2l_src, st); dev_free(d.p2p_start, st); dev_free(d.p2p_src, st);
     dev_free(d.geom, st); dev_free(d.status, st);
     if (d.grad_tmp) cudaFreeAsync(d.grad_tmp, st);
