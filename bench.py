@@ -53,7 +53,25 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=1 << 17)
+    ap.add_argument("--workload", default="plummer", choices=["plummer", "batched"],
+                    help="plummer: one 1M-particle system (default); batched: 512 systems of 1024..65536")
     return ap.parse_args()
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The slowest rank's value (max over the process group; x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_per_rank: int, world: int, steps: int, slowest_s: float) -> float:
+    """Particles of all ranks over the slowest rank's time (replicas: weak scaling)."""
+    return n_per_rank * world * steps / slowest_s
 
 
 def dist_env():
@@ -264,11 +282,8 @@ def run_ours(args):
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) * 1e-3
-    if world > 1:
-        tt_ = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt_, op=dist.ReduceOp.MAX)
-        total_s = float(tt_.item())
-    value = n * world * args.steps / total_s
+    total_s = max_over_ranks(total_s, dev)
+    value = job_throughput(n, world, args.steps, total_s)
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
     props = torch.cuda.get_device_properties(dev)
     roof = roofline(stage_ms, ex, args.precision, clocks.get("sm_mhz"), props.multi_processor_count, info)
@@ -391,10 +406,82 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_batched(args):
+    """512 independent systems (uniform / Plummer / clustered by index mod 3,
+    N_s log-uniform in [1024, 65536], q ~ U[-1,1], p = 6, theta = 0.5, FP32):
+    one batched tree, one task-queue evaluation replayed from a CUDA graph.
+    The leaf size is picked by the autotuner on the first 64 systems."""
+    import torch
+
+    import paper_1203_0889_gb300 as fmm
+    import workloads as W
+
+    dev = torch.device("cuda", 0)
+    systems = W.make_batched(512)
+    sizes = np.array([len(s[1]) for s in systems], np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    pos = torch.tensor(np.concatenate([s[0] for s in systems]), dtype=torch.float64, device=dev)
+    q = torch.tensor(np.concatenate([s[1] for s in systems]), dtype=torch.float32, device=dev)
+    n = int(off[-1])
+    k = 64
+    leaf, tune = fmm.autotune_leaf_size(pos[:off[k]], q[:off[k]], offsets=off[:k + 1], repeats=2, p=6, theta=0.5,
+                                        precision=fmm.PREC_FP32)
+    prm = dict(p=6, leaf_size=leaf, theta=0.5, precision=fmm.PREC_FP32)
+    phi = torch.empty(n, dtype=torch.float32, device=dev)
+    force = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        t = fmm.build_tree_batched(pos, off, **prm)
+        t.evaluate(q, phi=phi, force=force)
+        t.close()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k_ in range(args.steps):
+        flush.zero_()
+        ev[k_][0].record()
+        t = fmm.build_tree_batched(pos, off, **prm)
+        t.evaluate(q, phi=phi, force=force)
+        ev[k_][1].record()
+        if k_ < args.steps - 1:
+            t.close()
+    torch.cuda.synchronize()
+    total_s = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
+    g = fmm.capture_graph(t, q, phi, force)
+    gt = []
+    for _ in range(max(3, args.steps)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        gt.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    info = t.info()
+    out = {
+        "metric": METRIC, "value": n * args.steps / total_s, "unit": "particles/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched: 512 systems, N={n} in total (1024..65536 each), p=6, theta=0.5",
+                   "step": "fmm_build_tree_batched + fmm_evaluate_batched", "leaf_size": leaf,
+                   "autotune_ms": tune, "evaluate_graph_replay_ms": statistics.median(gt),
+                   "evaluate_particles_per_s": n / (statistics.median(gt) * 1e-3),
+                   "ncell": info.ncell, "nm2l": info.nm2l, "np2p": info.np2p,
+                   "l2": "flushed between steps (512 MB write)"},
+        "clocks": clocks, "gpu_launches": t.kernel_launches(build=True) + t.kernel_launches(build=False),
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 
