@@ -117,6 +117,18 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
         return rc;
     }
     t->launch_ctr = nullptr;
+    if (t->n > 0 && (!fmm::queue_supported(t))) {
+        // the stage-by-stage path runs P2P on a second stream (non-blocking with
+        // respect to the legacy stream; joined by events inside each evaluation)
+        if (cudaStreamCreateWithFlags(&t->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (t->side_stream) cudaStreamDestroy(t->side_stream);
+            if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+            t->side_stream = nullptr; t->ev_fork = nullptr; t->ev_join = nullptr;
+        }
+    }
     *out = t;
     return FMM_OK;
 }
@@ -155,13 +167,11 @@ int fmm_backward(fmm_tree* tree, const void* q, const void* w, const void* field
     if (tree->n == 0) return FMM_OK;
     if (!q || !w || (dx && !field_q)) { fmm_set_error("q, w (and field_q when dx is wanted) must not be NULL"); return FMM_ERR_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
-    size_t esz = dtype == FMM_F64 ? 8 : 4;
     if (!tree->d.grad_tmp) {
         cudaError_t e = cudaMallocAsync(&tree->d.grad_tmp, (size_t)tree->n * 3 * 8, st);
         if (e != cudaSuccess) { fmm_set_error("backward: %s", cudaGetErrorString(e)); return FMM_ERR_ALLOC; }
         tree->device_bytes += (int64_t)tree->n * 3 * 8;
     }
-    (void)esz;
     int rc = fmm_evaluate(tree, w, dq, dx ? tree->d.grad_tmp : nullptr, dtype, stream);
     if (rc) return rc;
     return fmm::grad_combine(tree, q, w, field_q, tree->d.grad_tmp, dx, dtype, st);
@@ -254,10 +264,24 @@ int fmm_tree_export(const fmm_tree* t, uint64_t* keys, int64_t* perm, int32_t* l
         if (count) { CP(v.data(), d.count, nc, 4); for (size_t i = 0; i < nc; i++) count[i] = v[i]; }
     }
     // lists: expand CSR back to (target, source) pairs
+    if (m2l && t->nm2l && !d.m2l_start) {
+        // tensor-core trees keep their M2L pairs in class order only: sort here
+        std::vector<int32_t> tg((size_t)t->nm2l), sr((size_t)t->nm2l);
+        CP(tg.data(), d.tc_tgt, (size_t)t->nm2l, 4);
+        CP(sr.data(), d.tc_src, (size_t)t->nm2l, 4);
+        std::vector<uint64_t> key((size_t)t->nm2l);
+        for (size_t k = 0; k < key.size(); k++) key[k] = ((uint64_t)(uint32_t)tg[k] << 32) | (uint32_t)sr[k];
+        std::sort(key.begin(), key.end());
+        for (size_t k = 0; k < key.size(); k++) {
+            m2l[2 * k] = (int32_t)(key[k] >> 32);
+            m2l[2 * k + 1] = (int32_t)(key[k] & 0xffffffffu);
+        }
+    }
     for (int which = 0; which < 2; which++) {
         int32_t* out = which == 0 ? m2l : p2p;
         int64_t np = which == 0 ? t->nm2l : t->np2p;
         if (!out || np == 0) continue;
+        if (which == 0 && !d.m2l_start) continue;
         std::vector<int64_t> st(nc + 1);
         std::vector<int32_t> src((size_t)np);
         CP(st.data(), which == 0 ? d.m2l_start : d.p2p_start, nc + 1, 8);
@@ -301,6 +325,9 @@ void fmm_tree_destroy(fmm_tree* t) {
     fmm::free_tree_device(t);
     cudaStreamSynchronize(0);
     if (t->timing) for (int i = 0; i < 2 * FMM_NUM_STAGES; i++) cudaEventDestroy(t->ev[i]);
+    if (t->side_stream) cudaStreamDestroy(t->side_stream);
+    if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+    if (t->ev_join) cudaEventDestroy(t->ev_join);
     delete t;
 }
 

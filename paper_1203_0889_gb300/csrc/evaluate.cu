@@ -118,6 +118,24 @@ __global__ void __launch_bounds__(128) k_shift_dense(int p, int lb, int le, int 
     shift_cell<T, RQ, false>(p, c, kind, lane, child_first, child_count, parent, ckey, ops, E, xin);
 }
 
+// one block per destination cell of one level (NW warps)
+template <typename T, int RQ, int NW>
+__global__ void __launch_bounds__(32 * NW) k_shift_block(int p, int lb, int le, int kind,
+                                                         const int32_t* __restrict__ child_first,
+                                                         const int32_t* __restrict__ child_count,
+                                                         const int32_t* __restrict__ parent,
+                                                         const uint64_t* __restrict__ ckey, const T* __restrict__ ops,
+                                                         cplx<T>* __restrict__ E) {
+    extern __shared__ unsigned char smem_raw[];
+    const int K2 = 2 * ntri(p);
+    T* xin = reinterpret_cast<T*>(smem_raw);
+    T* red = xin + NW * K2;
+    const int c = lb + blockIdx.x;
+    if (c >= le) return;
+    if (kind == 0 && child_count[c] == 0) return;
+    shift_cell_block<T, RQ, NW>(p, c, kind, child_first, child_count, parent, ckey, ops, E, xin, red);
+}
+
 // one warp per leaf
 template <typename T>
 __global__ void k_p2m(int p, int nleaf, const int32_t* __restrict__ leaves, const int32_t* __restrict__ first,
@@ -252,14 +270,33 @@ static int launch_shift(fmm_tree* t, int kind, int lb, int le, cplx<T>* E, cudaS
     if (le <= lb) return FMM_OK;
     const TreeDev& d = t->d;
     const T* ops = (const T*)d.shift_ops;
-    size_t smem = (size_t)W * K2 * sizeof(T);
-    unsigned grid = nblk(le - lb, W);
     int rq = (K2 + 31) / 32;
+    // few cells (the top levels): a block of warps per cell splits the inputs;
+    // many cells: one warp per cell
+    const bool block_mode = (le - lb) < 8 * t->num_sms;
+    const int NWB = kind == 0 ? 8 : 4;
+    size_t smem = block_mode ? (size_t)2 * NWB * K2 * sizeof(T) : (size_t)W * K2 * sizeof(T);
+    unsigned grid = block_mode ? (unsigned)(le - lb) : nblk(le - lb, W);
 #define SHIFT_CASE(R)                                                                                         \
     if (rq <= R) {                                                                                            \
-        k_shift_dense<T, R><<<grid, 32 * W, smem, st>>>(p, lb, le, kind, d.child_first, d.child_count, d.parent, \
-                                                        d.ckey, ops, E);                                      \
+        if (block_mode && kind == 0) {                                                                        \
+            if (smem > 48 * 1024)                                                                             \
+                FMM_CUDA_TRY(cudaFuncSetAttribute(k_shift_block<T, R, 8>,                                     \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));    \
+            k_shift_block<T, R, 8><<<grid, 256, smem, st>>>(p, lb, le, kind, d.child_first, d.child_count,     \
+                                                            d.parent, d.ckey, ops, E);                        \
+        } else if (block_mode) {                                                                              \
+            if (smem > 48 * 1024)                                                                             \
+                FMM_CUDA_TRY(cudaFuncSetAttribute(k_shift_block<T, R, 4>,                                     \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));    \
+            k_shift_block<T, R, 4><<<grid, 128, smem, st>>>(p, lb, le, kind, d.child_first, d.child_count,     \
+                                                            d.parent, d.ckey, ops, E);                        \
+        } else {                                                                                              \
+            k_shift_dense<T, R><<<grid, 32 * W, smem, st>>>(p, lb, le, kind, d.child_first, d.child_count,     \
+                                                            d.parent, d.ckey, ops, E);                        \
+        }                                                                                                     \
         count_launch(t);                                                                                      \
+        FMM_CUDA_TRY(cudaGetLastError());                                                                     \
         return FMM_OK;                                                                                        \
     }
     SHIFT_CASE(1) SHIFT_CASE(2) SHIFT_CASE(3) SHIFT_CASE(5) SHIFT_CASE(8) SHIFT_CASE(12) SHIFT_CASE(15)
@@ -315,16 +352,24 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
         }
         return evaluate_queue<T, float, O>(t, xq64, xq32, phi, force, st);
     }
-    // P2P (near field)
-    stage_begin(t, FMM_STAGE_P2P, st);
+    // P2P (near field) depends on nothing but the particles: it runs on the
+    // tree's second stream, concurrently with the upward pass, M2L and L2L,
+    // and joins before L2P (the far field and the near field meet there)
+    cudaStream_t sp = t->side_stream ? t->side_stream : st;
+    if (t->side_stream) {
+        FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(sp, t->ev_fork, 0));
+    }
+    stage_begin(t, FMM_STAGE_P2P, sp);
     if (p2p_fp64(t))
-        k_p2p<double><<<t->nleaf, P2P_THREADS, 0, st>>>(t->nleaf, d.leaves, d.first, d.count, d.p2p_start,
+        k_p2p<double><<<t->nleaf, P2P_THREADS, 0, sp>>>(t->nleaf, d.leaves, d.first, d.count, d.p2p_start,
                                                           d.p2p_rec, xq64, d.icentre, d.cu2f, d.near);
     else
-        k_p2p<float><<<t->nleaf, P2P_THREADS, 0, st>>>(t->nleaf, d.leaves, d.first, d.count, d.p2p_start,
+        k_p2p<float><<<t->nleaf, P2P_THREADS, 0, sp>>>(t->nleaf, d.leaves, d.first, d.count, d.p2p_start,
                                                          d.p2p_rec, xq32, d.icentre, d.cu2f, d.near);
     count_launch(t);
-    stage_end(t, FMM_STAGE_P2P, st);
+    stage_end(t, FMM_STAGE_P2P, sp);
+    if (t->side_stream) FMM_CUDA_TRY(cudaEventRecord(t->ev_join, sp));
     // upward pass
     const int W = 4;
     stage_begin(t, FMM_STAGE_P2M, st);
@@ -341,7 +386,7 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     // M2L over every target's list (writes L of every cell)
     stage_begin(t, FMM_STAGE_M2L, st);
     int rc;
-    if (t->prm.precision == FMM_PREC_MIXED_TC && t->tc_nitems > 0) {
+    if (d.rem_start) {
         // class-less pairs on the CUDA cores (this also initialises every L), then
         // the classes on the tensor cores, accumulated into L
         rc = launch_m2l_generic<T>(t, p, 0, t->ncell, d.rem_start, d.tc_src + t->tc_npairs, d, M, L, st);
@@ -359,6 +404,7 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
         if (rc) return rc;
     }
     stage_end(t, FMM_STAGE_L2L, st);
+    if (t->side_stream) FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
     stage_begin(t, FMM_STAGE_L2P, st);
     k_l2p_finalize<T, O><<<nblk(t->nleaf, W), 32 * W, W * K * sizeof(cplx<T>), st>>>(
         p, t->nleaf, d.leaves, d.first, d.count, d.centre, xq64, d.perm, L, d.near, phi, force,

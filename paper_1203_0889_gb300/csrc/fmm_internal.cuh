@@ -188,6 +188,9 @@ struct fmm_tree {
     bool ev_used[FMM_NUM_STAGES] = {};
     bool timing = false;
     int64_t launches_build = 0, launches_eval = 0;
+    // second stream of the stage-by-stage evaluation (P2P beside the far field)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t* launch_ctr = nullptr;  // which counter launches currently go to
     int64_t n = 0;
     int ncell = 0, nlevel = 0, nleaf = 0;
@@ -234,7 +237,7 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st);
 int set_positions_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st);
 int grad_combine(fmm_tree* t, const void* q, const void* w, const void* eq, const void* ew, void* dx, int dtype,
                  cudaStream_t st);
-int build_m2l_classes(fmm_tree* t, cudaStream_t st);
+int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st);
 int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st);
 int tc_kpad(int p);
 bool queue_supported(const fmm_tree* t);

@@ -31,7 +31,11 @@ static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / 
 
 constexpr int TC_MAX_DL = 10;
 constexpr int TC_ROWS = 128;                 // MMA M: pairs per work item
-constexpr uint64_t NOT_TC = ~0ull;
+// Class keys use 53 bits: (level gap + 16) in bits 48..52, each offset component
+// + 32768 in 16 bits.  A pair outside every class gets NOT_TC | target, so such
+// pairs sort after all classes and by target.
+constexpr uint64_t NOT_TC = 1ull << 53;
+constexpr int CLASS_KEY_BITS = 54;
 
 int tc_kpad(int p) { return ((2 * ntri(p)) + 15) & ~15; }
 bool tc_supported(int p) { return tc_kpad(p) <= 144; }
@@ -40,20 +44,21 @@ bool tc_supported(int p) { return tc_kpad(p) <= 144; }
 // build: class keys, grouping, operators, work items
 // ---------------------------------------------------------------------------
 
-__global__ void k_class_keys(int64_t np, const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
-                             const int4* __restrict__ icentre, uint64_t* keys, int32_t* idx) {
+__global__ void k_class_keys(int64_t np, const int2* __restrict__ pairs, const int4* __restrict__ icentre,
+                             uint64_t* keys, int32_t* idx) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= np) return;
-    int4 a = icentre[tgt[e]], b = icentre[src[e]];
+    const int2 pr = pairs[e];
+    int4 a = icentre[pr.x], b = icentre[pr.y];
     int dl = a.w - b.w;
-    uint64_t key = NOT_TC;
+    uint64_t key = NOT_TC | (uint64_t)(uint32_t)pr.x;
     if (dl <= TC_MAX_DL && dl >= -TC_MAX_DL) {
         int64_t mn = (int64_t)1 << (FMM_MAX_LEVEL - max(a.w, b.w));  // side of the smaller cell, units u
         int64_t v[3] = {((int64_t)a.x - b.x) / mn, ((int64_t)a.y - b.y) / mn, ((int64_t)a.z - b.z) / mn};
         bool fits = true;
         for (int d = 0; d < 3; d++) fits = fits && v[d] > -32768 && v[d] < 32768;
         if (fits)
-            key = ((uint64_t)(dl + 32) << 48) | ((uint64_t)(v[0] + 32768) << 32) | ((uint64_t)(v[1] + 32768) << 16) |
+            key = ((uint64_t)(dl + 16) << 48) | ((uint64_t)(v[0] + 32768) << 32) | ((uint64_t)(v[1] + 32768) << 16) |
                   (uint64_t)(v[2] + 32768);
     }
     keys[e] = key;
@@ -74,13 +79,23 @@ __global__ void k_emit_items(int nclass, const int32_t* counts, const int32_t* c
     for (int r = 0; r < n; r += TC_ROWS) items[w++] = make_int4(c, f + r, min(TC_ROWS, n - r), 0);
 }
 
-__global__ void k_gather_pairs(int64_t np, const int32_t* __restrict__ order, const int32_t* __restrict__ tgt,
-                               const int32_t* __restrict__ src, int32_t* otgt, int32_t* osrc) {
+__global__ void k_gather_pairs(int64_t np, const int32_t* __restrict__ order, const int2* __restrict__ pairs,
+                               int32_t* otgt, int32_t* osrc) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= np) return;
-    int e = order[i];
-    otgt[i] = tgt[e];
-    osrc[i] = src[e];
+    const int2 pr = pairs[order[i]];
+    otgt[i] = pr.x;
+    osrc[i] = pr.y;
+}
+
+// number of sorted keys below NOT_TC (the pairs that belong to a class)
+__global__ void k_count_classed(const uint64_t* keys, int64_t np, int64_t* out) {
+    int64_t a = 0, b = np;
+    while (a < b) {
+        int64_t mid = (a + b) >> 1;
+        if (keys[mid] < NOT_TC) a = mid + 1; else b = mid;
+    }
+    *out = a;
 }
 
 __global__ void k_csr_from_targets(const int32_t* tgt, int64_t np, int ncell, int64_t* start) {
@@ -108,7 +123,7 @@ __global__ void k_class_operators(int p, int Kp, const uint64_t* __restrict__ uk
     int8_t* tm = tk + 256;
     const int c = blockIdx.x;
     const uint64_t key = ukeys[c];
-    const int dl = (int)((key >> 48) & 0xffff) - 32;
+    const int dl = (int)((key >> 48) & 0x1f) - 16;
     const double scale = 1.0 / (double)(2 << max(0, -dl));
     const double dx = (double)((int)((key >> 32) & 0xffff) - 32768) * scale;
     const double dy = (double)((int)((key >> 16) & 0xffff) - 32768) * scale;
@@ -163,51 +178,61 @@ __global__ void k_class_operators(int p, int Kp, const uint64_t* __restrict__ uk
     }
 }
 
-int build_m2l_classes(fmm_tree* t, cudaStream_t st) {
+int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st) {
     TreeDev& d = t->d;
     int rc;
     const int64_t np = t->nm2l;
     const int p = t->prm.p, Kp = tc_kpad(p);
     t->tc_nclass = 0; t->tc_nitems = 0; t->tc_npairs = 0;
-    if (np == 0) return FMM_OK;
+    if (np == 0) {
+        // no M2L pair at all: an empty class-less CSR keeps the M2L stage uniform
+        if ((rc = dev_alloc(&d.tc_tgt, 1, t, st))) return rc;
+        if ((rc = dev_alloc(&d.tc_src, 1, t, st))) return rc;
+        if ((rc = dev_alloc(&d.rem_start, (size_t)t->ncell + 1, t, st))) return rc;
+        FMM_CUDA_TRY(cudaMemsetAsync(d.rem_start, 0, sizeof(int64_t) * ((size_t)t->ncell + 1), st));
+        return FMM_OK;
+    }
     uint64_t *k0 = nullptr, *k1 = nullptr;
     int32_t *i0 = nullptr, *i1 = nullptr;
     if ((rc = dev_alloc(&k0, np, nullptr, st))) return rc;
     if ((rc = dev_alloc(&k1, np, nullptr, st))) return rc;
     if ((rc = dev_alloc(&i0, np, nullptr, st))) return rc;
     if ((rc = dev_alloc(&i1, np, nullptr, st))) return rc;
-    k_class_keys<<<nblk(np, 256), 256, 0, st>>>(np, d.m2l_tgt, d.m2l_src, d.icentre, k0, i0);
+    k_class_keys<<<nblk(np, 256), 256, 0, st>>>(np, pairs, d.icentre, k0, i0);
     count_launch(t);
     size_t tb = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, tb, k0, k1, i0, i1, (int64_t)np, 0, 64, st);
+    cub::DeviceRadixSort::SortPairs(nullptr, tb, k0, k1, i0, i1, (int64_t)np, 0, CLASS_KEY_BITS, st);
     char* tmp = nullptr;
     if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
-    FMM_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tb, k0, k1, i0, i1, (int64_t)np, 0, 64, st));
+    FMM_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tb, k0, k1, i0, i1, (int64_t)np, 0, CLASS_KEY_BITS, st));
     count_launch(t);
     cudaFreeAsync(tmp, st);
+    int64_t* d_ntc = nullptr;
+    if ((rc = dev_alloc(&d_ntc, 1, nullptr, st))) return rc;
+    k_count_classed<<<1, 1, 0, st>>>(k1, np, d_ntc);
+    int64_t ntc = 0;
+    FMM_CUDA_TRY(cudaMemcpyAsync(&ntc, d_ntc, 8, cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFreeAsync(d_ntc, st);
+    const int64_t nrem = np - ntc;
     // run-length encode the sorted keys: classes and their sizes
     uint64_t* ukeys = nullptr;
     int32_t *counts = nullptr, *nruns = nullptr;
     if ((rc = dev_alloc(&ukeys, np, nullptr, st))) return rc;
     if ((rc = dev_alloc(&counts, np, nullptr, st))) return rc;
     if ((rc = dev_alloc(&nruns, 1, nullptr, st))) return rc;
-    tb = 0;
-    cub::DeviceRunLengthEncode::Encode(nullptr, tb, k1, ukeys, counts, nruns, (int64_t)np, st);
-    if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
-    FMM_CUDA_TRY(cub::DeviceRunLengthEncode::Encode(tmp, tb, k1, ukeys, counts, nruns, (int64_t)np, st));
-    count_launch(t);
-    cudaFreeAsync(tmp, st);
     int32_t h_nruns = 0;
-    FMM_CUDA_TRY(cudaMemcpyAsync(&h_nruns, nruns, 4, cudaMemcpyDeviceToHost, st));
-    FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    uint64_t last_key = 0;
-    int32_t last_count = 0;
-    FMM_CUDA_TRY(cudaMemcpyAsync(&last_key, ukeys + h_nruns - 1, 8, cudaMemcpyDeviceToHost, st));
-    FMM_CUDA_TRY(cudaMemcpyAsync(&last_count, counts + h_nruns - 1, 4, cudaMemcpyDeviceToHost, st));
-    FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    const int nclass = last_key == NOT_TC ? h_nruns - 1 : h_nruns;
-    const int64_t nrem = last_key == NOT_TC ? last_count : 0;
-    const int64_t ntc = np - nrem;
+    if (ntc > 0) {
+        tb = 0;
+        cub::DeviceRunLengthEncode::Encode(nullptr, tb, k1, ukeys, counts, nruns, ntc, st);
+        if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
+        FMM_CUDA_TRY(cub::DeviceRunLengthEncode::Encode(tmp, tb, k1, ukeys, counts, nruns, ntc, st));
+        count_launch(t);
+        cudaFreeAsync(tmp, st);
+        FMM_CUDA_TRY(cudaMemcpyAsync(&h_nruns, nruns, 4, cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    const int nclass = h_nruns;
     // class offsets, items
     int32_t *cfirst = nullptr, *tiles = nullptr, *tfirst = nullptr;
     if ((rc = dev_alloc(&cfirst, (size_t)nclass + 1, nullptr, st))) return rc;
@@ -243,7 +268,7 @@ int build_m2l_classes(fmm_tree* t, cudaStream_t st) {
     // pairs in class order; the tail (no class) keeps target order for the CUDA-core kernel
     if ((rc = dev_alloc(&d.tc_tgt, (size_t)np, t, st))) return rc;
     if ((rc = dev_alloc(&d.tc_src, (size_t)np, t, st))) return rc;
-    k_gather_pairs<<<nblk(np, 256), 256, 0, st>>>(np, i1, d.m2l_tgt, d.m2l_src, d.tc_tgt, d.tc_src);
+    k_gather_pairs<<<nblk(np, 256), 256, 0, st>>>(np, i1, pairs, d.tc_tgt, d.tc_src);
     count_launch(t);
     if ((rc = dev_alloc(&d.rem_start, (size_t)t->ncell + 1, t, st))) return rc;
     k_csr_from_targets<<<nblk(t->ncell + 1, 256), 256, 0, st>>>(d.tc_tgt + ntc, nrem, t->ncell, d.rem_start);
@@ -275,99 +300,285 @@ __global__ void k_split_multipoles(int ncell, int K2, int KS, int Kp, const floa
     Ms[(int64_t)c * 2 * Kp + Kp + j] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-__global__ void __launch_bounds__(128) k_m2l_tc(int Kp, int ncol4, int ldL, int n_items, int per_cta,
-                                                const int4* __restrict__ items, const int32_t* __restrict__ pc_src,
-                                                const int32_t* __restrict__ pc_tgt,
-                                                const __nv_bfloat16* __restrict__ ops,
-                                                const __nv_bfloat16* __restrict__ Ms, float* __restrict__ L,
-                                                int* status, long long budget_ns) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char* A_hi = sm;
-    unsigned char* A_lo = A_hi + TC_ROWS * Kp * 2;
-    unsigned char* B_hi = A_lo + TC_ROWS * Kp * 2;
-    unsigned char* B_lo = B_hi + Kp * Kp * 2;
-    __shared__ uint64_t bar;
-    __shared__ uint32_t tslot;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t tcols = Kp <= 128 ? 128u : 256u;
-    if (warp == 0) { tc::tmem_alloc(&tslot, tcols); tc::tmem_relinquish(); }
-    if (tid == 0) tc::mbar_init(&bar, 1);
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t taddr = tslot;
-    const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, Kp);
-    const uint32_t sbo_a = (Kp / 8) * 128, sbo_b = sbo_a;
-    const int cpr = Kp / 8;  // 16-byte chunks per row
-    const int i0 = blockIdx.x * per_cta, i1 = min(n_items, i0 + per_cta);
-    int cur = -1;
-    uint32_t phase = 0;
-    bool ok = true;
-    for (int it = i0; it < i1 && ok; it++) {
-        const int4 item = items[it];
-        if (item.x != cur) {
-            const unsigned char* g = reinterpret_cast<const unsigned char*>(ops + (size_t)item.x * 2 * Kp * Kp);
-            const int nchunk = Kp * Kp * 2 * 2 / 16;  // hi then lo, contiguous in both places
-            for (int q = tid; q < nchunk; q += 128) tc::cp_async16(B_hi + 16 * q, g + 16 * q, 16);
-            cur = item.x;
-        }
-        for (int q = tid; q < TC_ROWS * cpr; q += 128) {
-            int r = q / cpr, j = q - r * cpr;
-            bool valid = r < item.z;
-            int s = valid ? pc_src[item.y + r] : 0;
-            const __nv_bfloat16* g = Ms + (size_t)s * 2 * Kp + 8 * j;
-            uint32_t off = tc::core_offset(r, 8 * j, Kp);
-            tc::cp_async16(A_hi + off, g, valid ? 16u : 0u);
-            tc::cp_async16(A_lo + off, g + Kp, valid ? 16u : 0u);
-        }
-        tc::cp_async_commit();
-        tc::cp_async_wait_all();
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-            const uint32_t ah = tc::smem_u32(A_hi), al = tc::smem_u32(A_lo);
-            const uint32_t bh = tc::smem_u32(B_hi), bl = tc::smem_u32(B_lo);
-            for (int ks = 0; ks < Kp / 16; ks++) {
-                const uint32_t o = ks * 256;
-                const uint64_t dah = tc::make_desc(ah + o, 128, sbo_a), dal = tc::make_desc(al + o, 128, sbo_a);
-                const uint64_t dbh = tc::make_desc(bh + o, 128, sbo_b), dbl = tc::make_desc(bl + o, 128, sbo_b);
-                tc::mma_bf16(taddr, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-                tc::mma_bf16(taddr, dah, dbl, idesc, 1u);
-                tc::mma_bf16(taddr, dal, dbh, idesc, 1u);
+// One persistent block per SM runs its range of work items as a
+// warp-specialised pipeline:
+//   producer warps (4)  gather the 128 source rows of an item (hi and lo
+//                       bf16 halves) into one of `stages` shared-memory stages
+//                       with cp.async, plus the class operator into one of
+//                       `nslots` operator slots when the class changes;
+//   MMA warp (1)        one thread issues the 3 x Kp/16 tcgen05.mma of an item
+//                       into one of `nacc` TMEM accumulators (Kp columns each)
+//                       and commits them to mbarriers;
+//   epilogue warps (8)  drain a finished accumulator into the targets' rows
+//                       of L with float2 reductions, two warps per TMEM lane
+//                       quarter, each taking half of the column blocks.
+// mbarriers: full[s] (producers -> MMA), empty[s] (MMA completion ->
+// producers), accf[a] (MMA completion -> epilogue), acce[a] (epilogue ->
+// MMA), opfree[o] (MMA completion of a class run -> producers).  Every wait is
+// bounded; a wait that runs out raises a block-wide abort flag, every role
+// leaves its loop, and the kernel reports FMM_ERR_TIMEOUT through *status.
+constexpr int TC_EPI_WARPS = 8, TC_PROD_WARPS = 4;
+constexpr int TC_MMA_WARP = TC_EPI_WARPS + TC_PROD_WARPS;
+constexpr int TC_THREADS = 32 * (TC_EPI_WARPS + TC_PROD_WARPS + 1);
+constexpr int TC_PROD_THREADS = 32 * TC_PROD_WARPS;
+constexpr int TC_MAX_STAGES = 4, TC_MAX_ACC = 4, TC_TMEM_COLS = 512;
+
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, long long budget_ns, volatile int* abort_flag) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (uint32_t it = 0;; it++) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if ((it & 15) == 15) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > 2 * budget_ns) {  // clock64 runs at about 2 GHz
+                *abort_flag = 1;
+                return false;
             }
-            tc::commit(&bar);
         }
-        bool done = tc::mbar_wait_bounded(&bar, phase, budget_ns);
-        ok = __syncthreads_and(done) != 0;
-        phase ^= 1u;
-        tc::fence_after_sync();
-        if (ok) {
-            const int r = 32 * warp + lane;
-            const int tg = r < item.z ? pc_tgt[item.y + r] : -1;
-            float* Lrow = L + (size_t)(tg < 0 ? 0 : tg) * ldL;
-            for (int cb = 0; cb < Kp / 16; cb++) {
-                float v[16];
-                tc::tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + 16 * cb, v);
-                if (tg >= 0) {
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// producer thread pt (0..127): its share of the 128 x Kp source rows (hi,
+// lo); src[r] is the source cell of row r, -1 for an empty row
+__device__ __forceinline__ void tc_gather(int pt, int Kp, int cpr, const int* src,
+                                          const __nv_bfloat16* __restrict__ Ms, unsigned char* A_hi,
+                                          unsigned char* A_lo) {
+    for (int q = pt; q < TC_ROWS * cpr; q += TC_PROD_THREADS) {
+        const int r = q / cpr, j = q - r * cpr;
+        const int sc = src[r];
+        const bool valid = sc >= 0;
+        const __nv_bfloat16* g = Ms + (size_t)(valid ? sc : 0) * 2 * Kp + 8 * j;
+        const uint32_t off = tc::core_offset(r, 8 * j, Kp);
+        tc::cp_async16(A_hi + off, g, valid ? 16u : 0u);
+        tc::cp_async16(A_lo + off, g + Kp, valid ? 16u : 0u);
+    }
+}
+
+__device__ __forceinline__ void tc_load_operator(int pt, int Kp, int cls, const __nv_bfloat16* __restrict__ ops,
+                                                 unsigned char* B) {
+    const unsigned char* g = reinterpret_cast<const unsigned char*>(ops + (size_t)cls * 2 * Kp * Kp);
+    const int nchunk = Kp * Kp * 2 * 2 / 16;  // hi then lo, contiguous in both places
+    for (int q = pt; q < nchunk; q += TC_PROD_THREADS) tc::cp_async16(B + 16 * q, g + 16 * q, 16);
+}
+
+// Adds one accumulator (TMEM columns from tacc on) into the targets' rows of
+// L; tgt[h][0..1] are the targets of rows 32 quarter + 16 h + lane/4 (+ 8),
+// -1 for an empty row.  The 16x256b TMEM load gives four consecutive threads
+// eight consecutive columns of one row, so each warp-wide float2 reduction
+// covers eight whole 32-byte sectors.
+__device__ __forceinline__ void tc_drain(uint32_t tacc, int quarter, int cb0, int cb1, int ncols, int ldL,
+                                         const int (&tgt)[2][2], float* __restrict__ L) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        int c4 = 4 * cb + q;
-                        if (c4 < ncol4)
-                            atomicAdd(reinterpret_cast<float4*>(Lrow) + c4,
-                                      make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
-                    }
+    for (int h = 0; h < 2; h++) {
+        const int ta = tgt[h][0], tb = tgt[h][1];
+        float* La = L + (size_t)(ta < 0 ? 0 : ta) * ldL;
+        float* Lb = L + (size_t)(tb < 0 ? 0 : tb) * ldL;
+        for (int cb = cb0; cb < cb1; cb++) {
+            float v[8];
+            tc::tmem_ld16x256(tacc + ((uint32_t)(32 * quarter + 16 * h) << 16) + 16 * cb, v);
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const int col = 16 * cb + 8 * k + 2 * (lane & 3);
+                if (col < ncols) {
+                    if (ta >= 0) atomicAdd(reinterpret_cast<float2*>(La + col), make_float2(v[4 * k], v[4 * k + 1]));
+                    if (tb >= 0)
+                        atomicAdd(reinterpret_cast<float2*>(Lb + col), make_float2(v[4 * k + 2], v[4 * k + 3]));
                 }
             }
         }
-        tc::fence_before_sync();
-        __syncthreads();
     }
-    if (!ok && tid == 0) atomicExch(status, 1);
+}
+
+struct TcShape {
+    int stages, nslots, nacc;
+    size_t smem;
+};
+
+// stages and operator slots that fit `cap` bytes of shared memory, and TMEM
+// accumulators that fit the 512 columns of one SM (one block per SM)
+static TcShape tc_shape(int Kp, size_t cap) {
+    const size_t stage = (size_t)2 * TC_ROWS * Kp * 2 + TC_ROWS * sizeof(int), slot = (size_t)2 * Kp * Kp * 2;
+    TcShape sh{};
+    sh.nslots = 2 * slot + 2 * stage <= cap ? 2 : 1;
+    sh.stages = (int)std::min<size_t>(TC_MAX_STAGES, (cap - sh.nslots * slot) / stage);
+    sh.nacc = std::min(TC_MAX_ACC, TC_TMEM_COLS / Kp);
+    sh.smem = sh.stages * stage + sh.nslots * slot;
+    return sh;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_m2l_tc(int Kp, int stages, int nslots, int nacc, int ncols, int ldL, int n_items, int per_cta,
+             const int4* __restrict__ items, const int32_t* __restrict__ pc_src, const int32_t* __restrict__ pc_tgt,
+             const __nv_bfloat16* __restrict__ ops, const __nv_bfloat16* __restrict__ Ms, float* __restrict__ L,
+             int* status, long long budget_ns) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ uint64_t full[TC_MAX_STAGES], empty[TC_MAX_STAGES], accf[TC_MAX_ACC], acce[TC_MAX_ACC], opfree[2];
+    __shared__ uint32_t tslot;
+    __shared__ int abort_flag;
+    const size_t abytes = (size_t)TC_ROWS * Kp * 2, bbytes = (size_t)Kp * Kp * 2;
+    // stage s: A hi at sm + 2 s abytes, A lo right after; operator slot o: hi at
+    // sm + 2 stages abytes + 2 o bbytes, lo right after; then the row sources
+    // of each stage (TC_ROWS ints per stage)
+    auto A_of = [&](int s) { return sm + 2 * s * abytes; };
+    auto B_of = [&](int o) { return sm + 2 * stages * abytes + 2 * o * bbytes; };
+    int* src_idx = reinterpret_cast<int*>(sm + 2 * stages * abytes + 2 * nslots * bbytes);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < stages; s++) { tc::mbar_init(&full[s], TC_PROD_THREADS); tc::mbar_init(&empty[s], 1); }
+        for (int a = 0; a < nacc; a++) { tc::mbar_init(&accf[a], 1); tc::mbar_init(&acce[a], TC_EPI_WARPS); }
+        tc::mbar_init(&opfree[0], 1);
+        tc::mbar_init(&opfree[1], 1);
+        abort_flag = 0;
+    }
+    if (warp == TC_MMA_WARP) { tc::tmem_alloc(&tslot, TC_TMEM_COLS); tc::tmem_relinquish(); }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(taddr, tcols);
+    const uint32_t tbase = tslot;
+    const int i0 = blockIdx.x * per_cta, i1 = min(n_items, i0 + per_cta), nit = max(0, i1 - i0);
+    volatile int* abort_p = &abort_flag;
+
+    if (warp >= TC_EPI_WARPS && warp < TC_MMA_WARP) {
+        // ---------------- producers
+        // Item j+1 and the source of row pt of item j+1 are loaded while item j
+        // is gathered; the 128 sources of an item go through shared memory so
+        // that no cp.async waits on a global load.
+        const int pt = tid - 32 * TC_EPI_WARPS, cpr = Kp / 8, D = stages - 1;
+        int cur_cls = -1, cur_slot = 0, loads[2] = {0, 0}, signalled = 0;
+        bool ok = true;
+        int4 item_n = nit > 0 ? items[i0] : make_int4(0, 0, 0, 0);
+        int src_n = (nit > 0 && pt < item_n.z) ? pc_src[item_n.y + pt] : -1;
+        for (int j = 0; j < nit && ok; j++) {
+            const int s = j % stages;
+            const int4 item = item_n;
+            const int src_j = src_n;
+            if (j + 1 < nit) item_n = items[i0 + j + 1];
+            if (item.x != cur_cls) {
+                const int o = (nslots == 2 && cur_cls >= 0) ? cur_slot ^ 1 : 0;
+                if ((o == 0 ? loads[0] : loads[1]) > 0) {
+                    // the slot is released by the MMA thread once the last run that
+                    // used it is issued: hand over every item gathered so far first
+                    cp_async_wait_group<0>();
+                    tc::fence_proxy_async();
+                    for (; signalled < j; signalled++) mbar_arrive(&full[signalled % stages]);
+                    const int n = o == 0 ? loads[0] : loads[1];
+                    if (!tc_wait(&opfree[o], (uint32_t)((n - 1) & 1), budget_ns, abort_p)) { ok = false; break; }
+                }
+                tc_load_operator(pt, Kp, item.x, ops, B_of(o));
+                if (o == 0) loads[0]++; else loads[1]++;
+                cur_cls = item.x;
+                cur_slot = o;
+            }
+            if (j >= stages && !tc_wait(&empty[s], (uint32_t)(((j / stages) - 1) & 1), budget_ns, abort_p)) {
+                ok = false;
+                break;
+            }
+            src_idx[s * TC_ROWS + pt] = src_j;
+            asm volatile("bar.sync 1, %0;" ::"n"(TC_PROD_THREADS) : "memory");
+            if (j + 1 < nit) src_n = pt < item_n.z ? pc_src[item_n.y + pt] : -1;
+            tc_gather(pt, Kp, cpr, src_idx + s * TC_ROWS, Ms, A_of(s), A_of(s) + abytes);
+            tc::cp_async_commit();
+            if (j - signalled >= D) {
+                if (D >= 3) cp_async_wait_group<3>();
+                else if (D == 2) cp_async_wait_group<2>();
+                else cp_async_wait_group<1>();
+                tc::fence_proxy_async();
+                for (; signalled <= j - D; signalled++) mbar_arrive(&full[signalled % stages]);
+            }
+        }
+        cp_async_wait_group<0>();
+        tc::fence_proxy_async();
+        if (ok)
+            for (; signalled < nit; signalled++) mbar_arrive(&full[signalled % stages]);
+    } else if (warp == TC_MMA_WARP) {
+        // ---------------- MMA issue (one thread)
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, Kp);
+            const uint32_t sbo = (Kp / 8) * 128;
+            int cur_cls = -1, cur_slot = 0, last_a = -1;
+            uint32_t last_parity = 0;
+            int cls_n = nit > 0 ? items[i0].x : -1;
+            for (int j = 0; j < nit; j++) {
+                const int s = j % stages, a = j % nacc;
+                const int4 item = make_int4(cls_n, 0, 0, 0);
+                cls_n = j + 1 < nit ? items[i0 + j + 1].x : -1;   // used after this item's MMAs
+                if (item.x != cur_cls) {
+                    cur_slot = (nslots == 2 && cur_cls >= 0) ? cur_slot ^ 1 : 0;
+                    cur_cls = item.x;
+                }
+                if (!tc_wait(&full[s], (uint32_t)((j / stages) & 1), budget_ns, abort_p)) break;
+                if (j >= nacc && !tc_wait(&acce[a], (uint32_t)(((j / nacc) - 1) & 1), budget_ns, abort_p)) break;
+                tc::fence_after_sync();
+                const uint32_t ah = tc::smem_u32(A_of(s)), al = ah + (uint32_t)abytes;
+                const uint32_t bh = tc::smem_u32(B_of(cur_slot)), bl = bh + (uint32_t)bbytes;
+                const uint32_t dacc = tbase + (uint32_t)(a * Kp);
+                for (int ks = 0; ks < Kp / 16; ks++) {
+                    const uint32_t o = ks * 256;
+                    const uint64_t dah = tc::make_desc(ah + o, 128, sbo), dal = tc::make_desc(al + o, 128, sbo);
+                    const uint64_t dbh = tc::make_desc(bh + o, 128, sbo), dbl = tc::make_desc(bl + o, 128, sbo);
+                    tc::mma_bf16(dacc, dah, dbh, idesc, ks > 0 ? 1u : 0u);
+                    tc::mma_bf16(dacc, dah, dbl, idesc, 1u);
+                    tc::mma_bf16(dacc, dal, dbh, idesc, 1u);
+                }
+                tc::commit(&empty[s]);
+                tc::commit(&accf[a]);
+                last_a = a;
+                last_parity = (uint32_t)((j / nacc) & 1);
+                if (j + 1 < nit && cls_n != item.x) tc::commit(&opfree[cur_slot]);
+            }
+            // every MMA issued here has completed before TMEM is released
+            if (last_a >= 0) {
+                volatile int never = 0;
+                tc_wait(&accf[last_a], last_parity, budget_ns, &never);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue
+        // the targets of item j+1 are loaded while item j is drained
+        const int quarter = warp & 3, part = warp >> 2, nblk = Kp / 16;
+        const int cb0 = nblk * part / 2, cb1 = nblk * (part + 1) / 2;
+        auto load_targets = [&](const int4 it, int (&tg)[2][2]) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int ra = 32 * quarter + 16 * h + (lane >> 2);
+                tg[h][0] = ra < it.z ? pc_tgt[it.y + ra] : -1;
+                tg[h][1] = ra + 8 < it.z ? pc_tgt[it.y + ra + 8] : -1;
+            }
+        };
+        int tgt[2][2], tgt_n[2][2];
+        int4 item_n = nit > 1 ? items[i0 + 1] : make_int4(0, 0, 0, 0);
+        if (nit > 0) load_targets(items[i0], tgt);
+        for (int j = 0; j < nit; j++) {
+            const int a = j % nacc;
+            if (j + 1 < nit) load_targets(item_n, tgt_n);
+            if (j + 2 < nit) item_n = items[i0 + j + 2];
+            const bool got = tc_wait(&accf[a], (uint32_t)((j / nacc) & 1), budget_ns, abort_p);
+            if (!__all_sync(0xffffffffu, got)) break;
+            tc::fence_after_sync();
+            tc_drain(tbase + (uint32_t)(a * Kp), quarter, cb0, cb1, ncols, ldL, tgt, L);
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[a]);
+#pragma unroll
+            for (int h = 0; h < 2; h++) { tgt[h][0] = tgt_n[h][0]; tgt[h][1] = tgt_n[h][1]; }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0 && abort_flag) atomicExch(status, 1);
+    if (warp == TC_MMA_WARP) tc::tmem_dealloc(tbase, TC_TMEM_COLS);
 }
 
 int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st) {
@@ -379,16 +590,28 @@ int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st) {
     const __nv_bfloat16* ops = (const __nv_bfloat16*)d.tc_ops;
     k_split_multipoles<<<nblk(ne, 256), 256, 0, st>>>(t->ncell, K2, KS, Kp, M, msplit);
     count_launch(t);
-    size_t smem = (size_t)2 * TC_ROWS * Kp * 2 + (size_t)2 * Kp * Kp * 2;
+    int dev = 0, optin = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    FMM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    FMM_CUDA_TRY(cudaFuncGetAttributes(&fa, k_m2l_tc));
+    const size_t cap = (size_t)optin - fa.sharedSizeBytes - 128;  // slack for the 128-byte alignment
+    const TcShape sh = tc_shape(Kp, cap);
+    if (sh.stages < 2 || sh.nacc < 2) {
+        fmm_set_error("tensor-core M2L: Kp = %d does not fit shared memory", Kp);
+        return FMM_ERR_ARG;
+    }
+    // at least half of the SM's shared memory, so that one block (and its 512
+    // TMEM columns) runs per SM
+    const size_t smem = std::max(sh.smem, (size_t)optin / 2 + 1024);
     FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = smem <= 100 * 1024 ? 2 : 1;
-    int grid = std::min<int64_t>(t->tc_nitems, (int64_t)per_sm * t->num_sms);
+    int grid = (int)std::min<int64_t>(t->tc_nitems, (int64_t)t->num_sms);
     int per_cta = (int)((t->tc_nitems + grid - 1) / grid);
     grid = (int)((t->tc_nitems + per_cta - 1) / per_cta);
-    const int ncol4 = (K2 + 3) / 4;
     stage_begin(t, FMM_STAGE_M2L_TC, st);
-    k_m2l_tc<<<grid, 128, smem, st>>>(Kp, ncol4, 2 * KS, (int)t->tc_nitems, per_cta, d.tc_items, d.tc_src,
-                                      d.tc_tgt, ops, msplit, L, d.status, t->prm.timeout_ns);
+    k_m2l_tc<<<grid, TC_THREADS, smem, st>>>(Kp, sh.stages, sh.nslots, sh.nacc, K2, 2 * KS, (int)t->tc_nitems,
+                                              per_cta, d.tc_items, d.tc_src, d.tc_tgt, ops, msplit, L, d.status,
+                                              t->prm.timeout_ns);
     count_launch(t);
     stage_end(t, FMM_STAGE_M2L_TC, st);
     FMM_CUDA_TRY(cudaGetLastError());

@@ -142,6 +142,69 @@ __device__ void shift_cell(int p, int c, int kind, int lane, const int32_t* __re
     }
 }
 
+// Block version for the stage-by-stage kernels: NW warps share one destination
+// cell and split its inputs (M2M: warp w takes child w; L2L: warp w takes a
+// slice of the parent's coefficients), so the chain of dependent operator-row
+// loads per warp is NW times shorter; partial sums meet in shared memory.
+// red: NW * K2 entries; xin: NW * K2 entries.
+template <typename T, int RQ, int NW>
+__device__ void shift_cell_block(int p, int c, int kind, const int32_t* __restrict__ child_first,
+                                 const int32_t* __restrict__ child_count, const int32_t* __restrict__ parent,
+                                 const uint64_t* __restrict__ ckey, const T* __restrict__ ops, cplx<T>* E, T* xin,
+                                 T* red) {
+    const int K2 = 2 * ntri(p), ld = 2 * kstride(p);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* Ef = reinterpret_cast<T*>(E);
+    T* xw = xin + warp * K2;
+    T acc[RQ];
+#pragma unroll
+    for (int q = 0; q < RQ; q++) acc[q] = T(0);
+    int s = -1, i_lo = 0, i_hi = K2;
+    if (kind == 0) {
+        if (warp < child_count[c]) s = child_first[c] + warp;
+    } else {
+        s = parent[c];
+        const int per = (K2 + NW - 1) / NW;
+        i_lo = min(K2, warp * per);
+        i_hi = min(K2, i_lo + per);
+    }
+    if (s >= 0 && i_hi > i_lo) {
+        const int oct = (int)(ckey[kind == 0 ? s : c] & 7);
+        const T* op = ops + (size_t)(kind * 8 + oct) * K2 * K2;
+        for (int j = lane; j < K2; j += 32) xw[j] = Ef[(size_t)s * ld + j];
+        __syncwarp();
+        for (int i0 = i_lo; i0 < i_hi; i0 += 8) {
+            T w[8][RQ];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const T* row = op + (size_t)min(i0 + u, K2 - 1) * K2;
+#pragma unroll
+                for (int q = 0; q < RQ; q++) {
+                    const int j = lane + 32 * q;
+                    w[u][q] = j < K2 ? __ldg(row + j) : T(0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const T x = (i0 + u < i_hi) ? xw[i0 + u] : T(0);
+#pragma unroll
+                for (int q = 0; q < RQ; q++) acc[q] = fma(w[u][q], x, acc[q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RQ; q++) {
+        const int j = lane + 32 * q;
+        if (j < K2) red[warp * K2 + j] = acc[q];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < K2; j += 32 * NW) {
+        T v = kind == 0 ? T(0) : Ef[(size_t)c * ld + j];
+        for (int w = 0; w < NW; w++) v += red[w * K2 + j];
+        Ef[(size_t)c * ld + j] = v;
+    }
+}
+
 // ---------------------------------------------------------------- M2L
 // One source slot (a half-warp) accumulates, into acc[r], the outputs
 // j = hl + 16 r of target t over the sources e = s0 + slot, s0 + slot + nslot, ...
@@ -238,7 +301,17 @@ __device__ __forceinline__ float4 shift_src(float4 v, Offset3<float> o) {
     return make_float4(v.x + o.x, v.y + o.y, v.z + o.z, v.w);
 }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
-__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+// FP32: the hardware reciprocal square root (PTX rsqrt.approx.ftz.f32, relative
+// error below 2^-22.9), one MUFU instruction per pair interaction
+__device__ __forceinline__ float rsqrt_t(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// a pair closer than this is treated as coincident (the FP32 reciprocal square
+// root flushes subnormal inputs)
+__device__ __forceinline__ double pair_floor(double) { return 0.0; }
+__device__ __forceinline__ float pair_floor(float) { return 1.17549435e-38f; }
 
 constexpr int P2P_THREADS = 128;
 constexpr int P2P_BUF = 1024;
@@ -248,7 +321,7 @@ __device__ __forceinline__ void p2p_pair(const typename Vec4<T>::type& me, const
                                          T& gx, T& gy, T& gz) {
     const T dx = me.x - s.x, dy = me.y - s.y, dz = me.z - s.z;
     const T r2 = dx * dx + dy * dy + dz * dz;
-    const T rinv = r2 > T(0) ? rsqrt_t(r2) : T(0);
+    const T rinv = r2 > pair_floor(r2) ? rsqrt_t(r2) : T(0);
     const T qr = s.w * rinv;
     phi += qr;
     const T qr3 = qr * rinv * rinv;
@@ -258,8 +331,9 @@ __device__ __forceinline__ void p2p_pair(const typename Vec4<T>::type& me, const
 // One block of P2P_THREADS threads, target leaf c.  The target's sources are
 // one concatenated particle stream (each P2P record gives a source leaf's
 // offset in it), staged P2P_BUF at a time, the four warps copying different
-// source leaves.  Thread t works on target (t mod nt) over the staged sources
-// j = (t / nt) (mod G), G = 128 / nt streams, so small leaves fill the block.
+// source leaves.  Each thread holds two targets, so one staged source feeds two
+// pair interactions: thread t works on targets 2u, 2u+1 (u = t mod nu, nu =
+// ceil(nt/2)) over the staged sources j = (t / nu) (mod G), G = 128 / nu.
 template <typename T>
 __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t* __restrict__ count,
                          const int64_t* __restrict__ start, const int4* __restrict__ rec,
@@ -274,13 +348,16 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
     if (s1 > s0) { const int4 r = rec[s1 - 1]; total = r.z + r.y; }
     const int4 ict = icentre[c];
     const float u2f = cu2f[c];   // side/2^22 of the target's system (sources share it)
-    for (int tb = 0; tb < nt; tb += P2P_THREADS) {
-        const int ntc = min(P2P_THREADS, nt - tb);
-        const int G = P2P_THREADS / ntc;
-        const int ti = threadIdx.x % ntc, sub = threadIdx.x / ntc;
+    for (int tb = 0; tb < nt; tb += 2 * P2P_THREADS) {
+        const int ntc = min(2 * P2P_THREADS, nt - tb);
+        const int nu = (ntc + 1) >> 1;
+        const int G = P2P_THREADS / nu;
+        const int u = threadIdx.x % nu, sub = threadIdx.x / nu;
         const bool active = sub < G;
-        const V me = xq[tf + tb + ti];
-        T phi = 0, gx = 0, gy = 0, gz = 0;
+        const bool two = 2 * u + 1 < ntc;
+        const V me0 = xq[tf + tb + 2 * u];
+        const V me1 = two ? xq[tf + tb + 2 * u + 1] : me0;
+        T p0 = 0, x0 = 0, y0 = 0, z0 = 0, p1 = 0, x1 = 0, y1 = 0, z1 = 0;
         int64_t e_lo = s0;
         for (int base = 0; base < total; base += P2P_BUF) {
             const int lim = min(P2P_BUF, total - base);
@@ -301,14 +378,18 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
             __syncthreads();
             if (active) {
                 int j = sub;
-                for (; j + 3 * G < lim; j += 4 * G) {
-                    const V a = buf[j], b = buf[j + G], cc = buf[j + 2 * G], d = buf[j + 3 * G];
-                    p2p_pair<T>(me, a, phi, gx, gy, gz);
-                    p2p_pair<T>(me, b, phi, gx, gy, gz);
-                    p2p_pair<T>(me, cc, phi, gx, gy, gz);
-                    p2p_pair<T>(me, d, phi, gx, gy, gz);
+                for (; j + G < lim; j += 2 * G) {
+                    const V a = buf[j], bb = buf[j + G];
+                    p2p_pair<T>(me0, a, p0, x0, y0, z0);
+                    p2p_pair<T>(me1, a, p1, x1, y1, z1);
+                    p2p_pair<T>(me0, bb, p0, x0, y0, z0);
+                    p2p_pair<T>(me1, bb, p1, x1, y1, z1);
                 }
-                for (; j < lim; j += G) p2p_pair<T>(me, buf[j], phi, gx, gy, gz);
+                if (j < lim) {
+                    const V a = buf[j];
+                    p2p_pair<T>(me0, a, p0, x0, y0, z0);
+                    p2p_pair<T>(me1, a, p1, x1, y1, z1);
+                }
             }
             __syncthreads();
             while (e_lo < s1) {
@@ -317,19 +398,23 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
                 e_lo++;
             }
         }
-        part[threadIdx.x][0] = phi; part[threadIdx.x][1] = gx; part[threadIdx.x][2] = gy; part[threadIdx.x][3] = gz;
-        __syncthreads();
-        if (threadIdx.x < ntc) {
-            T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-            for (int q = 0; q < G; q++) {
-                const int k = q * ntc + threadIdx.x;
-                a0 += part[k][0]; a1 += part[k][1]; a2 += part[k][2]; a3 += part[k][3];
+        // partial sums of the two targets, reduced over the G source streams
+        for (int h = 0; h < 2; h++) {
+            part[threadIdx.x][0] = h ? p1 : p0; part[threadIdx.x][1] = h ? x1 : x0;
+            part[threadIdx.x][2] = h ? y1 : y0; part[threadIdx.x][3] = h ? z1 : z0;
+            __syncthreads();
+            if (threadIdx.x < nu && 2 * threadIdx.x + h < ntc) {
+                T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+                for (int q = 0; q < G; q++) {
+                    const int k = q * nu + threadIdx.x;
+                    a0 += part[k][0]; a1 += part[k][1]; a2 += part[k][2]; a3 += part[k][3];
+                }
+                const int64_t i = tf + tb + 2 * threadIdx.x + h;
+                near[4 * i] = (double)a0; near[4 * i + 1] = (double)a1; near[4 * i + 2] = (double)a2;
+                near[4 * i + 3] = (double)a3;
             }
-            const int64_t i = tf + tb + threadIdx.x;
-            near[4 * i] = (double)a0; near[4 * i + 1] = (double)a1; near[4 * i + 2] = (double)a2;
-            near[4 * i + 3] = (double)a3;
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 

@@ -85,6 +85,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// whole warp, shape 16x256b repeated twice: 16 TMEM lanes starting at the
+// address's lane field, 16 columns.  Thread t holds lane t/4 in v[0..1] and
+// v[4..5] and lane t/4 + 8 in v[2..3] and v[6..7]; v[4k + j] sits at column
+// 8k + 2 (t % 4) + (j & 1).  Four consecutive threads thus hold 8 consecutive
+// columns of one lane.
+__device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+
 // mbarrier helpers
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");

@@ -6,6 +6,7 @@
 // contraction), the acceptance test compares an exact integer with one FP64
 // product, and the lists are put in canonical (target, source) order by a
 // radix sort.
+#include <cooperative_groups.h>
 #include <cub/cub.cuh>
 #include <cuda_bf16.h>
 
@@ -360,23 +361,112 @@ __global__ void k_traverse(const int2* __restrict__ front, int64_t nf, const int
     }
 }
 
-__global__ void k_pack_pairs(const int2* pr, int64_t np, uint64_t* key) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < np) key[i] = ((uint64_t)(uint32_t)pr[i].x << 32) | (uint32_t)pr[i].y;
+// (target, source) packed as target * 2^B + source, B = bits of the cell count,
+// so the sort touches 2B bits
+// All rounds of the breadth-first traversal in one cooperative launch: the
+// blocks process the current frontier, meet at a grid-wide barrier, swap the
+// frontier buffers and go on until the frontier is empty.  Writes are checked
+// against the buffer capacities; on overflow the kernel stops and reports it,
+// and the host reruns the traversal round by round with growing buffers.
+struct TravState {
+    unsigned long long nf, nnext, nm2l, np2p;
+    int overflow, rounds;
+};
+
+__device__ __forceinline__ void traverse_pair(int ci, int cj, bool valid, const int32_t* __restrict__ lev,
+                                              const uint64_t* __restrict__ ckey,
+                                              const int32_t* __restrict__ child_first,
+                                              const int32_t* __restrict__ child_count, double th2, int2* m2l,
+                                              int2* p2p, int2* next, TravState* stt, unsigned long long cap_m,
+                                              unsigned long long cap_p, unsigned long long cap_f) {
+    int action = -1, nsplit = 0, split_target = 0;
+    if (valid) {
+        int li = lev[ci], lj = lev[cj];
+        int64_t si = (int64_t)1 << (FMM_MAX_LEVEL - li), sj = (int64_t)1 << (FMM_MAX_LEVEL - lj);
+        uint64_t ki = ckey[ci], kj = ckey[cj];
+        int64_t D2 = 0;
+        for (int d = 0; d < 3; d++) {
+            int64_t a = 2 * compact3(ki >> d) * si + si;
+            int64_t b = 2 * compact3(kj >> d) * sj + sj;
+            D2 += (a - b) * (a - b);
+        }
+        int64_t S = si + sj;
+        bool accept = (double)(S * S) < __dmul_rn(th2, (double)D2);
+        bool leaf_i = child_count[ci] == 0, leaf_j = child_count[cj] == 0;
+        if (accept) action = 0;
+        else if (leaf_i && leaf_j) action = 1;
+        else {
+            action = 2;
+            split_target = leaf_j || (!leaf_i && li <= lj);
+            nsplit = split_target ? child_count[ci] : child_count[cj];
+        }
+    }
+    unsigned long long s0 = warp_reserve(&stt->nm2l, action == 0 ? 1u : 0u);
+    unsigned long long s1 = warp_reserve(&stt->np2p, action == 1 ? 1u : 0u);
+    unsigned long long s2 = warp_reserve(&stt->nnext, (unsigned)nsplit);
+    if (action == 0) {
+        if (s0 < cap_m) m2l[s0] = make_int2(ci, cj); else stt->overflow = 1;
+    } else if (action == 1) {
+        if (s1 < cap_p) p2p[s1] = make_int2(ci, cj); else stt->overflow = 1;
+    } else if (action == 2) {
+        if (s2 + nsplit > cap_f) { stt->overflow = 1; return; }
+        if (split_target) {
+            int cf = child_first[ci];
+            for (int k = 0; k < nsplit; k++) next[s2 + k] = make_int2(cf + k, cj);
+        } else {
+            int cf = child_first[cj];
+            for (int k = 0; k < nsplit; k++) next[s2 + k] = make_int2(ci, cf + k);
+        }
+    }
 }
 
-__global__ void k_unpack_sources(const uint64_t* key, int64_t np, int32_t* src, int32_t* tgt) {
+__global__ void k_traverse_coop(int2* fa, int2* fb, const int32_t* __restrict__ lev, const uint64_t* __restrict__ ckey,
+                                const int32_t* __restrict__ child_first, const int32_t* __restrict__ child_count,
+                                double th2, int2* m2l, int2* p2p, TravState* stt, unsigned long long cap_m,
+                                unsigned long long cap_p, unsigned long long cap_f) {
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long gtid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long wbase = gtid & ~31ull;   // first index of this thread's warp
+    for (int round = 0;; round++) {
+        int2* cur = (round & 1) ? fb : fa;
+        int2* nxt = (round & 1) ? fa : fb;
+        const unsigned long long nf = *(volatile unsigned long long*)&stt->nf;
+        if (nf == 0 || *(volatile int*)&stt->overflow) break;
+        for (unsigned long long base = wbase; base < nf; base += nthreads) {
+            const unsigned long long i = base + (threadIdx.x & 31);
+            const bool valid = i < nf;
+            const int2 pr = valid ? cur[i] : make_int2(0, 0);
+            traverse_pair(pr.x, pr.y, valid, lev, ckey, child_first, child_count, th2, m2l, p2p, nxt, stt, cap_m,
+                          cap_p, cap_f);
+        }
+        grid.sync();
+        if (gtid == 0) {
+            stt->nf = stt->nnext;
+            stt->nnext = 0;
+            stt->rounds = round + 1;
+        }
+        grid.sync();
+    }
+}
+
+__global__ void k_pack_pairs(const int2* pr, int64_t np, int B, uint64_t* key) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < np) key[i] = ((uint64_t)(uint32_t)pr[i].x << B) | (uint32_t)pr[i].y;
+}
+
+__global__ void k_unpack_sources(const uint64_t* key, int64_t np, int B, int32_t* src, int32_t* tgt) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= np) return;
-    src[i] = (int32_t)(key[i] & 0xffffffffull);
-    if (tgt) tgt[i] = (int32_t)(key[i] >> 32);
+    src[i] = (int32_t)(key[i] & ((1ull << B) - 1ull));
+    if (tgt) tgt[i] = (int32_t)(key[i] >> B);
 }
 
 // start[c] = first list entry whose target is >= c, for c = 0..ncell
-__global__ void k_csr_start(const uint64_t* key, int64_t np, int ncell, int64_t* start) {
+__global__ void k_csr_start(const uint64_t* key, int64_t np, int ncell, int B, int64_t* start) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c > ncell) return;
-    uint64_t lim = (uint64_t)c << 32;
+    uint64_t lim = (uint64_t)c << B;
     int64_t a = 0, b = np;
     while (a < b) {
         int64_t mid = (a + b) >> 1;
@@ -428,9 +518,10 @@ static int finish_list(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, in
     uint64_t *k0 = nullptr, *k1 = nullptr;
     if ((rc = dev_alloc(&k0, np, nullptr, st))) return rc;
     if ((rc = dev_alloc(&k1, np, nullptr, st))) return rc;
-    if (np) { k_pack_pairs<<<nblk(np, 256), 256, 0, st>>>(pairs, np, k0); count_launch(t); }
+    const int B = bits_for(t->ncell);
+    if (np) { k_pack_pairs<<<nblk(np, 256), 256, 0, st>>>(pairs, np, B, k0); count_launch(t); }
     size_t tmp_bytes = 0;
-    int end_bit = 32 + bits_for(t->ncell);
+    int end_bit = 2 * B;
     cub::DeviceRadixSort::SortKeys(nullptr, tmp_bytes, k0, k1, (int64_t)np, 0, end_bit, st);
     char* tmp = nullptr;
     if ((rc = dev_alloc(&tmp, tmp_bytes, nullptr, st))) return rc;
@@ -438,8 +529,8 @@ static int finish_list(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, in
     if ((rc = dev_alloc(src, np, t, st))) return rc;
     if ((rc = dev_alloc(start, (size_t)t->ncell + 1, t, st))) return rc;
     if (tgt && (rc = dev_alloc(tgt, np, t, st))) return rc;
-    if (np) { k_unpack_sources<<<nblk(np, 256), 256, 0, st>>>(k1, np, *src, tgt ? *tgt : nullptr); count_launch(t); }
-    k_csr_start<<<nblk(t->ncell + 1, 256), 256, 0, st>>>(k1, np, t->ncell, *start);
+    if (np) { k_unpack_sources<<<nblk(np, 256), 256, 0, st>>>(k1, np, B, *src, tgt ? *tgt : nullptr); count_launch(t); }
+    k_csr_start<<<nblk(t->ncell + 1, 256), 256, 0, st>>>(k1, np, t->ncell, B, *start);
     count_launch(t);
     dev_free(tmp, st);
     dev_free(k0, st);
@@ -674,6 +765,47 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     count_launch(t);
     int64_t nf = nsys, nm = 0, npp = 0;
     const double th2 = t->prm.theta * t->prm.theta;
+    {
+        // one cooperative launch for every round, with buffers sized from the
+        // cell count; the round-by-round loop below runs only on overflow
+        const size_t nc0 = (size_t)t->ncell;
+        const size_t cf = std::max<size_t>(1 << 20, 96 * nc0), cm = std::max<size_t>(1 << 22, 640 * nc0),
+                     cp = std::max<size_t>(1 << 20, 160 * nc0);
+        int2 *fa = nullptr, *fb = nullptr, *mm = nullptr, *pp = nullptr;
+        TravState* stt = nullptr;
+        bool ok = dev_alloc(&fa, cf, nullptr, st) == FMM_OK && dev_alloc(&fb, cf, nullptr, st) == FMM_OK &&
+                  dev_alloc(&mm, cm, nullptr, st) == FMM_OK && dev_alloc(&pp, cp, nullptr, st) == FMM_OK &&
+                  dev_alloc((char**)&stt, sizeof(TravState), nullptr, st) == FMM_OK;
+        int per_sm = 0;
+        if (ok) ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_coop, 256, 0) == cudaSuccess &&
+                     per_sm > 0;
+        if (ok) {
+            TravState h0 = {(unsigned long long)nsys, 0ull, 0ull, 0ull, 0, 0};
+            FMM_CUDA_TRY(cudaMemcpyAsync(stt, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+            k_init_frontier<<<nblk(nsys, 128), 128, 0, st>>>(nsys, fa);
+            unsigned long long a_cm = cm, a_cp = cp, a_cf = cf;
+            int32_t *a_lev = d.level, *a_cfirst = d.child_first, *a_ccount = d.child_count;
+            uint64_t* a_ckey = d.ckey;
+            double a_th2 = th2;
+            void* args[] = {&fa, &fb, &a_lev, &a_ckey, &a_cfirst, &a_ccount, &a_th2, &mm, &pp, &stt, &a_cm, &a_cp, &a_cf};
+            dim3 grid(per_sm * t->num_sms), block(256);
+            FMM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_traverse_coop, grid, block, args, 0, st));
+            count_launch(t, 2);
+            TravState h;
+            FMM_CUDA_TRY(cudaMemcpyAsync(&h, stt, sizeof(h), cudaMemcpyDeviceToHost, st));
+            FMM_CUDA_TRY(cudaStreamSynchronize(st));
+            if (!h.overflow) {
+                dev_free(m2l, st); dev_free(p2p, st);
+                m2l = mm; p2p = pp; c_m = cm; c_p = cp;
+                mm = pp = nullptr;
+                nm = (int64_t)h.nm2l;
+                npp = (int64_t)h.np2p;
+                nf = 0;   // done
+            }
+        }
+        dev_free(fa, st); dev_free(fb, st); dev_free(mm, st); dev_free(pp, st);
+        if (stt) cudaFreeAsync(stt, st);
+    }
     while (nf > 0) {
         if ((rc = grow(next, c_next, (size_t)nf * 8, 0, st))) return rc;
         if ((rc = grow(m2l, c_m, (size_t)(nm + nf), (size_t)nm, st))) return rc;
@@ -695,7 +827,13 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     t->nm2l = nm;
     t->np2p = npp;
     const bool want_classes = t->prm.precision == FMM_PREC_MIXED_TC && tc_supported(t->prm.p);
-    if ((rc = finish_list(t, m2l, nm, &d.m2l_start, &d.m2l_src, want_classes ? &d.m2l_tgt : nullptr, st))) return rc;
+    // with the tensor cores the M2L pairs are grouped by class straight from the
+    // traversal output; no (target, source) order is needed on that path
+    if (want_classes) {
+        if ((rc = build_m2l_classes(t, m2l, st))) return rc;
+    } else if ((rc = finish_list(t, m2l, nm, &d.m2l_start, &d.m2l_src, nullptr, st))) {
+        return rc;
+    }
     int32_t* p2p_tgt = nullptr;
     if ((rc = finish_list(t, p2p, npp, &d.p2p_start, &d.p2p_src, &p2p_tgt, st))) return rc;
     {
@@ -717,10 +855,6 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         dev_free(cnt, st); dev_free(gcum, st); dev_free(p2p_tgt, st);
     }
     dev_free(m2l, st); dev_free(p2p, st);
-    if (want_classes) {
-        if ((rc = build_m2l_classes(t, st))) return rc;
-        dev_free(d.m2l_tgt, st);
-    }
     if (queue_supported(t) && (rc = build_queue(t, st))) return rc;
     stage_end(t, FMM_STAGE_LISTS, st);
     FMM_CUDA_TRY(cudaGetLastError());
