@@ -103,6 +103,21 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev);
     }
+    if (t->n > 0 && (!fmm::queue_supported(t))) {
+        // the stage-by-stage path runs P2P (and, at build time, the tensor-core
+        // class operators) on a second stream, non-blocking with respect to the
+        // legacy stream and joined by events
+        if (cudaStreamCreateWithFlags(&t->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&t->ev_ops, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (t->side_stream) cudaStreamDestroy(t->side_stream);
+            if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+            if (t->ev_join) cudaEventDestroy(t->ev_join);
+            t->side_stream = nullptr; t->ev_fork = nullptr; t->ev_join = nullptr; t->ev_ops = nullptr;
+        }
+    }
     rc = fmm::build_tree_impl(t, pos, pos_dtype, st);
     if (!rc) rc = fmm::alloc_eval_workspace(t, st);
     if (!rc) {
@@ -111,24 +126,17 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
     }
     if (rc) {
         cudaStreamSynchronize(st);
+        if (t->side_stream) cudaStreamSynchronize(t->side_stream);
         fmm::free_tree_device(t);
         if (t->timing) for (int i = 0; i < 2 * FMM_NUM_STAGES; i++) cudaEventDestroy(t->ev[i]);
+        if (t->side_stream) cudaStreamDestroy(t->side_stream);
+        if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+        if (t->ev_join) cudaEventDestroy(t->ev_join);
+        if (t->ev_ops) cudaEventDestroy(t->ev_ops);
         delete t;
         return rc;
     }
     t->launch_ctr = nullptr;
-    if (t->n > 0 && (!fmm::queue_supported(t))) {
-        // the stage-by-stage path runs P2P on a second stream (non-blocking with
-        // respect to the legacy stream; joined by events inside each evaluation)
-        if (cudaStreamCreateWithFlags(&t->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            if (t->side_stream) cudaStreamDestroy(t->side_stream);
-            if (t->ev_fork) cudaEventDestroy(t->ev_fork);
-            t->side_stream = nullptr; t->ev_fork = nullptr; t->ev_join = nullptr;
-        }
-    }
     *out = t;
     return FMM_OK;
 }
@@ -322,12 +330,14 @@ int fmm_status(fmm_tree* t) {
 void fmm_tree_destroy(fmm_tree* t) {
     if (!t) return;
     cudaDeviceSynchronize();
+    if (t->side_stream) cudaStreamSynchronize(t->side_stream);
     fmm::free_tree_device(t);
     cudaStreamSynchronize(0);
     if (t->timing) for (int i = 0; i < 2 * FMM_NUM_STAGES; i++) cudaEventDestroy(t->ev[i]);
     if (t->side_stream) cudaStreamDestroy(t->side_stream);
     if (t->ev_fork) cudaEventDestroy(t->ev_fork);
     if (t->ev_join) cudaEventDestroy(t->ev_join);
+    if (t->ev_ops) cudaEventDestroy(t->ev_ops);
     delete t;
 }
 

@@ -154,6 +154,7 @@ struct TreeDev {
     // tensor-core M2L (FMM_PREC_MIXED_TC): pairs grouped by translation class
     int4* tc_items = nullptr;     // [tc_nitems] (class, first pair, rows, -)
     void* tc_ops = nullptr;       // [nclass][hi|lo][Kp x Kp] bf16 operators
+    uint64_t* tc_keys = nullptr;  // [nclass] class keys, in class order
     int32_t* tc_tgt = nullptr;    // [nm2l] targets in class order (class-less pairs last)
     int32_t* tc_src = nullptr;
     int64_t* rem_start = nullptr; // CSR of the class-less pairs by target
@@ -191,6 +192,9 @@ struct fmm_tree {
     // second stream of the stage-by-stage evaluation (P2P beside the far field)
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // recorded on side_stream after the tensor-core class operators are built
+    // (they are computed there, overlapping the rest of the build)
+    cudaEvent_t ev_ops = nullptr;
     int64_t* launch_ctr = nullptr;  // which counter launches currently go to
     int64_t n = 0;
     int ncell = 0, nlevel = 0, nleaf = 0;

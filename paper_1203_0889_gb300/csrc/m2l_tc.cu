@@ -44,24 +44,29 @@ bool tc_supported(int p) { return tc_kpad(p) <= 144; }
 // build: class keys, grouping, operators, work items
 // ---------------------------------------------------------------------------
 
-__global__ void k_class_keys(int64_t np, const int2* __restrict__ pairs, const int4* __restrict__ icentre,
-                             uint64_t* keys, int32_t* idx) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= np) return;
-    const int2 pr = pairs[e];
-    int4 a = icentre[pr.x], b = icentre[pr.y];
-    int dl = a.w - b.w;
+// class key of an M2L pair (target, source); NOT_TC | target when the pair
+// has no class
+__device__ __forceinline__ uint64_t pair_class_key(const int2 pr, const int4* __restrict__ icentre) {
+    const int4 a = icentre[pr.x], b = icentre[pr.y];
+    const int dl = a.w - b.w;
     uint64_t key = NOT_TC | (uint64_t)(uint32_t)pr.x;
     if (dl <= TC_MAX_DL && dl >= -TC_MAX_DL) {
-        int64_t mn = (int64_t)1 << (FMM_MAX_LEVEL - max(a.w, b.w));  // side of the smaller cell, units u
-        int64_t v[3] = {((int64_t)a.x - b.x) / mn, ((int64_t)a.y - b.y) / mn, ((int64_t)a.z - b.z) / mn};
+        const int64_t mn = (int64_t)1 << (FMM_MAX_LEVEL - max(a.w, b.w));  // side of the smaller cell, units u
+        const int64_t v[3] = {((int64_t)a.x - b.x) / mn, ((int64_t)a.y - b.y) / mn, ((int64_t)a.z - b.z) / mn};
         bool fits = true;
         for (int d = 0; d < 3; d++) fits = fits && v[d] > -32768 && v[d] < 32768;
         if (fits)
             key = ((uint64_t)(dl + 16) << 48) | ((uint64_t)(v[0] + 32768) << 32) | ((uint64_t)(v[1] + 32768) << 16) |
                   (uint64_t)(v[2] + 32768);
     }
-    keys[e] = key;
+    return key;
+}
+
+__global__ void k_class_keys(int64_t np, const int2* __restrict__ pairs, const int4* __restrict__ icentre,
+                             uint64_t* keys, int32_t* idx) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= np) return;
+    keys[e] = pair_class_key(pairs[e], icentre);
     idx[e] = (int32_t)e;
 }
 
@@ -107,6 +112,97 @@ __global__ void k_csr_from_targets(const int32_t* tgt, int64_t np, int ncell, in
         if (tgt[mid] < c) a = mid + 1; else b = mid;
     }
     start[c] = a;
+}
+
+// ---- grouping by hashing: class key -> slot of an open-addressing table;
+// sorting the (few) occupied slots numbers the classes in key order, and a
+// stable sort of the pairs on these short class ids groups them.
+constexpr int CLASS_HASH_BITS = 18;
+constexpr int CLASS_HASH_PROBES = 256;
+constexpr uint64_t HASH_EMPTY = ~0ull;
+
+__device__ __forceinline__ uint32_t class_hash(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return (uint32_t)k;
+}
+
+// ctr[0]: pairs without a class, ctr[1]: probe limit reached
+__global__ void k_class_hash(int64_t np, const int2* __restrict__ pairs, const int4* __restrict__ icentre,
+                             uint64_t* table, uint32_t mask, int32_t* slot_of, unsigned long long* ctr) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int slot = -2;  // -2: no pair, -1: pair without a class
+    if (e < np) {
+        const uint64_t key = pair_class_key(pairs[e], icentre);
+        slot = -1;
+        if (!(key & NOT_TC)) {
+            uint32_t h = class_hash(key) & mask;
+            for (int probe = 0; probe < CLASS_HASH_PROBES; probe++) {
+                uint64_t cur = table[h];
+                if (cur == HASH_EMPTY) {
+                    cur = atomicCAS(reinterpret_cast<unsigned long long*>(table + h), HASH_EMPTY, key);
+                    if (cur == HASH_EMPTY) cur = key;
+                }
+                if (cur == key) { slot = (int)h; break; }
+                h = (h + 1) & mask;
+            }
+            if (slot < 0) atomicExch(&ctr[1], 1ull);
+        }
+        slot_of[e] = slot;
+    }
+    const unsigned rem = __ballot_sync(0xffffffffu, slot == -1);
+    if ((threadIdx.x & 31) == 0 && rem) atomicAdd(&ctr[0], (unsigned long long)__popc(rem));
+}
+
+// class c = rank of its key among the occupied slots
+__global__ void k_number_classes(int nclass, const int32_t* __restrict__ sorted_slot, int32_t* class_of_slot) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < nclass) class_of_slot[sorted_slot[c]] = c;
+}
+
+// sort keys of the pairs: their class, nclass for a pair without one
+__global__ void k_class_ids(int64_t np, const int32_t* __restrict__ slot_of, const int32_t* __restrict__ class_of_slot,
+                            int nclass, int32_t* cid, int32_t* idx) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= np) return;
+    const int sl = slot_of[e];
+    cid[e] = sl >= 0 ? class_of_slot[sl] : nclass;
+    idx[e] = (int32_t)e;
+}
+
+// sizes of the classes from the sorted ids: counts[c] for c < nclass, and
+// counts[nclass] = the first pair without a class
+__global__ void k_class_bounds(int nclass, const int32_t* __restrict__ cid, int64_t np, int32_t* counts) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > nclass) return;
+    auto lower = [&](int v) {
+        int64_t a = 0, b = np;
+        while (a < b) {
+            const int64_t m = (a + b) >> 1;
+            if (cid[m] < v) a = m + 1; else b = m;
+        }
+        return a;
+    };
+    const int64_t lo = lower(c);
+    counts[c] = c < nclass ? (int32_t)(lower(c + 1) - lo) : (int32_t)lo;
+}
+
+__global__ void k_iota32(int n, int32_t* v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = i;
+}
+
+// remainder pairs (no class) as (target << 32 | source) keys and back
+__global__ void k_pack_rem(int64_t n, const int32_t* tg, const int32_t* sr, uint64_t* k) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) k[i] = ((uint64_t)(uint32_t)tg[i] << 32) | (uint32_t)sr[i];
+}
+__global__ void k_unpack_rem(int64_t n, const uint64_t* k, int32_t* tg, int32_t* sr) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) { tg[i] = (int32_t)(k[i] >> 32); sr[i] = (int32_t)(k[i] & 0xffffffffu); }
 }
 
 // Operator of one class, split into bf16 hi/lo, K-major core-matrix layout:
@@ -178,11 +274,180 @@ __global__ void k_class_operators(int p, int Kp, const uint64_t* __restrict__ uk
     }
 }
 
+// Work items and operators of nclass classes with sizes counts[] and keys
+// ukeys[] (both in class order); cfirst[c] receives the first pair of class c.
+static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const int32_t* counts, int32_t* cfirst,
+                        int64_t* items_out, cudaStream_t st) {
+    TreeDev& d = t->d;
+    int rc;
+    const int p = t->prm.p, Kp = tc_kpad(p);
+    *items_out = 0;
+    if (nclass == 0) return FMM_OK;
+    int32_t *tiles = nullptr, *tfirst = nullptr;
+    if ((rc = dev_alloc(&tiles, (size_t)nclass + 1, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&tfirst, (size_t)nclass + 1, nullptr, st))) return rc;
+    size_t tb = 0;
+    char* tmp = nullptr;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb, counts, cfirst, nclass, st);
+    if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
+    FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, counts, cfirst, nclass, st));
+    k_class_tiles<<<nblk(nclass, 256), 256, 0, st>>>(nclass, counts, tiles);
+    FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, tiles, tfirst, nclass, st));
+    count_launch(t, 3);
+    cudaFreeAsync(tmp, st);
+    int32_t lt = 0, lf = 0;
+    FMM_CUDA_TRY(cudaMemcpyAsync(&lt, tiles + nclass - 1, 4, cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(&lf, tfirst + nclass - 1, 4, cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    const int64_t h_items = (int64_t)lt + lf;
+    if ((rc = dev_alloc(&d.tc_items, (size_t)h_items, t, st))) return rc;
+    k_emit_items<<<nblk(nclass, 256), 256, 0, st>>>(nclass, counts, cfirst, tfirst, d.tc_items);
+    count_launch(t);
+    // operators: on the side stream, so that they overlap the rest of the
+    // build and the upward pass; the tensor-core M2L waits for ev_ops
+    size_t ob = (size_t)nclass * 2 * Kp * Kp;
+    __nv_bfloat16* ops = nullptr;
+    if ((rc = dev_alloc(&ops, ob, t, st))) return rc;
+    d.tc_ops = ops;
+    if ((rc = dev_alloc(&d.tc_keys, (size_t)nclass, t, st))) return rc;
+    FMM_CUDA_TRY(cudaMemcpyAsync(d.tc_keys, ukeys, sizeof(uint64_t) * nclass, cudaMemcpyDeviceToDevice, st));
+    cudaStream_t so = st;
+    if (t->side_stream && t->ev_ops) {
+        so = t->side_stream;
+        FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(so, t->ev_fork, 0));
+    }
+    size_t smem = ntri(2 * p) * (sizeof(cplx<double>) + sizeof(cplx<float>)) + 32 * 4 + 512;
+    k_class_operators<<<nclass, 256, smem, so>>>(p, Kp, d.tc_keys, ops);
+    count_launch(t);
+    FMM_CUDA_TRY(cudaGetLastError());
+    if (so != st) FMM_CUDA_TRY(cudaEventRecord(t->ev_ops, so));
+    cudaFreeAsync(tiles, st);
+    cudaFreeAsync(tfirst, st);
+    *items_out = h_items;
+    return FMM_OK;
+}
+
+// The pairs without a class, tc_tgt/tc_src[ntc, np), sorted by (target,
+// source), and their CSR by target for the CUDA-core kernel.
+static int finish_remainder(fmm_tree* t, int64_t ntc, int64_t nrem, cudaStream_t st) {
+    TreeDev& d = t->d;
+    int rc;
+    if (nrem > 0) {
+        uint64_t *k0 = nullptr, *k1 = nullptr;
+        if ((rc = dev_alloc(&k0, (size_t)nrem, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&k1, (size_t)nrem, nullptr, st))) return rc;
+        k_pack_rem<<<nblk(nrem, 256), 256, 0, st>>>(nrem, d.tc_tgt + ntc, d.tc_src + ntc, k0);
+        size_t tb = 0;
+        char* tmp = nullptr;
+        cub::DeviceRadixSort::SortKeys(nullptr, tb, k0, k1, nrem, 0, 64, st);
+        if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
+        FMM_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tb, k0, k1, nrem, 0, 64, st));
+        k_unpack_rem<<<nblk(nrem, 256), 256, 0, st>>>(nrem, k1, d.tc_tgt + ntc, d.tc_src + ntc);
+        count_launch(t, 3);
+        cudaFreeAsync(tmp, st);
+        cudaFreeAsync(k0, st);
+        cudaFreeAsync(k1, st);
+    }
+    if ((rc = dev_alloc(&d.rem_start, (size_t)t->ncell + 1, t, st))) return rc;
+    k_csr_from_targets<<<nblk(t->ncell + 1, 256), 256, 0, st>>>(d.tc_tgt + ntc, nrem, t->ncell, d.rem_start);
+    count_launch(t);
+    return FMM_OK;
+}
+
+// Grouping by hashing (no sort of the pairs).  *done stays false when the
+// table overflows; the caller then groups by sorting the class keys.
+static int classes_by_hash(fmm_tree* t, const int2* pairs, bool* done, cudaStream_t st) {
+    TreeDev& d = t->d;
+    int rc;
+    *done = false;
+    const int64_t np = t->nm2l;
+    const int H = 1 << CLASS_HASH_BITS;
+    uint64_t *table = nullptr, *skeys = nullptr;
+    int32_t *slot_of = nullptr, *iota = nullptr, *sslot = nullptr;
+    unsigned long long* ctr = nullptr;
+    int64_t* d_nclass = nullptr;
+    if ((rc = dev_alloc(&table, H, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&skeys, H, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&iota, H, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&sslot, H, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&slot_of, (size_t)np, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&ctr, 2, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&d_nclass, 1, nullptr, st))) return rc;
+    FMM_CUDA_TRY(cudaMemsetAsync(table, 0xff, sizeof(uint64_t) * H, st));
+    FMM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 2, st));
+    k_class_hash<<<nblk(np, 256), 256, 0, st>>>(np, pairs, d.icentre, table, (uint32_t)(H - 1), slot_of, ctr);
+    k_iota32<<<nblk(H, 256), 256, 0, st>>>(H, iota);
+    size_t tb = 0;
+    char* tmp = nullptr;
+    cub::DeviceRadixSort::SortPairs(nullptr, tb, table, skeys, iota, sslot, H, 0, CLASS_KEY_BITS, st);
+    if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
+    FMM_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tb, table, skeys, iota, sslot, H, 0, CLASS_KEY_BITS, st));
+    cudaFreeAsync(tmp, st);
+    k_count_classed<<<1, 1, 0, st>>>(skeys, H, d_nclass);
+    count_launch(t, 4);
+    unsigned long long hc[2] = {0, 0};
+    int64_t nclass64 = 0;
+    FMM_CUDA_TRY(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(&nclass64, d_nclass, 8, cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    auto release = [&]() {
+        cudaFreeAsync(table, st); cudaFreeAsync(skeys, st); cudaFreeAsync(iota, st); cudaFreeAsync(sslot, st);
+        cudaFreeAsync(slot_of, st); cudaFreeAsync(ctr, st); cudaFreeAsync(d_nclass, st);
+    };
+    if (hc[1] || nclass64 > H / 2) {  // probe limit hit, or a crowded table: sort the keys instead
+        release();
+        return FMM_OK;
+    }
+    const int nclass = (int)nclass64;
+    const int64_t nrem = (int64_t)hc[0], ntc = np - nrem;
+    // stable sort of the pairs by class id (a few bits: nclass + 1 ids)
+    int32_t *class_of_slot = nullptr, *cid0 = nullptr, *cid1 = nullptr, *idx0 = nullptr, *idx1 = nullptr;
+    int32_t *counts = nullptr, *cfirst = nullptr;
+    if ((rc = dev_alloc(&class_of_slot, H, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&cid0, (size_t)np, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&cid1, (size_t)np, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&idx0, (size_t)np, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&idx1, (size_t)np, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&counts, (size_t)nclass + 1, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&cfirst, (size_t)nclass + 1, nullptr, st))) return rc;
+    if (nclass > 0) {
+        k_number_classes<<<nblk(nclass, 256), 256, 0, st>>>(nclass, sslot, class_of_slot);
+        count_launch(t);
+    }
+    k_class_ids<<<nblk(np, 256), 256, 0, st>>>(np, slot_of, class_of_slot, nclass, cid0, idx0);
+    int bits = 1;
+    while ((1ll << bits) <= nclass) bits++;
+    tb = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tb, cid0, cid1, idx0, idx1, np, 0, bits, st);
+    if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
+    FMM_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tb, cid0, cid1, idx0, idx1, np, 0, bits, st));
+    cudaFreeAsync(tmp, st);
+    k_class_bounds<<<nblk(nclass + 1, 256), 256, 0, st>>>(nclass, cid1, np, counts);
+    count_launch(t, 3);
+    int64_t h_items = 0;
+    if ((rc = emit_classes(t, nclass, skeys, counts, cfirst, &h_items, st))) return rc;
+    if ((rc = dev_alloc(&d.tc_tgt, (size_t)np, t, st))) return rc;
+    if ((rc = dev_alloc(&d.tc_src, (size_t)np, t, st))) return rc;
+    k_gather_pairs<<<nblk(np, 256), 256, 0, st>>>(np, idx1, pairs, d.tc_tgt, d.tc_src);
+    count_launch(t);
+    if ((rc = finish_remainder(t, ntc, nrem, st))) return rc;
+    FMM_CUDA_TRY(cudaGetLastError());
+    t->tc_nclass = nclass;
+    t->tc_nitems = h_items;
+    t->tc_npairs = ntc;
+    t->tc_nrem = nrem;
+    release();
+    cudaFreeAsync(class_of_slot, st); cudaFreeAsync(cid0, st); cudaFreeAsync(cid1, st); cudaFreeAsync(idx0, st);
+    cudaFreeAsync(idx1, st); cudaFreeAsync(counts, st); cudaFreeAsync(cfirst, st);
+    *done = true;
+    return FMM_OK;
+}
+
 int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st) {
     TreeDev& d = t->d;
     int rc;
     const int64_t np = t->nm2l;
-    const int p = t->prm.p, Kp = tc_kpad(p);
     t->tc_nclass = 0; t->tc_nitems = 0; t->tc_npairs = 0;
     if (np == 0) {
         // no M2L pair at all: an empty class-less CSR keeps the M2L stage uniform
@@ -192,6 +457,10 @@ int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st) {
         FMM_CUDA_TRY(cudaMemsetAsync(d.rem_start, 0, sizeof(int64_t) * ((size_t)t->ncell + 1), st));
         return FMM_OK;
     }
+    bool done = false;
+    if ((rc = classes_by_hash(t, pairs, &done, st))) return rc;
+    if (done) return FMM_OK;
+    // grouping by sorting the class keys (tables too crowded for hashing)
     uint64_t *k0 = nullptr, *k1 = nullptr;
     int32_t *i0 = nullptr, *i1 = nullptr;
     if ((rc = dev_alloc(&k0, np, nullptr, st))) return rc;
@@ -233,46 +502,16 @@ int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st) {
         FMM_CUDA_TRY(cudaStreamSynchronize(st));
     }
     const int nclass = h_nruns;
-    // class offsets, items
-    int32_t *cfirst = nullptr, *tiles = nullptr, *tfirst = nullptr;
+    int32_t* cfirst = nullptr;
     if ((rc = dev_alloc(&cfirst, (size_t)nclass + 1, nullptr, st))) return rc;
-    if ((rc = dev_alloc(&tiles, (size_t)nclass + 1, nullptr, st))) return rc;
-    if ((rc = dev_alloc(&tfirst, (size_t)nclass + 1, nullptr, st))) return rc;
-    int32_t h_items = 0;
-    if (nclass > 0) {
-        tb = 0;
-        cub::DeviceScan::ExclusiveSum(nullptr, tb, counts, cfirst, nclass, st);
-        if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
-        FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, counts, cfirst, nclass, st));
-        k_class_tiles<<<nblk(nclass, 256), 256, 0, st>>>(nclass, counts, tiles);
-        FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, tiles, tfirst, nclass, st));
-        count_launch(t, 3);
-        cudaFreeAsync(tmp, st);
-        int32_t lt = 0, lf = 0;
-        FMM_CUDA_TRY(cudaMemcpyAsync(&lt, tiles + nclass - 1, 4, cudaMemcpyDeviceToHost, st));
-        FMM_CUDA_TRY(cudaMemcpyAsync(&lf, tfirst + nclass - 1, 4, cudaMemcpyDeviceToHost, st));
-        FMM_CUDA_TRY(cudaStreamSynchronize(st));
-        h_items = lt + lf;
-        if ((rc = dev_alloc(&d.tc_items, (size_t)h_items, t, st))) return rc;
-        k_emit_items<<<nblk(nclass, 256), 256, 0, st>>>(nclass, counts, cfirst, tfirst, d.tc_items);
-        count_launch(t);
-        // operators
-        size_t ob = (size_t)nclass * 2 * Kp * Kp;
-        __nv_bfloat16* ops = nullptr;
-        if ((rc = dev_alloc(&ops, ob, t, st))) return rc;
-        d.tc_ops = ops;
-        size_t smem = ntri(2 * p) * (sizeof(cplx<double>) + sizeof(cplx<float>)) + 32 * 4 + 512;
-        k_class_operators<<<nclass, 256, smem, st>>>(p, Kp, ukeys, ops);
-        count_launch(t);
-    }
-    // pairs in class order; the tail (no class) keeps target order for the CUDA-core kernel
+    int64_t h_items = 0;
+    if ((rc = emit_classes(t, nclass, ukeys, counts, cfirst, &h_items, st))) return rc;
+    // pairs in class order; the tail (no class) is in target order already
     if ((rc = dev_alloc(&d.tc_tgt, (size_t)np, t, st))) return rc;
     if ((rc = dev_alloc(&d.tc_src, (size_t)np, t, st))) return rc;
     k_gather_pairs<<<nblk(np, 256), 256, 0, st>>>(np, i1, pairs, d.tc_tgt, d.tc_src);
     count_launch(t);
-    if ((rc = dev_alloc(&d.rem_start, (size_t)t->ncell + 1, t, st))) return rc;
-    k_csr_from_targets<<<nblk(t->ncell + 1, 256), 256, 0, st>>>(d.tc_tgt + ntc, nrem, t->ncell, d.rem_start);
-    count_launch(t);
+    if ((rc = finish_remainder(t, ntc, nrem, st))) return rc;
     FMM_CUDA_TRY(cudaGetLastError());
     t->tc_nclass = nclass;
     t->tc_nitems = h_items;
@@ -280,7 +519,7 @@ int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st) {
     t->tc_nrem = nrem;
     cudaFreeAsync(k0, st); cudaFreeAsync(k1, st); cudaFreeAsync(i0, st); cudaFreeAsync(i1, st);
     cudaFreeAsync(ukeys, st); cudaFreeAsync(counts, st); cudaFreeAsync(nruns, st);
-    cudaFreeAsync(cfirst, st); cudaFreeAsync(tiles, st); cudaFreeAsync(tfirst, st);
+    cudaFreeAsync(cfirst, st);
     return FMM_OK;
 }
 
@@ -322,6 +561,8 @@ constexpr int TC_MMA_WARP = TC_EPI_WARPS + TC_PROD_WARPS;
 constexpr int TC_THREADS = 32 * (TC_EPI_WARPS + TC_PROD_WARPS + 1);
 constexpr int TC_PROD_THREADS = 32 * TC_PROD_WARPS;
 constexpr int TC_MAX_STAGES = 4, TC_MAX_ACC = 4, TC_TMEM_COLS = 512;
+// drain accumulators with TMA bulk reductions where the staging tiles fit
+constexpr bool TC_BULK_DRAIN = true;
 
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, long long budget_ns, volatile int* abort_flag) {
     if (tc::mbar_try_wait(bar, parity)) return true;
@@ -348,18 +589,24 @@ __device__ __forceinline__ void cp_async_wait_group() {
 }
 
 // producer thread pt (0..127): its share of the 128 x Kp source rows (hi,
-// lo); src[r] is the source cell of row r, -1 for an empty row
+// lo); src[r] is the source cell of row r, -1 for an empty row.  One warp
+// instruction covers 8 rows x 4 consecutive 16-byte chunks: 64 contiguous
+// bytes (two whole sectors) per source row, and four whole 128-byte core
+// matrices in shared memory (no bank conflicts).
 __device__ __forceinline__ void tc_gather(int pt, int Kp, int cpr, const int* src,
                                           const __nv_bfloat16* __restrict__ Ms, unsigned char* A_hi,
                                           unsigned char* A_lo) {
-    for (int q = pt; q < TC_ROWS * cpr; q += TC_PROD_THREADS) {
-        const int r = q / cpr, j = q - r * cpr;
+    const int lane = pt & 31, r_in = lane & 7, j_in = lane >> 3;
+    const int ntile = (TC_ROWS / 8) * ((cpr + 3) / 4);
+    for (int t = pt >> 5; t < ntile; t += TC_PROD_WARPS) {
+        const int r = 8 * (t % (TC_ROWS / 8)) + r_in, j = 4 * (t / (TC_ROWS / 8)) + j_in;
+        if (j >= cpr) continue;
         const int sc = src[r];
         const bool valid = sc >= 0;
         const __nv_bfloat16* g = Ms + (size_t)(valid ? sc : 0) * 2 * Kp + 8 * j;
         const uint32_t off = tc::core_offset(r, 8 * j, Kp);
-        tc::cp_async16(A_hi + off, g, valid ? 16u : 0u);
-        tc::cp_async16(A_lo + off, g + Kp, valid ? 16u : 0u);
+        tc::cp_async16_ca(A_hi + off, g, valid ? 16u : 0u);
+        tc::cp_async16_ca(A_lo + off, g + Kp, valid ? 16u : 0u);
     }
 }
 
@@ -370,6 +617,24 @@ __device__ __forceinline__ void tc_load_operator(int pt, int Kp, int cls, const 
     for (int q = pt; q < nchunk; q += TC_PROD_THREADS) tc::cp_async16(B + 16 * q, g + 16 * q, 16);
 }
 
+// Column blocks of 16 a drain warp reads per item: half of Kp / 16, at most
+// 5 (Kp = 144).
+constexpr int TC_MAX_CB = 5;
+
+// Reads the warp's share of one accumulator: rows 32 quarter + 16 h + lane/4
+// (v[h][c][0..1], v[h][c][4..5]) and that row + 8 (v[h][c][2..3],
+// v[h][c][6..7]), column blocks cb0 + c for c < ncb, all loads issued before
+// one wait.
+__device__ __forceinline__ void tc_load_acc(uint32_t tacc, int quarter, int cb0, int ncb,
+                                            uint32_t (&v)[2][TC_MAX_CB][8]) {
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int c = 0; c < TC_MAX_CB; c++)
+            if (c < ncb) tc::tmem_ld16x256_nowait(tacc + ((uint32_t)(32 * quarter + 16 * h) << 16) + 16 * (cb0 + c), v[h][c]);
+    tc::tmem_wait_ld();
+}
+
 // Adds one accumulator (TMEM columns from tacc on) into the targets' rows of
 // L; tgt[h][0..1] are the targets of rows 32 quarter + 16 h + lane/4 (+ 8),
 // -1 for an empty row.  The 16x256b TMEM load gives four consecutive threads
@@ -378,46 +643,94 @@ __device__ __forceinline__ void tc_load_operator(int pt, int Kp, int cls, const 
 __device__ __forceinline__ void tc_drain(uint32_t tacc, int quarter, int cb0, int cb1, int ncols, int ldL,
                                          const int (&tgt)[2][2], float* __restrict__ L) {
     const int lane = threadIdx.x & 31;
+    uint32_t v[2][TC_MAX_CB][8];
+    tc_load_acc(tacc, quarter, cb0, cb1 - cb0, v);
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int ta = tgt[h][0], tb = tgt[h][1];
         float* La = L + (size_t)(ta < 0 ? 0 : ta) * ldL;
         float* Lb = L + (size_t)(tb < 0 ? 0 : tb) * ldL;
-        for (int cb = cb0; cb < cb1; cb++) {
-            float v[8];
-            tc::tmem_ld16x256(tacc + ((uint32_t)(32 * quarter + 16 * h) << 16) + 16 * cb, v);
+#pragma unroll
+        for (int c = 0; c < TC_MAX_CB; c++) {
+            if (c >= cb1 - cb0) break;
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                const int col = 16 * cb + 8 * k + 2 * (lane & 3);
+                const int col = 16 * (cb0 + c) + 8 * k + 2 * (lane & 3);
                 if (col < ncols) {
-                    if (ta >= 0) atomicAdd(reinterpret_cast<float2*>(La + col), make_float2(v[4 * k], v[4 * k + 1]));
+                    if (ta >= 0)
+                        atomicAdd(reinterpret_cast<float2*>(La + col),
+                                  make_float2(__uint_as_float(v[h][c][4 * k]), __uint_as_float(v[h][c][4 * k + 1])));
                     if (tb >= 0)
-                        atomicAdd(reinterpret_cast<float2*>(Lb + col), make_float2(v[4 * k + 2], v[4 * k + 3]));
+                        atomicAdd(reinterpret_cast<float2*>(Lb + col), make_float2(__uint_as_float(v[h][c][4 * k + 2]),
+                                                                                   __uint_as_float(v[h][c][4 * k + 3])));
                 }
             }
         }
     }
 }
 
+// Bulk-reduction form of the drain: the warp's 32 rows x [c0, c1) columns go
+// through a shared-memory tile (row stride `stride` floats), then lane r adds
+// row r into its target's row of L with one TMA bulk reduction of
+// 4 (c1 - c0) bytes.  tgt_row is the target of row 32 quarter + lane.
+__device__ __forceinline__ void tc_drain_bulk(uint32_t tacc, int quarter, int cb0, int cb1, int c0, int c1,
+                                              int stride, int ldL, int tgt_row, float* stg,
+                                              float* __restrict__ L) {
+    const int lane = threadIdx.x & 31;
+    uint32_t v[2][TC_MAX_CB][8];
+    tc_load_acc(tacc, quarter, cb0, cb1 - cb0, v);
+    tc::bulk_wait_read();  // the previous item's reductions have read the tile
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int ra = 16 * h + (lane >> 2);
+#pragma unroll
+        for (int c = 0; c < TC_MAX_CB; c++) {
+            if (c >= cb1 - cb0) break;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const int col = 16 * c + 8 * k + 2 * (lane & 3);
+                *reinterpret_cast<uint2*>(stg + ra * stride + col) = make_uint2(v[h][c][4 * k], v[h][c][4 * k + 1]);
+                *reinterpret_cast<uint2*>(stg + (ra + 8) * stride + col) =
+                    make_uint2(v[h][c][4 * k + 2], v[h][c][4 * k + 3]);
+            }
+        }
+    }
+    tc::fence_proxy_async();
+    __syncwarp();
+    if (tgt_row >= 0 && c1 > c0) {
+        tc::bulk_reduce_add_f32(L + (size_t)tgt_row * ldL + c0, stg + lane * stride, (uint32_t)(4 * (c1 - c0)));
+        tc::bulk_commit();
+    }
+}
+
 struct TcShape {
-    int stages, nslots, nacc;
+    int stages, nslots, nacc, stg_stride;  // stg_stride 0: float2 reductions, no staging tiles
     size_t smem;
 };
 
-// stages and operator slots that fit `cap` bytes of shared memory, and TMEM
-// accumulators that fit the 512 columns of one SM (one block per SM)
-static TcShape tc_shape(int Kp, size_t cap) {
+// Stages and operator slots that fit `cap` bytes of shared memory, and TMEM
+// accumulators that fit the 512 columns of one SM (one block per SM).  With
+// `bulk`, each epilogue warp also gets a 32-row staging tile for the bulk
+// reductions, if two stages and one operator slot still fit.
+static TcShape tc_shape(int Kp, size_t cap, bool bulk) {
     const size_t stage = (size_t)2 * TC_ROWS * Kp * 2 + TC_ROWS * sizeof(int), slot = (size_t)2 * Kp * Kp * 2;
     TcShape sh{};
-    sh.nslots = 2 * slot + 2 * stage <= cap ? 2 : 1;
-    sh.stages = (int)std::min<size_t>(TC_MAX_STAGES, (cap - sh.nslots * slot) / stage);
+    size_t stg = 0;
+    if (bulk) {
+        sh.stg_stride = 16 * ((Kp / 16 + 1) / 2) + 4;
+        stg = (size_t)TC_EPI_WARPS * 32 * sh.stg_stride * 4;
+        if (stg + 2 * stage + slot > cap) { sh.stg_stride = 0; stg = 0; }
+    }
+    sh.nslots = 2 * slot + 2 * stage + stg <= cap ? 2 : 1;
+    sh.stages = (int)std::min<size_t>(TC_MAX_STAGES, (cap - stg - sh.nslots * slot) / stage);
     sh.nacc = std::min(TC_MAX_ACC, TC_TMEM_COLS / Kp);
-    sh.smem = sh.stages * stage + sh.nslots * slot;
+    sh.smem = sh.stages * stage + sh.nslots * slot + stg;
     return sh;
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_m2l_tc(int Kp, int stages, int nslots, int nacc, int ncols, int ldL, int n_items, int per_cta,
+    k_m2l_tc(int Kp, int stages, int nslots, int nacc, int stg_stride, int ncols, int ldL, int n_items, int per_cta,
              const int4* __restrict__ items, const int32_t* __restrict__ pc_src, const int32_t* __restrict__ pc_tgt,
              const __nv_bfloat16* __restrict__ ops, const __nv_bfloat16* __restrict__ Ms, float* __restrict__ L,
              int* status, long long budget_ns) {
@@ -432,6 +745,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     auto A_of = [&](int s) { return sm + 2 * s * abytes; };
     auto B_of = [&](int o) { return sm + 2 * stages * abytes + 2 * o * bbytes; };
     int* src_idx = reinterpret_cast<int*>(sm + 2 * stages * abytes + 2 * nslots * bbytes);
+    float* stg_all = reinterpret_cast<float*>(src_idx + stages * TC_ROWS);  // staging tiles (bulk drain)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < stages; s++) { tc::mbar_init(&full[s], TC_PROD_THREADS); tc::mbar_init(&empty[s], 1); }
@@ -452,54 +766,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- producers
         // Item j+1 and the source of row pt of item j+1 are loaded while item j
         // is gathered; the 128 sources of an item go through shared memory so
-        // that no cp.async waits on a global load.
-        const int pt = tid - 32 * TC_EPI_WARPS, cpr = Kp / 8, D = stages - 1;
-        int cur_cls = -1, cur_slot = 0, loads[2] = {0, 0}, signalled = 0;
-        bool ok = true;
+        // that no cp.async waits on a global load.  Each producer thread's
+        // copies arrive on full[s] by themselves when they land
+        // (cp.async.mbarrier.arrive.noinc), so the gather of item j+1 never
+        // waits for item j.
+        const int pt = tid - 32 * TC_EPI_WARPS, cpr = Kp / 8;
+        int cur_cls = -1, cur_slot = 0, loads[2] = {0, 0};
         int4 item_n = nit > 0 ? items[i0] : make_int4(0, 0, 0, 0);
         int src_n = (nit > 0 && pt < item_n.z) ? pc_src[item_n.y + pt] : -1;
-        for (int j = 0; j < nit && ok; j++) {
+        for (int j = 0; j < nit; j++) {
             const int s = j % stages;
             const int4 item = item_n;
             const int src_j = src_n;
             if (j + 1 < nit) item_n = items[i0 + j + 1];
+            bool ok = true;
             if (item.x != cur_cls) {
                 const int o = (nslots == 2 && cur_cls >= 0) ? cur_slot ^ 1 : 0;
-                if ((o == 0 ? loads[0] : loads[1]) > 0) {
-                    // the slot is released by the MMA thread once the last run that
-                    // used it is issued: hand over every item gathered so far first
-                    cp_async_wait_group<0>();
-                    tc::fence_proxy_async();
-                    for (; signalled < j; signalled++) mbar_arrive(&full[signalled % stages]);
-                    const int n = o == 0 ? loads[0] : loads[1];
-                    if (!tc_wait(&opfree[o], (uint32_t)((n - 1) & 1), budget_ns, abort_p)) { ok = false; break; }
-                }
-                tc_load_operator(pt, Kp, item.x, ops, B_of(o));
+                const int n = o == 0 ? loads[0] : loads[1];
+                // the slot is released once the MMAs of the last run that used it are done
+                if (n > 0) ok = tc_wait(&opfree[o], (uint32_t)((n - 1) & 1), budget_ns, abort_p);
+                if (ok) tc_load_operator(pt, Kp, item.x, ops, B_of(o));
                 if (o == 0) loads[0]++; else loads[1]++;
                 cur_cls = item.x;
                 cur_slot = o;
             }
-            if (j >= stages && !tc_wait(&empty[s], (uint32_t)(((j / stages) - 1) & 1), budget_ns, abort_p)) {
-                ok = false;
-                break;
-            }
+            if (ok && j >= stages) ok = tc_wait(&empty[s], (uint32_t)(((j / stages) - 1) & 1), budget_ns, abort_p);
             src_idx[s * TC_ROWS + pt] = src_j;
-            asm volatile("bar.sync 1, %0;" ::"n"(TC_PROD_THREADS) : "memory");
+            // all producers leave together (a named barrier with an AND reduction)
+            int all_ok;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
+                "bar.red.and.pred q, 1, %2, p;\n\tselp.b32 %0, 1, 0, q;\n\t}\n"
+                : "=r"(all_ok)
+                : "r"((int)ok), "n"(TC_PROD_THREADS)
+                : "memory");
+            if (!all_ok) break;
             if (j + 1 < nit) src_n = pt < item_n.z ? pc_src[item_n.y + pt] : -1;
             tc_gather(pt, Kp, cpr, src_idx + s * TC_ROWS, Ms, A_of(s), A_of(s) + abytes);
-            tc::cp_async_commit();
-            if (j - signalled >= D) {
-                if (D >= 3) cp_async_wait_group<3>();
-                else if (D == 2) cp_async_wait_group<2>();
-                else cp_async_wait_group<1>();
-                tc::fence_proxy_async();
-                for (; signalled <= j - D; signalled++) mbar_arrive(&full[signalled % stages]);
-            }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::smem_u32(&full[s]))
+                         : "memory");
         }
         cp_async_wait_group<0>();
-        tc::fence_proxy_async();
-        if (ok)
-            for (; signalled < nit; signalled++) mbar_arrive(&full[signalled % stages]);
     } else if (warp == TC_MMA_WARP) {
         // ---------------- MMA issue (one thread)
         if (lane == 0) {
@@ -518,6 +825,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 if (!tc_wait(&full[s], (uint32_t)((j / stages) & 1), budget_ns, abort_p)) break;
                 if (j >= nacc && !tc_wait(&acce[a], (uint32_t)(((j / nacc) - 1) & 1), budget_ns, abort_p)) break;
+                // the stage was written by the producers' cp.async (generic proxy)
+                // and is read by the tensor core (async proxy)
+                tc::fence_proxy_async();
                 tc::fence_after_sync();
                 const uint32_t ah = tc::smem_u32(A_of(s)), al = ah + (uint32_t)abytes;
                 const uint32_t bh = tc::smem_u32(B_of(cur_slot)), bl = bh + (uint32_t)bbytes;
@@ -556,22 +866,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tg[h][1] = ra + 8 < it.z ? pc_tgt[it.y + ra + 8] : -1;
             }
         };
-        int tgt[2][2], tgt_n[2][2];
-        int4 item_n = nit > 1 ? items[i0 + 1] : make_int4(0, 0, 0, 0);
-        if (nit > 0) load_targets(items[i0], tgt);
-        for (int j = 0; j < nit; j++) {
-            const int a = j % nacc;
-            if (j + 1 < nit) load_targets(item_n, tgt_n);
-            if (j + 2 < nit) item_n = items[i0 + j + 2];
-            const bool got = tc_wait(&accf[a], (uint32_t)((j / nacc) & 1), budget_ns, abort_p);
-            if (!__all_sync(0xffffffffu, got)) break;
-            tc::fence_after_sync();
-            tc_drain(tbase + (uint32_t)(a * Kp), quarter, cb0, cb1, ncols, ldL, tgt, L);
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[a]);
+        if (stg_stride > 0) {
+            // bulk reductions: lane r owns row 32 quarter + r of the item
+            const int c0 = 16 * cb0, c1 = min(16 * cb1, (ncols + 3) & ~3);
+            float* stg = stg_all + (size_t)warp * 32 * stg_stride;
+            const int row = 32 * quarter + lane;
+            int4 item_n = nit > 1 ? items[i0 + 1] : make_int4(0, 0, 0, 0);
+            int tg = -1, tg_n = -1;
+            if (nit > 0) { const int4 it = items[i0]; tg = row < it.z ? pc_tgt[it.y + row] : -1; }
+            for (int j = 0; j < nit; j++) {
+                const int a = j % nacc;
+                if (j + 1 < nit) tg_n = row < item_n.z ? pc_tgt[item_n.y + row] : -1;
+                if (j + 2 < nit) item_n = items[i0 + j + 2];
+                const bool got = tc_wait(&accf[a], (uint32_t)((j / nacc) & 1), budget_ns, abort_p);
+                if (!__all_sync(0xffffffffu, got)) break;
+                tc::fence_after_sync();
+                tc_drain_bulk(tbase + (uint32_t)(a * Kp), quarter, cb0, cb1, c0, c1, stg_stride, ldL, tg, stg, L);
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[a]);
+                tg = tg_n;
+            }
+            tc::bulk_wait_all();
+        } else {
+            int tgt[2][2], tgt_n[2][2];
+            int4 item_n = nit > 1 ? items[i0 + 1] : make_int4(0, 0, 0, 0);
+            if (nit > 0) load_targets(items[i0], tgt);
+            for (int j = 0; j < nit; j++) {
+                const int a = j % nacc;
+                if (j + 1 < nit) load_targets(item_n, tgt_n);
+                if (j + 2 < nit) item_n = items[i0 + j + 2];
+                const bool got = tc_wait(&accf[a], (uint32_t)((j / nacc) & 1), budget_ns, abort_p);
+                if (!__all_sync(0xffffffffu, got)) break;
+                tc::fence_after_sync();
+                tc_drain(tbase + (uint32_t)(a * Kp), quarter, cb0, cb1, ncols, ldL, tgt, L);
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[a]);
 #pragma unroll
-            for (int h = 0; h < 2; h++) { tgt[h][0] = tgt_n[h][0]; tgt[h][1] = tgt_n[h][1]; }
+                for (int h = 0; h < 2; h++) { tgt[h][0] = tgt_n[h][0]; tgt[h][1] = tgt_n[h][1]; }
+            }
         }
     }
     tc::fence_before_sync();
@@ -596,7 +930,7 @@ int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st) {
     cudaFuncAttributes fa{};
     FMM_CUDA_TRY(cudaFuncGetAttributes(&fa, k_m2l_tc));
     const size_t cap = (size_t)optin - fa.sharedSizeBytes - 128;  // slack for the 128-byte alignment
-    const TcShape sh = tc_shape(Kp, cap);
+    const TcShape sh = tc_shape(Kp, cap, TC_BULK_DRAIN);
     if (sh.stages < 2 || sh.nacc < 2) {
         fmm_set_error("tensor-core M2L: Kp = %d does not fit shared memory", Kp);
         return FMM_ERR_ARG;
@@ -608,8 +942,16 @@ int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st) {
     int grid = (int)std::min<int64_t>(t->tc_nitems, (int64_t)t->num_sms);
     int per_cta = (int)((t->tc_nitems + grid - 1) / grid);
     grid = (int)((t->tc_nitems + per_cta - 1) / per_cta);
+    if (t->ev_ops) {
+        // the class operators are built on the side stream; under stream capture
+        // the wait enters the graph as an external event wait node
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        FMM_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_ops,
+                                         cs == cudaStreamCaptureStatusNone ? cudaEventWaitDefault : cudaEventWaitExternal));
+    }
     stage_begin(t, FMM_STAGE_M2L_TC, st);
-    k_m2l_tc<<<grid, TC_THREADS, smem, st>>>(Kp, sh.stages, sh.nslots, sh.nacc, K2, 2 * KS, (int)t->tc_nitems,
+    k_m2l_tc<<<grid, TC_THREADS, smem, st>>>(Kp, sh.stages, sh.nslots, sh.nacc, sh.stg_stride, K2, 2 * KS, (int)t->tc_nitems,
                                               per_cta, d.tc_items, d.tc_src, d.tc_tgt, ops, msplit, L, d.status,
                                               t->prm.timeout_ns);
     count_launch(t);

@@ -42,6 +42,7 @@ template int dev_alloc<int4>(int4**, size_t, fmm_tree*, cudaStream_t);
 template int dev_alloc<__nv_bfloat16>(__nv_bfloat16**, size_t, fmm_tree*, cudaStream_t);
 template int dev_alloc<int2>(int2**, size_t, fmm_tree*, cudaStream_t);
 template int dev_alloc<double4_32a>(double4_32a**, size_t, fmm_tree*, cudaStream_t);
+template int dev_alloc<unsigned long long>(unsigned long long**, size_t, fmm_tree*, cudaStream_t);
 
 template <typename T>
 static void dev_free(T*& p, cudaStream_t st) {
@@ -907,6 +908,7 @@ void free_tree_device(fmm_tree* t) {
     dev_free(d.rem_start, st);
     dev_free(d.tr_start, st); dev_free(d.tr_tgt, st); dev_free(d.q_cnt_init, st); dev_free(d.q_cnt, st);
     dev_free(d.q_init, st); dev_free(d.q_work, st); dev_free(d.q_ctr, st);
+    dev_free(d.tc_keys, st);
     if (d.tc_ops) cudaFreeAsync(d.tc_ops, st);
     if (d.tc_msplit) cudaFreeAsync(d.tc_msplit, st);
     d.tc_ops = nullptr; d.tc_msplit = nullptr;

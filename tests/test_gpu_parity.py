@@ -115,3 +115,29 @@ def test_duplicates_and_single_particle():
     assert O.rel_l2(phi, ref_phi) <= FP64_TOL and O.rel_l2(f, ref_f) <= FP64_TOL
     phi, f = gpu_eval(gpu_tree(np.array([[0.3, 0.3, 0.3]]), p=4), np.array([1.0]))
     assert phi[0] == 0.0 and np.all(f == 0.0)
+
+
+def test_tensor_core_graph_replay_and_early_destroy():
+    """Mixed tensor-core trees build their class operators on a second stream:
+    a graph captured after one evaluation replays the same result (up to the
+    order of the M2L accumulation), and a tree destroyed straight after its
+    build (operators possibly still running) releases cleanly."""
+    import paper_1203_0889_gb300 as fmm
+    torch, dev = torch_dev()
+    wl = W.make_workload("plummer", n=50000)
+    pos = torch.tensor(wl.pos, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        fmm.build_tree(pos, p=8, leaf_size=64, theta=0.4, precision=fmm.PREC_MIXED_TC).close()
+    t = fmm.build_tree(pos, p=8, leaf_size=64, theta=0.4, precision=fmm.PREC_MIXED_TC)
+    assert t.info().tc_pairs > 0
+    qt = torch.tensor(wl.q, dtype=torch.float32, device=dev)
+    phi = torch.empty(len(wl.q), dtype=torch.float32, device=dev)
+    force = torch.empty((len(wl.q), 3), dtype=torch.float32, device=dev)
+    eager_phi, eager_f = t.evaluate(qt)
+    g = fmm.capture_graph(t, qt, phi, force)
+    phi.zero_(); force.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert t.status() == fmm.FMM_OK
+    assert ((phi - eager_phi).norm() / eager_phi.norm()).item() <= 1e-6
+    assert ((force - eager_f).norm() / eager_f.norm()).item() <= 1e-6
