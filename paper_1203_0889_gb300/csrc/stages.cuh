@@ -328,12 +328,73 @@ __device__ __forceinline__ void p2p_pair(const typename Vec4<T>::type& me, const
     gx -= qr3 * dx; gy -= qr3 * dy; gz -= qr3 * dz;
 }
 
+// Paired FP32 arithmetic (PTX add/mul/fma .f32x2, sm_100 and later): one
+// instruction applies the operation to both 32-bit halves of a 64-bit
+// register pair.  The FP32 pair kernel keeps its two targets in the two
+// halves, which halves the issue slots of the pair arithmetic.
+namespace f2 {
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pack(float lo, float hi) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack(u64 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 add(u64 a, u64 b) {
+    u64 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 mul(u64 a, u64 b) {
+    u64 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 fma(u64 a, u64 b, u64 c) {
+    u64 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+}  // namespace f2
+
+// One staged source against the two targets held in the halves of X, Y, Z.
+// The source is staged negated and duplicated: s01 = (-x, -x | -y, -y),
+// s23 = (-z, -z | -q, -q), so that d = X + (-x) and the negated potential
+// and field accumulate with adds and fmas only (NP = -phi, G = the field
+// term, both per half).
+__device__ __forceinline__ void p2p_pair_x2(f2::u64 X, f2::u64 Y, f2::u64 Z, const ulonglong2 s01,
+                                            const ulonglong2 s23, f2::u64& NP, f2::u64& GX, f2::u64& GY,
+                                            f2::u64& GZ) {
+    const f2::u64 dx = f2::add(X, s01.x), dy = f2::add(Y, s01.y), dz = f2::add(Z, s23.x);
+    const f2::u64 r2 = f2::fma(dz, dz, f2::fma(dy, dy, f2::mul(dx, dx)));
+    float ra, rb;
+    f2::unpack(r2, ra, rb);
+    ra = ra > pair_floor(ra) ? rsqrt_t(ra) : 0.f;
+    rb = rb > pair_floor(rb) ? rsqrt_t(rb) : 0.f;
+    const f2::u64 rinv = f2::pack(ra, rb);
+    const f2::u64 nqr = f2::mul(s23.y, rinv);
+    NP = f2::add(NP, nqr);
+    const f2::u64 nqr3 = f2::mul(f2::mul(nqr, rinv), rinv);
+    GX = f2::fma(nqr3, dx, GX);
+    GY = f2::fma(nqr3, dy, GY);
+    GZ = f2::fma(nqr3, dz, GZ);
+}
+
+// Targets held by one thread: each staged source feeds this many pair
+// interactions (four was measured slower than two in FP32: fewer source
+// streams per target and more registers).
+template <typename T>
+struct P2PBlocking { static constexpr int TPT = 2; };
+
 // One block of P2P_THREADS threads, target leaf c.  The target's sources are
 // one concatenated particle stream (each P2P record gives a source leaf's
 // offset in it), staged P2P_BUF at a time, the four warps copying different
-// source leaves.  Each thread holds two targets, so one staged source feeds two
-// pair interactions: thread t works on targets 2u, 2u+1 (u = t mod nu, nu =
-// ceil(nt/2)) over the staged sources j = (t / nu) (mod G), G = 128 / nu.
+// source leaves.  Each thread holds TPT targets, so one staged source feeds TPT
+// pair interactions: thread t works on targets TPT u + i (u = t mod nu,
+// nu = ceil(nt / TPT)) over the staged sources j = (t / nu) (mod G),
+// G = P2P_THREADS / nu.
 template <typename T>
 __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t* __restrict__ count,
                          const int64_t* __restrict__ start, const int4* __restrict__ rec,
@@ -341,6 +402,11 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
                          const float* __restrict__ cu2f, double* __restrict__ near, typename Vec4<T>::type* buf,
                          T (*part)[4]) {
     typedef typename Vec4<T>::type V;
+    constexpr int TPT = P2PBlocking<T>::TPT;
+    static_assert(sizeof(T) == 8 || TPT == 2, "the paired FP32 loop holds two targets");
+    // sources per staging round: FP32 stages each source as two float4 (negated,
+    // duplicated for the paired arithmetic), so half as many fit the buffer
+    constexpr int NB = sizeof(T) == 4 ? P2P_BUF / 2 : P2P_BUF;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tf = first[c], nt = count[c];
     const int64_t s0 = start[c], s1 = start[c + 1];
@@ -348,23 +414,34 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
     if (s1 > s0) { const int4 r = rec[s1 - 1]; total = r.z + r.y; }
     const int4 ict = icentre[c];
     const float u2f = cu2f[c];   // side/2^22 of the target's system (sources share it)
-    for (int tb = 0; tb < nt; tb += 2 * P2P_THREADS) {
-        const int ntc = min(2 * P2P_THREADS, nt - tb);
-        const int nu = (ntc + 1) >> 1;
+    for (int tb = 0; tb < nt; tb += TPT * P2P_THREADS) {
+        const int ntc = min(TPT * P2P_THREADS, nt - tb);
+        const int nu = (ntc + TPT - 1) / TPT;
         const int G = P2P_THREADS / nu;
         const int u = threadIdx.x % nu, sub = threadIdx.x / nu;
         const bool active = sub < G;
-        const bool two = 2 * u + 1 < ntc;
-        const V me0 = xq[tf + tb + 2 * u];
-        const V me1 = two ? xq[tf + tb + 2 * u + 1] : me0;
-        T p0 = 0, x0 = 0, y0 = 0, z0 = 0, p1 = 0, x1 = 0, y1 = 0, z1 = 0;
+        V me[TPT];
+        T ph[TPT], gx[TPT], gy[TPT], gz[TPT];
+#pragma unroll
+        for (int i = 0; i < TPT; i++) {
+            const int ti = TPT * u + i;
+            me[i] = xq[tf + tb + (ti < ntc ? ti : TPT * u)];
+            ph[i] = gx[i] = gy[i] = gz[i] = T(0);
+        }
+        // FP32: paired accumulators, targets TPT u (low half) and TPT u + 1 (high)
+        f2::u64 X = 0, Y = 0, Z = 0, NP = 0, GX = 0, GY = 0, GZ = 0;
+        if constexpr (sizeof(T) == 4) {
+            X = f2::pack(me[0].x, me[1].x);
+            Y = f2::pack(me[0].y, me[1].y);
+            Z = f2::pack(me[0].z, me[1].z);
+        }
         int64_t e_lo = s0;
-        for (int base = 0; base < total; base += P2P_BUF) {
-            const int lim = min(P2P_BUF, total - base);
+        for (int base = 0; base < total; base += NB) {
+            const int lim = min(NB, total - base);
             for (int64_t e = e_lo + warp; e < s1; e += P2P_THREADS / 32) {
                 const int4 r = rec[e];
-                if (r.z >= base + P2P_BUF) break;
-                const int k0 = max(0, base - r.z), k1 = min(r.y, base + P2P_BUF - r.z);
+                if (r.z >= base + NB) break;
+                const int k0 = max(0, base - r.z), k1 = min(r.y, base + NB - r.z);
                 if (k1 <= k0) continue;
                 Offset3<T> o = {T(0), T(0), T(0)};
                 if (sizeof(T) == 4) {
@@ -373,43 +450,67 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
                     o.y = (T)((float)(ics.y - ict.y) * u2f);
                     o.z = (T)((float)(ics.z - ict.z) * u2f);
                 }
-                for (int k = k0 + lane; k < k1; k += 32) buf[r.z + k - base] = shift_src(xq[r.x + k], o);
+                for (int k = k0 + lane; k < k1; k += 32) {
+                    const V v = shift_src(xq[r.x + k], o);
+                    if constexpr (sizeof(T) == 4) {
+                        float4* b2 = reinterpret_cast<float4*>(buf) + 2 * (r.z + k - base);
+                        b2[0] = make_float4(-v.x, -v.x, -v.y, -v.y);
+                        b2[1] = make_float4(-v.z, -v.z, -v.w, -v.w);
+                    } else {
+                        buf[r.z + k - base] = v;
+                    }
+                }
             }
             __syncthreads();
             if (active) {
-                int j = sub;
-                for (; j + G < lim; j += 2 * G) {
-                    const V a = buf[j], bb = buf[j + G];
-                    p2p_pair<T>(me0, a, p0, x0, y0, z0);
-                    p2p_pair<T>(me1, a, p1, x1, y1, z1);
-                    p2p_pair<T>(me0, bb, p0, x0, y0, z0);
-                    p2p_pair<T>(me1, bb, p1, x1, y1, z1);
-                }
-                if (j < lim) {
-                    const V a = buf[j];
-                    p2p_pair<T>(me0, a, p0, x0, y0, z0);
-                    p2p_pair<T>(me1, a, p1, x1, y1, z1);
+                if constexpr (sizeof(T) == 4) {
+                    const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(buf);
+#pragma unroll 4
+                    for (int j = sub; j < lim; j += G)
+                        p2p_pair_x2(X, Y, Z, b2[2 * j], b2[2 * j + 1], NP, GX, GY, GZ);
+                } else {
+                    int j = sub;
+                    for (; j + G < lim; j += 2 * G) {
+                        const V a = buf[j], bb = buf[j + G];
+#pragma unroll
+                        for (int i = 0; i < TPT; i++) p2p_pair<T>(me[i], a, ph[i], gx[i], gy[i], gz[i]);
+#pragma unroll
+                        for (int i = 0; i < TPT; i++) p2p_pair<T>(me[i], bb, ph[i], gx[i], gy[i], gz[i]);
+                    }
+                    if (j < lim) {
+                        const V a = buf[j];
+#pragma unroll
+                        for (int i = 0; i < TPT; i++) p2p_pair<T>(me[i], a, ph[i], gx[i], gy[i], gz[i]);
+                    }
                 }
             }
             __syncthreads();
             while (e_lo < s1) {
                 const int4 r = rec[e_lo];
-                if (r.z + r.y > base + P2P_BUF) break;
+                if (r.z + r.y > base + NB) break;
                 e_lo++;
             }
         }
-        // partial sums of the two targets, reduced over the G source streams
-        for (int h = 0; h < 2; h++) {
-            part[threadIdx.x][0] = h ? p1 : p0; part[threadIdx.x][1] = h ? x1 : x0;
-            part[threadIdx.x][2] = h ? y1 : y0; part[threadIdx.x][3] = h ? z1 : z0;
+        if constexpr (sizeof(T) == 4) {
+            float a, b;
+            f2::unpack(NP, a, b); ph[0] = -a; ph[1] = -b;
+            f2::unpack(GX, a, b); gx[0] = a; gx[1] = b;
+            f2::unpack(GY, a, b); gy[0] = a; gy[1] = b;
+            f2::unpack(GZ, a, b); gz[0] = a; gz[1] = b;
+        }
+        // partial sums of the TPT targets, reduced over the G source streams
+#pragma unroll
+        for (int h = 0; h < TPT; h++) {
+            part[threadIdx.x][0] = ph[h]; part[threadIdx.x][1] = gx[h];
+            part[threadIdx.x][2] = gy[h]; part[threadIdx.x][3] = gz[h];
             __syncthreads();
-            if (threadIdx.x < nu && 2 * threadIdx.x + h < ntc) {
+            if (threadIdx.x < nu && TPT * threadIdx.x + h < ntc) {
                 T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
                 for (int q = 0; q < G; q++) {
                     const int k = q * nu + threadIdx.x;
                     a0 += part[k][0]; a1 += part[k][1]; a2 += part[k][2]; a3 += part[k][3];
                 }
-                const int64_t i = tf + tb + 2 * threadIdx.x + h;
+                const int64_t i = tf + tb + TPT * threadIdx.x + h;
                 near[4 * i] = (double)a0; near[4 * i + 1] = (double)a1; near[4 * i + 2] = (double)a2;
                 near[4 * i + 3] = (double)a3;
             }
