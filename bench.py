@@ -9,6 +9,11 @@ truncated at r = 50), charges 1/N, order p = 8, leaf size 64, theta = 0.4.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The headline is the mixed form (tensor-core M2L from split bf16 products,
+FP32 elsewhere), whose error against the plain FP64 GPU path is measured in
+the same run and printed beside it; the FP64, FP32-P2P/FP64-expansion and
+FP32 forms are timed on the same system as context ("variants").
+
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own system
 (replicas: the single-system path has no exchange step) and the value is the
 particles of all ranks over the slowest rank's time.
@@ -48,7 +53,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--precision", type=int, default=2, help="0 fp64, 1 fp32 P2P, 2 fp32, 3 mixed tensor-core")
+    ap.add_argument("--precision", type=int, default=3,
+                    help="0 fp64, 1 fp32 P2P + fp64 expansions, 2 fp32, 3 mixed: bf16x3 tensor-core M2L + fp32")
+    ap.add_argument("--no-variants", action="store_true", help="skip the other precisions' context timings")
     ap.add_argument("--staged", action="store_true", help="one kernel per stage instead of the task queue")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -154,62 +161,70 @@ def p2p_pairs(ex) -> int:
     return int((cnt[pl[:, 0]] * cnt[pl[:, 1]]).sum() - len(ex["keys"]))
 
 
-def roofline(stage_ms: dict, ex, prec: int, sm_clock_mhz: float, n_sm: int, info=None):
-    """Roofline object for the stage that dominates the evaluation."""
+# FP64 FMA throughput of one GB300 (TFLOP/s) from a dependent-chain FMA probe
+# over all SMs at the loaded clock: the FP64 pipe is narrow on this part.
+FP64_TFLOPS_MEASURED = 1.256
+
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
+# stands (summaries in profiles/); None once the kernel has changed since.
+TRAFFIC = {"k_p2p": 89188608 + 15778048,        # profiles/k_p2p_plummer1m_p8_fp32.md
+           "k_m2l_tc": 535333376 + 10936832}    # profiles/k_m2l_tc_plummer1m_p8.md
+
+
+def kernel_rooflines(stage_ms: dict, ex, prec: int, n_sm: int, info=None):
+    """Roofline objects of the evaluation's heavy kernels.  Their times are the
+    library's own CUDA events around each stage inside the timed region,
+    recorded on the stream the stage is launched on (P2P runs on the tree's
+    second stream)."""
     pk, how = peaks()
+    clk = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = n_sm * 128 * 2 * clk * 1e6 / 1e12          # TFLOP/s, FP32 FMA lanes at the maximum clock
+    fp32_src = f"{n_sm} SM x 128 FP32 lanes x 2 flop x {clk:.0f} MHz (derived, not measured)"
+    fp64_src = "FP64 FMA probe, measured"
     K = (P + 1) ** 2
-    clk = 2070.0 if not sm_clock_mhz else 2070.0
-    fp32_peak = n_sm * 128 * 2 * clk * 1e6 / 1e12          # TFLOP/s, FP32 FMA lanes at max clock
-    fp64_peak = FP64_TFLOPS_MEASURED                        # from the FMA probe (see DESIGN)
-    cand = {k: v for k, v in stage_ms.items() if k in ("p2p", "m2l", "p2m", "m2m", "l2l", "l2p")}
-    if not cand and "queue" in stage_ms:
-        # one persistent kernel runs every evaluation stage: its algorithmic work is
-        # dominated by the M2L contractions and the P2P pair sums
+    out = []
+    pairs = p2p_pairs(ex)
+    if "queue" in stage_ms:
         tq = stage_ms["queue"] * 1e-3
         nm2l = len(ex["m2l"])
-        pairs = p2p_pairs(ex)
         flops = nm2l * 2.0 * K * K + pairs * float(P2P_FLOPS_PER_PAIR)
-        peak = fp64_peak if prec in (0, 1) else fp32_peak
-        return {"kernel": "k_queue", "bound": "alu", "achieved": flops / tq / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": flops / tq / 1e12 / peak, "traffic": None,
-                "algorithmic": f"{nm2l} M2L pairs x 2K^2 + {pairs} P2P pairs x {P2P_FLOPS_PER_PAIR} flops",
-                "peak_source": "FP64 FMA probe" if prec in (0, 1) else f"{n_sm} SM x 128 FP32 lanes x 2 x {clk} MHz"}
-    dom = max(cand, key=cand.get)
-    t = cand[dom] * 1e-3
-    nm2l = len(ex["m2l"])
-    if dom == "m2l" and prec == 3 and info is not None and info.tc_pairs > 0 and "m2l_tc" in stage_ms:
-        t_tc = stage_ms["m2l_tc"] * 1e-3
+        peak = FP64_TFLOPS_MEASURED if prec in (0, 1) else fp32_peak
+        out.append({"kernel": "k_queue", "bound": "alu", "achieved": flops / tq / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "frac": flops / tq / 1e12 / peak, "traffic": None, "ms": stage_ms["queue"],
+                    "algorithmic": f"{nm2l} M2L pairs x 2K^2 + {pairs} P2P pairs x {P2P_FLOPS_PER_PAIR} flops",
+                    "peak_source": fp64_src if prec in (0, 1) else fp32_src})
+        return out
+    if "p2p" in stage_ms and pairs > 0:
+        t = stage_ms["p2p"] * 1e-3
+        flops = pairs * float(P2P_FLOPS_PER_PAIR)
+        peak = FP64_TFLOPS_MEASURED if prec == 0 else fp32_peak
+        out.append({"kernel": "k_p2p", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": TRAFFIC["k_p2p"],
+                    "ms": stage_ms["p2p"],
+                    "algorithmic": f"{pairs} pair interactions x {P2P_FLOPS_PER_PAIR} flops",
+                    "peak_source": fp64_src if prec == 0 else fp32_src})
+    if prec == 3 and info is not None and info.tc_pairs > 0 and "m2l_tc" in stage_ms:
+        t = stage_ms["m2l_tc"] * 1e-3
         kp = ((P + 1) * (P + 2) + 15) // 16 * 16
         useful = info.tc_pairs * 2.0 * K * K
         issued = info.tc_items * 128 * 2.0 * kp * kp * 3
-        peak = pk["bf16_tflops"]
-        return {"kernel": "k_m2l_tc", "bound": "tensor", "achieved": useful / t_tc / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "frac": useful / t_tc / 1e12 / peak, "traffic": None,
-                "algorithmic": f"{info.tc_pairs} tensor-core M2L pairs x 2K^2 flops, K=(p+1)^2={K}",
-                "issued_frac": issued / t_tc / 1e12 / peak,
-                "peak_source": f"bf16 dense, {how} (MEASURED_PEAKS.json burst)",
-                "m2l_stage_ms": stage_ms["m2l"], "m2l_tc_ms": stage_ms["m2l_tc"]}
-    if dom == "m2l":
+        peak = float(pk["bf16_tflops"])
+        out.append({"kernel": "k_m2l_tc", "bound": "tensor", "achieved": useful / t / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "frac": useful / t / 1e12 / peak, "traffic": TRAFFIC["k_m2l_tc"],
+                    "ms": stage_ms["m2l_tc"],
+                    "algorithmic": f"{info.tc_pairs} M2L pairs x 2K^2 flops, K=(p+1)^2={K}",
+                    "issued_frac": issued / t / 1e12 / peak,
+                    "peak_source": f"bf16 dense, {how} (MEASURED_PEAKS.json burst)"})
+    elif "m2l" in stage_ms:
+        t = stage_ms["m2l"] * 1e-3
+        nm2l = len(ex["m2l"])
         flops = nm2l * 2.0 * K * K
-        peak = fp64_peak if prec in (0, 1) else fp32_peak
-        return {"kernel": "k_m2l_generic", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
-                "algorithmic": f"{nm2l} M2L pairs x 2K^2 flops, K=(p+1)^2={K}",
-                "peak_source": "FP64 FMA probe" if prec in (0, 1) else f"{n_sm} SM x 128 FP32 lanes x 2 x {clk} MHz"}
-    if dom == "p2p":
-        pairs = p2p_pairs(ex)
-        flops = pairs * float(P2P_FLOPS_PER_PAIR)
-        peak = fp64_peak if prec == 0 else fp32_peak
-        return {"kernel": "k_p2p", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": flops / t / 1e12 / peak, "traffic": None,
-                "algorithmic": f"{pairs} pair interactions x {P2P_FLOPS_PER_PAIR} flops",
-                "peak_source": "FP64 FMA probe" if prec == 0 else f"{n_sm} SM x 128 FP32 lanes x 2 x {clk} MHz"}
-    return {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": None,
-            "traffic": None}
-
-
-# FP64 FMA throughput of one GB300 from the probe kernel (TFLOP/s at the loaded clock)
-FP64_TFLOPS_MEASURED = 1.2
+        peak = FP64_TFLOPS_MEASURED if prec in (0, 1) else fp32_peak
+        out.append({"kernel": "k_m2l_generic", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None, "ms": stage_ms["m2l"],
+                    "algorithmic": f"{nm2l} M2L pairs x 2K^2 flops, K=(p+1)^2={K}",
+                    "peak_source": fp64_src if prec in (0, 1) else fp32_src})
+    return out
 
 
 def run_ours(args):
@@ -251,7 +266,6 @@ def run_ours(args):
     tt.close()
     err_phi = float(((phi - phi64).norm() / phi64.norm()).item())
     err_f = float(((force - f64).norm() / f64.norm()).item())
-    del phi64, f64
 
     for _ in range(args.warmup):
         step().close()
@@ -286,7 +300,38 @@ def run_ours(args):
     value = job_throughput(n, world, args.steps, total_s)
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
     props = torch.cuda.get_device_properties(dev)
-    roof = roofline(stage_ms, ex, args.precision, clocks.get("sm_mhz"), props.multi_processor_count, info)
+    roofs = kernel_rooflines(stage_ms, ex, args.precision, props.multi_processor_count, info)
+    roof = max(roofs, key=lambda r: r["ms"]) if roofs else None
+
+    # the other precisions on the same system, a few steps each (context for the
+    # headline: the plain FP64 GPU path is the accuracy reference)
+    variants = {}
+    if not args.no_variants:
+        for vp in (0, 1, 2):
+            if vp == args.precision:
+                continue
+            vsteps = 2 if vp in (0, 1) else 3
+            step_v = lambda: fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=vp)  # noqa: E731
+            tv = step_v()
+            pv, fv = tv.evaluate(q)
+            tv.close()
+            torch.cuda.synchronize()
+            ms = 0.0
+            for _ in range(vsteps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tv = step_v()
+                tv.evaluate(q, phi=phi, force=force)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1) / vsteps
+                tv.close()
+            variants[PREC_NAMES[vp]] = {
+                "value": n / (ms * 1e-3), "ms_per_step": ms, "steps": vsteps, "dtype": PREC_DTYPE[vp],
+                "rel_l2_vs_fp64_gpu": {"phi": float(((pv - phi64).norm() / phi64.norm()).item()),
+                                       "force": float(((fv - f64).norm() / f64.norm()).item())}}
+            del pv, fv
 
     # end to end through the public API with host buffers
     e2e = None
@@ -344,7 +389,8 @@ def run_ours(args):
                                                 if k in ("prepare", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p",
                                                          "queue")), 4),
                        "wall_s": wall},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "roofline": roof, "rooflines": roofs, "variants": variants, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(out), flush=True)
     if world > 1:

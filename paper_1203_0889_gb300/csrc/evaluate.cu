@@ -118,6 +118,109 @@ __global__ void __launch_bounds__(128) k_shift_dense(int p, int lb, int le, int 
     shift_cell<T, RQ, false>(p, c, kind, lane, child_first, child_count, parent, ckey, ops, E, xin);
 }
 
+// FP32, many destination cells (the fine levels): block (x, o) takes the
+// (destination, input) pairs of octant o among destination cells
+// lb + ndst x ... + ndst - 1 (M2M: a parent and its child in octant o; L2L: a
+// child in octant o and its parent).  Pairs go through in chunks of 32 rows;
+// thread (lane, warp g) computes outputs lane + 32 q of rows 4 g .. 4 g + 3
+// with the octant's operator read through L1.  M2M results from the eight
+// octants meet by FP32 atomics in parents zeroed beforehand; an L2L
+// destination has one octant and is updated in place.
+constexpr int SHO_THREADS = 256, SHO_CHUNK = 32;
+static int shift_oct_ndst(int kind) { return kind == 0 ? 32 : 256; }
+
+template <int RQ>
+__global__ void __launch_bounds__(SHO_THREADS) k_shift_oct(int p, int lb, int le, int kind, int ndst,
+                                                           const int32_t* __restrict__ child_first,
+                                                           const int32_t* __restrict__ child_count,
+                                                           const int32_t* __restrict__ parent,
+                                                           const uint64_t* __restrict__ ckey,
+                                                           const float* __restrict__ ops, cplx<float>* __restrict__ E) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int K2 = 2 * ntri(p), ld = 2 * kstride(p);
+    float* xin = reinterpret_cast<float*>(smem_raw);
+    int* pd = reinterpret_cast<int*>(xin + (size_t)SHO_CHUNK * K2);   // destination cell
+    int* ps = pd + ndst;                                                 // input cell
+    __shared__ int npair;
+    float* Ef = reinterpret_cast<float*>(E);
+    const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5, o = blockIdx.y;
+    const int c0 = lb + blockIdx.x * ndst, nd = min(ndst, le - c0);
+    if (tid == 0) npair = 0;
+    __syncthreads();
+    for (int d = tid; d < nd; d += SHO_THREADS) {
+        const int c = c0 + d;
+        int src = -1;
+        if (kind == 0) {
+            const int f = child_first[c], nc = child_count[c];
+            for (int k = 0; k < nc; k++)
+                if ((int)(ckey[f + k] & 7) == o) { src = f + k; break; }
+        } else if ((int)(ckey[c] & 7) == o) {
+            src = parent[c];
+        }
+        if (src >= 0) {
+            const int slot = atomicAdd(&npair, 1);
+            pd[slot] = c;
+            ps[slot] = src;
+        }
+    }
+    __syncthreads();
+    const int np = npair;
+    const float* op = ops + (size_t)(kind * 8 + o) * K2 * K2;
+    for (int pc = 0; pc < np; pc += SHO_CHUNK) {
+        const int npc = min(SHO_CHUNK, np - pc);
+        for (int e = tid; e < npc * K2; e += SHO_THREADS) {
+            const int r = e / K2, i = e - r * K2;
+            xin[e] = Ef[(size_t)ps[pc + r] * ld + i];
+        }
+        __syncthreads();
+        if (4 * g < npc) {
+            float a[4][RQ];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int q = 0; q < RQ; q++) a[u][q] = 0.f;
+            for (int i = 0; i < K2; i++) {
+                float w[RQ];
+#pragma unroll
+                for (int q = 0; q < RQ; q++) {
+                    const int j = lane + 32 * q;
+                    w[q] = j < K2 ? __ldg(op + (size_t)i * K2 + j) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const float x = xin[(4 * g + u) * K2 + i];
+#pragma unroll
+                    for (int q = 0; q < RQ; q++) a[u][q] = fmaf(w[q], x, a[u][q]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int r = 4 * g + u;
+                if (r < npc) {
+                    float* er = Ef + (size_t)pd[pc + r] * ld;
+#pragma unroll
+                    for (int q = 0; q < RQ; q++) {
+                        const int j = lane + 32 * q;
+                        if (j < K2) {
+                            if (kind == 0) atomicAdd(er + j, a[u][q]);
+                            else er[j] += a[u][q];
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// M of the cells with children set to zero (their M2M results are sums of
+// atomics); leaves keep the multipoles P2M wrote
+__global__ void k_zero_parents(int64_t ncell, int ld, const int32_t* __restrict__ child_count, float* __restrict__ M) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= ncell * ld) return;
+    if (child_count[e / ld] > 0) M[e] = 0.f;
+}
+
 // one block per destination cell of one level (NW warps)
 template <typename T, int RQ, int NW>
 __global__ void __launch_bounds__(32 * NW) k_shift_block(int p, int lb, int le, int kind,
@@ -277,6 +380,9 @@ static int launch_shift(fmm_tree* t, int kind, int lb, int le, cplx<T>* E, cudaS
     const int NWB = kind == 0 ? 8 : 4;
     size_t smem = block_mode ? (size_t)2 * NWB * K2 * sizeof(T) : (size_t)W * K2 * sizeof(T);
     unsigned grid = block_mode ? (unsigned)(le - lb) : nblk(le - lb, W);
+    // many cells, FP32: one block per (run of destination cells, octant)
+    const int ndst = shift_oct_ndst(kind);
+    const size_t osmem = sizeof(float) * (size_t)SHO_CHUNK * K2 + 2 * sizeof(int) * ndst;
 #define SHIFT_CASE(R)                                                                                         \
     if (rq <= R) {                                                                                            \
         if (block_mode && kind == 0) {                                                                        \
@@ -291,6 +397,10 @@ static int launch_shift(fmm_tree* t, int kind, int lb, int le, cplx<T>* E, cudaS
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));    \
             k_shift_block<T, R, 4><<<grid, 128, smem, st>>>(p, lb, le, kind, d.child_first, d.child_count,     \
                                                             d.parent, d.ckey, ops, E);                        \
+        } else if constexpr (sizeof(T) == 4) {                                                                \
+            k_shift_oct<R><<<dim3(nblk(le - lb, ndst), 8), SHO_THREADS, osmem, st>>>(                         \
+                p, lb, le, kind, ndst, d.child_first, d.child_count, d.parent, d.ckey, (const float*)ops,     \
+                (cplx<float>*)E);                                                                             \
         } else {                                                                                              \
             k_shift_dense<T, R><<<grid, 32 * W, smem, st>>>(p, lb, le, kind, d.child_first, d.child_count,     \
                                                             d.parent, d.ckey, ops, E);                        \
@@ -378,6 +488,12 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     count_launch(t);
     stage_end(t, FMM_STAGE_P2M, st);
     stage_begin(t, FMM_STAGE_M2M, st);
+    if constexpr (sizeof(T) == 4) {
+        const int64_t ldf = 2 * kstride(p);
+        k_zero_parents<<<nblk((int64_t)t->ncell * ldf, 256), 256, 0, st>>>(t->ncell, (int)ldf, d.child_count,
+                                                                          (float*)M);
+        count_launch(t);
+    }
     for (int l = t->nlevel - 2; l >= 0; l--) {
         int rc0 = launch_shift<T>(t, 0, t->level_start[l], t->level_start[l + 1], M, st);
         if (rc0) return rc0;
