@@ -316,6 +316,46 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* c
     return base + v - cnt;
 }
 
+// Block-wide version for three counters at once: every thread of the block
+// calls it; thread t gets the first of its c[k] slots in counter k.  One global
+// atomic per counter per call (the three counters are hot: every warp of the
+// grid appends to them).
+constexpr int TRAV_THREADS = 256;
+__device__ __forceinline__ void block_reserve3(unsigned long long* ctr0, unsigned long long* ctr1,
+                                               unsigned long long* ctr2, const unsigned c[3],
+                                               unsigned long long slot[3]) {
+    __shared__ unsigned wsum[3][TRAV_THREADS / 32];
+    __shared__ unsigned long long base[3];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned v[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        v[k] = c[k];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(FULL, v[k], o);
+            if (lane >= o) v[k] += t;
+        }
+        if (lane == 31) wsum[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int k = threadIdx.x;
+        unsigned tot = 0;
+        for (int w = 0; w < TRAV_THREADS / 32; w++) {
+            const unsigned x = wsum[k][w];
+            wsum[k][w] = tot;   // exclusive prefix over the warps
+            tot += x;
+        }
+        unsigned long long* ctr = k == 0 ? ctr0 : (k == 1 ? ctr1 : ctr2);
+        base[k] = tot ? atomicAdd(ctr, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 3; k++) slot[k] = base[k] + wsum[k][warp] + v[k] - c[k];
+    __syncthreads();   // wsum / base are reused by the next call
+}
+
 __global__ void k_traverse(const int2* __restrict__ front, int64_t nf, const int32_t* __restrict__ lev,
                            const uint64_t* __restrict__ ckey, const int32_t* __restrict__ child_first,
                            const int32_t* __restrict__ child_count, double th2, int2* m2l, int2* p2p,
@@ -362,95 +402,106 @@ __global__ void k_traverse(const int2* __restrict__ front, int64_t nf, const int
     }
 }
 
-// (target, source) packed as target * 2^B + source, B = bits of the cell count,
-// so the sort touches 2B bits
-// All rounds of the breadth-first traversal in one cooperative launch: the
-// blocks process the current frontier, meet at a grid-wide barrier, swap the
-// frontier buffers and go on until the frontier is empty.  Writes are checked
-// against the buffer capacities; on overflow the kernel stops and reports it,
-// and the host reruns the traversal round by round with growing buffers.
 struct TravState {
-    unsigned long long nf, nnext, nm2l, np2p;
-    int overflow, rounds;
+    // frontier sizes, rotating: round r reads front[r % 3] and appends to
+    // front[(r + 1) % 3]; front[(r + 2) % 3] is cleared during round r
+    unsigned long long front[3];
+    unsigned long long nm2l, np2p;
+    // overflow seen in round r goes to ovf[r % 2], read by every thread only at
+    // the top of round r + 1 (after the barrier), so all threads decide alike
+    int ovf[2], rounds;
 };
 
-__device__ __forceinline__ void traverse_pair(int ci, int cj, bool valid, const int32_t* __restrict__ lev,
-                                              const uint64_t* __restrict__ ckey,
-                                              const int32_t* __restrict__ child_first,
-                                              const int32_t* __restrict__ child_count, double th2, int2* m2l,
-                                              int2* p2p, int2* next, TravState* stt, unsigned long long cap_m,
-                                              unsigned long long cap_p, unsigned long long cap_f) {
-    int action = -1, nsplit = 0, split_target = 0;
+// (first child, child count) of every cell, one 8-byte load in the traversal
+__global__ void k_child_pack(int ncell, const int32_t* __restrict__ cf, const int32_t* __restrict__ cc, int2* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) out[c] = make_int2(cf[c], cc[c]);
+}
+
+// The multipole acceptance test on the integer centres: icentre holds twice
+// each centre in units of 2^-22 of the system's side (and the level), so
+// D2 = sum (2 c_i - 2 c_j)^2 and S = s_i + s_j are the same integers the
+// Morton keys give.
+__device__ __forceinline__ void traverse_pair(int ci, int cj, bool valid, const int4* __restrict__ icentre,
+                                              const int2* __restrict__ child, double th2, int2* m2l, int2* p2p,
+                                              int2* next, TravState* stt, unsigned long long* nnext, int* ovf,
+                                              unsigned long long cap_m, unsigned long long cap_p,
+                                              unsigned long long cap_f) {
+    int action = -1, nsplit = 0, split_target = 0, cfirst = 0;
     if (valid) {
-        int li = lev[ci], lj = lev[cj];
-        int64_t si = (int64_t)1 << (FMM_MAX_LEVEL - li), sj = (int64_t)1 << (FMM_MAX_LEVEL - lj);
-        uint64_t ki = ckey[ci], kj = ckey[cj];
-        int64_t D2 = 0;
-        for (int d = 0; d < 3; d++) {
-            int64_t a = 2 * compact3(ki >> d) * si + si;
-            int64_t b = 2 * compact3(kj >> d) * sj + sj;
-            D2 += (a - b) * (a - b);
-        }
-        int64_t S = si + sj;
-        bool accept = (double)(S * S) < __dmul_rn(th2, (double)D2);
-        bool leaf_i = child_count[ci] == 0, leaf_j = child_count[cj] == 0;
+        const int4 a = icentre[ci], b = icentre[cj];
+        const int2 ch_i = child[ci], ch_j = child[cj];
+        const int64_t si = (int64_t)1 << (FMM_MAX_LEVEL - a.w), sj = (int64_t)1 << (FMM_MAX_LEVEL - b.w);
+        const int64_t dx = (int64_t)a.x - b.x, dy = (int64_t)a.y - b.y, dz = (int64_t)a.z - b.z;
+        const int64_t D2 = dx * dx + dy * dy + dz * dz;
+        const int64_t S = si + sj;
+        const bool accept = (double)(S * S) < __dmul_rn(th2, (double)D2);
+        const bool leaf_i = ch_i.y == 0, leaf_j = ch_j.y == 0;
         if (accept) action = 0;
         else if (leaf_i && leaf_j) action = 1;
         else {
             action = 2;
-            split_target = leaf_j || (!leaf_i && li <= lj);
-            nsplit = split_target ? child_count[ci] : child_count[cj];
+            split_target = leaf_j || (!leaf_i && a.w <= b.w);
+            nsplit = split_target ? ch_i.y : ch_j.y;
+            cfirst = split_target ? ch_i.x : ch_j.x;
         }
     }
-    unsigned long long s0 = warp_reserve(&stt->nm2l, action == 0 ? 1u : 0u);
-    unsigned long long s1 = warp_reserve(&stt->np2p, action == 1 ? 1u : 0u);
-    unsigned long long s2 = warp_reserve(&stt->nnext, (unsigned)nsplit);
+    const unsigned cnt[3] = {action == 0 ? 1u : 0u, action == 1 ? 1u : 0u, (unsigned)nsplit};
+    unsigned long long sl[3];
+    block_reserve3(&stt->nm2l, &stt->np2p, nnext, cnt, sl);
+    const unsigned long long s0 = sl[0], s1 = sl[1], s2 = sl[2];
     if (action == 0) {
-        if (s0 < cap_m) m2l[s0] = make_int2(ci, cj); else stt->overflow = 1;
+        if (s0 < cap_m) m2l[s0] = make_int2(ci, cj); else *ovf = 1;
     } else if (action == 1) {
-        if (s1 < cap_p) p2p[s1] = make_int2(ci, cj); else stt->overflow = 1;
+        if (s1 < cap_p) p2p[s1] = make_int2(ci, cj); else *ovf = 1;
     } else if (action == 2) {
-        if (s2 + nsplit > cap_f) { stt->overflow = 1; return; }
+        if (s2 + nsplit > cap_f) { *ovf = 1; return; }
         if (split_target) {
-            int cf = child_first[ci];
-            for (int k = 0; k < nsplit; k++) next[s2 + k] = make_int2(cf + k, cj);
+            for (int k = 0; k < nsplit; k++) next[s2 + k] = make_int2(cfirst + k, cj);
         } else {
-            int cf = child_first[cj];
-            for (int k = 0; k < nsplit; k++) next[s2 + k] = make_int2(ci, cf + k);
+            for (int k = 0; k < nsplit; k++) next[s2 + k] = make_int2(ci, cfirst + k);
         }
     }
 }
 
-__global__ void k_traverse_coop(int2* fa, int2* fb, const int32_t* __restrict__ lev, const uint64_t* __restrict__ ckey,
-                                const int32_t* __restrict__ child_first, const int32_t* __restrict__ child_count,
+// All rounds of the breadth-first traversal in one cooperative launch, one
+// grid-wide barrier per round (the frontier counters rotate, see TravState).
+// Writes are checked against the buffer capacities; on overflow the kernel
+// stops and reports it, and the host reruns the traversal round by round
+// with growing buffers.
+__global__ void k_traverse_coop(int2* fa, int2* fb, const int4* __restrict__ icentre, const int2* __restrict__ child,
                                 double th2, int2* m2l, int2* p2p, TravState* stt, unsigned long long cap_m,
                                 unsigned long long cap_p, unsigned long long cap_f) {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
     const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned long long gtid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned long long wbase = gtid & ~31ull;   // first index of this thread's warp
+    const unsigned long long bbase = (unsigned long long)blockIdx.x * blockDim.x;   // block-uniform loop
     for (int round = 0;; round++) {
         int2* cur = (round & 1) ? fb : fa;
         int2* nxt = (round & 1) ? fa : fb;
-        const unsigned long long nf = *(volatile unsigned long long*)&stt->nf;
-        if (nf == 0 || *(volatile int*)&stt->overflow) break;
-        for (unsigned long long base = wbase; base < nf; base += nthreads) {
-            const unsigned long long i = base + (threadIdx.x & 31);
+        const unsigned long long nf = *(volatile unsigned long long*)&stt->front[round % 3];
+        // overflow of the previous round (written before the barrier only)
+        const int ovf_prev = round > 0 ? *(volatile int*)&stt->ovf[(round + 1) & 1] : 0;
+        if (nf == 0 || ovf_prev) {
+            if (gtid == 0) stt->rounds = round;
+            break;
+        }
+        if (gtid == 0) stt->front[(round + 2) % 3] = 0;
+        unsigned long long* nnext = &stt->front[(round + 1) % 3];
+        int* ovf = &stt->ovf[round & 1];
+        for (unsigned long long base = bbase; base < nf; base += nthreads) {
+            const unsigned long long i = base + threadIdx.x;
             const bool valid = i < nf;
             const int2 pr = valid ? cur[i] : make_int2(0, 0);
-            traverse_pair(pr.x, pr.y, valid, lev, ckey, child_first, child_count, th2, m2l, p2p, nxt, stt, cap_m,
-                          cap_p, cap_f);
-        }
-        grid.sync();
-        if (gtid == 0) {
-            stt->nf = stt->nnext;
-            stt->nnext = 0;
-            stt->rounds = round + 1;
+            traverse_pair(pr.x, pr.y, valid, icentre, child, th2, m2l, p2p, nxt, stt, nnext, ovf, cap_m, cap_p,
+                          cap_f);
         }
         grid.sync();
     }
 }
 
+// (target, source) packed as target * 2^B + source, B = bits of the cell count,
+// so the sort touches 2B bits
 __global__ void k_pack_pairs(const int2* pr, int64_t np, int B, uint64_t* key) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < np) key[i] = ((uint64_t)(uint32_t)pr[i].x << B) | (uint32_t)pr[i].y;
@@ -772,30 +823,33 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         const size_t nc0 = (size_t)t->ncell;
         const size_t cf = std::max<size_t>(1 << 20, 96 * nc0), cm = std::max<size_t>(1 << 22, 640 * nc0),
                      cp = std::max<size_t>(1 << 20, 160 * nc0);
-        int2 *fa = nullptr, *fb = nullptr, *mm = nullptr, *pp = nullptr;
+        int2 *fa = nullptr, *fb = nullptr, *mm = nullptr, *pp = nullptr, *chpk = nullptr;
         TravState* stt = nullptr;
         bool ok = dev_alloc(&fa, cf, nullptr, st) == FMM_OK && dev_alloc(&fb, cf, nullptr, st) == FMM_OK &&
                   dev_alloc(&mm, cm, nullptr, st) == FMM_OK && dev_alloc(&pp, cp, nullptr, st) == FMM_OK &&
+                  dev_alloc(&chpk, (size_t)t->ncell, nullptr, st) == FMM_OK &&
                   dev_alloc((char**)&stt, sizeof(TravState), nullptr, st) == FMM_OK;
         int per_sm = 0;
-        if (ok) ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_coop, 256, 0) == cudaSuccess &&
+        if (ok) ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_coop, TRAV_THREADS, 0) ==
+                         cudaSuccess &&
                      per_sm > 0;
         if (ok) {
-            TravState h0 = {(unsigned long long)nsys, 0ull, 0ull, 0ull, 0, 0};
+            TravState h0 = {{(unsigned long long)nsys, 0ull, 0ull}, 0ull, 0ull, {0, 0}, 0};
             FMM_CUDA_TRY(cudaMemcpyAsync(stt, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
             k_init_frontier<<<nblk(nsys, 128), 128, 0, st>>>(nsys, fa);
+            k_child_pack<<<nblk(t->ncell, 256), 256, 0, st>>>(t->ncell, d.child_first, d.child_count, chpk);
             unsigned long long a_cm = cm, a_cp = cp, a_cf = cf;
-            int32_t *a_lev = d.level, *a_cfirst = d.child_first, *a_ccount = d.child_count;
-            uint64_t* a_ckey = d.ckey;
+            const int4* a_ic = d.icentre;
+            const int2* a_ch = chpk;
             double a_th2 = th2;
-            void* args[] = {&fa, &fb, &a_lev, &a_ckey, &a_cfirst, &a_ccount, &a_th2, &mm, &pp, &stt, &a_cm, &a_cp, &a_cf};
-            dim3 grid(per_sm * t->num_sms), block(256);
+            void* args[] = {&fa, &fb, &a_ic, &a_ch, &a_th2, &mm, &pp, &stt, &a_cm, &a_cp, &a_cf};
+            dim3 grid(per_sm * t->num_sms), block(TRAV_THREADS);
             FMM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_traverse_coop, grid, block, args, 0, st));
-            count_launch(t, 2);
+            count_launch(t, 3);
             TravState h;
             FMM_CUDA_TRY(cudaMemcpyAsync(&h, stt, sizeof(h), cudaMemcpyDeviceToHost, st));
             FMM_CUDA_TRY(cudaStreamSynchronize(st));
-            if (!h.overflow) {
+            if (!h.ovf[0] && !h.ovf[1]) {
                 dev_free(m2l, st); dev_free(p2p, st);
                 m2l = mm; p2p = pp; c_m = cm; c_p = cp;
                 mm = pp = nullptr;
@@ -804,7 +858,7 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
                 nf = 0;   // done
             }
         }
-        dev_free(fa, st); dev_free(fb, st); dev_free(mm, st); dev_free(pp, st);
+        dev_free(fa, st); dev_free(fb, st); dev_free(mm, st); dev_free(pp, st); dev_free(chpk, st);
         if (stt) cudaFreeAsync(stt, st);
     }
     while (nf > 0) {
