@@ -51,8 +51,10 @@ __device__ __forceinline__ uint64_t pair_class_key(const int2 pr, const int4* __
     const int dl = a.w - b.w;
     uint64_t key = NOT_TC | (uint64_t)(uint32_t)pr.x;
     if (dl <= TC_MAX_DL && dl >= -TC_MAX_DL) {
-        const int64_t mn = (int64_t)1 << (FMM_MAX_LEVEL - max(a.w, b.w));  // side of the smaller cell, units u
-        const int64_t v[3] = {((int64_t)a.x - b.x) / mn, ((int64_t)a.y - b.y) / mn, ((int64_t)a.z - b.z) / mn};
+        // offset in units of the smaller cell's side 2^sh: twice-centre differences
+        // are exact multiples of it, so the arithmetic shift divides exactly
+        const int sh = FMM_MAX_LEVEL - max(a.w, b.w);
+        const int64_t v[3] = {((int64_t)a.x - b.x) >> sh, ((int64_t)a.y - b.y) >> sh, ((int64_t)a.z - b.z) >> sh};
         bool fits = true;
         for (int d = 0; d < 3; d++) fits = fits && v[d] > -32768 && v[d] < 32768;
         if (fits)
@@ -117,7 +119,7 @@ __global__ void k_csr_from_targets(const int32_t* tgt, int64_t np, int ncell, in
 // ---- grouping by hashing: class key -> slot of an open-addressing table;
 // sorting the (few) occupied slots numbers the classes in key order, and a
 // stable sort of the pairs on these short class ids groups them.
-constexpr int CLASS_HASH_BITS = 18;
+constexpr int CLASS_HASH_BITS = 17;
 constexpr int CLASS_HASH_PROBES = 256;
 constexpr uint64_t HASH_EMPTY = ~0ull;
 
