@@ -60,8 +60,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=1 << 17)
-    ap.add_argument("--workload", default="plummer", choices=["plummer", "batched"],
-                    help="plummer: one 1M-particle system (default); batched: 512 systems of 1024..65536")
+    ap.add_argument("--workload", default="plummer", choices=["plummer", "batched", "table"],
+                    help="plummer: one 1M-particle system (default); batched: 512 systems of 1024..65536; "
+                         "table: every configuration against the oracle (context, several minutes)")
     return ap.parse_args()
 
 
@@ -522,12 +523,128 @@ def run_batched(args):
     print(json.dumps(out), flush=True)
 
 
+def run_table(args):
+    """Every configuration of the workload set on this GPU: throughput of the
+    FP64 and reduced-precision forms (tree build + evaluation per step), their
+    error against the FP64 oracle on sampled leaves, and the oracle itself on
+    the host cores (bounded samples of the same recipes).  One JSON line plus a
+    markdown table on stderr."""
+    import torch
+
+    import oracle
+    import paper_1203_0889_gb300 as fmm
+    import workloads as W
+
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    cores = os.cpu_count() or 1
+    out = {"table": [], "cores": cores}
+
+    def gpu_rate(pos, q, prec, p, leaf, theta, steps):
+        res = None
+        for k in range(steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            t = fmm.build_tree(pos, p=p, leaf_size=leaf, theta=theta, precision=prec)
+            phi, f = t.evaluate(q)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            t.close()
+            if k == 0:
+                res = (phi.double().cpu().numpy(), f.double().cpu().numpy(), [])
+            else:
+                res[2].append(dt)
+        return res[0], res[1], statistics.median(res[2])
+
+    def cpu_rate(name, n, threads):
+        wl = W.make_workload(name, n=n)
+        t0 = time.perf_counter()
+        T = oracle.build_tree(wl.pos, wl.leaf_size, wl.theta)
+        T.evaluate(wl.p, wl.q, nthreads=threads)
+        return n / (time.perf_counter() - t0)
+
+    for name in ("uniform", "plummer", "clustered", "gradient"):
+        wl = W.make_workload(name)
+        n, p, leaf, theta = wl.n, wl.p, wl.leaf_size, wl.theta
+        T = oracle.Tree(wl.pos, leaf, theta)
+        leaves = np.nonzero(T.is_leaf)[0]
+        pick = np.random.default_rng(1203).choice(leaves, size=min(64, len(leaves)), replace=False)
+        idx, phi_ref, grad_ref = T.evaluate_leaves(p, wl.q, np.sort(pick))
+        f_ref = -wl.q[idx, None] * grad_ref
+        pos = torch.tensor(wl.pos, dtype=torch.float64, device=dev)
+        q = torch.tensor(wl.q, dtype=torch.float64, device=dev)
+        row = {"config": name, "n": n, "p": p, "leaf": leaf, "theta": theta, "sampled_particles": int(len(idx))}
+        for prec in (0, 2, 3):
+            phi, f, dt = gpu_rate(pos, q, prec, p, leaf, theta, steps=2 if prec == 0 else 3)
+            row[PREC_NAMES[prec]] = {
+                "particles_per_s": n / dt, "ms_per_step": dt * 1e3,
+                "rel_l2_vs_oracle": {"phi": float(np.linalg.norm(phi[idx] - phi_ref) / np.linalg.norm(phi_ref)),
+                                     "force": float(np.linalg.norm(f[idx] - f_ref) / np.linalg.norm(f_ref))}}
+        del T
+        row["oracle_all_cores"] = cpu_rate(name, min(n, 1 << 17), cores)
+        row["oracle_1_core"] = cpu_rate(name, min(n, 1 << 14), 1)
+        if name == "gradient":
+            # forward + backward through the autograd node (FP32), L = sum w phi
+            fn = fmm.FMMFunction
+            w = torch.tensor(wl.extra["w"], dtype=torch.float32, device=dev)
+            pos32 = pos.clone().requires_grad_(True)
+            q32 = q.float().requires_grad_(True)
+            ts = []
+            for k in range(4):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                t = fmm.build_tree(pos32.detach(), p=p, leaf_size=leaf, theta=theta, precision=fmm.PREC_FP32,
+                                   flags=fmm.OUT_FIELD)
+                loss = (fn.apply(pos32, q32, t) * w).sum()
+                loss.backward()
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+                t.close()
+                pos32.grad = None
+                q32.grad = None
+            row["forward_backward_fp32_particles_per_s"] = n / statistics.median(ts[1:])
+        out["table"].append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    # batched systems (FP32, task queue), build + evaluate per step
+    systems = W.make_batched(512)
+    sizes = np.array([len(s_[1]) for s_ in systems], np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    pos = torch.tensor(np.concatenate([s_[0] for s_ in systems]), dtype=torch.float64, device=dev)
+    q = torch.tensor(np.concatenate([s_[1] for s_ in systems]), dtype=torch.float32, device=dev)
+    ts = []
+    for k in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t = fmm.build_tree_batched(pos, off, p=6, leaf_size=32, theta=0.5, precision=fmm.PREC_FP32)
+        t.evaluate(q)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+        t.close()
+    out["table"].append({"config": "batched", "n": int(off[-1]), "systems": 512, "p": 6,
+                         "fp32": {"particles_per_s": int(off[-1]) / statistics.median(ts[1:])}})
+    print(json.dumps(out), flush=True)
+    lines = ["| config | N | GPU FP64 p/s | GPU FP32 p/s | GPU mixed p/s | error FP64 / FP32 / mixed (phi, F) vs oracle "
+             f"| oracle {cores} cores p/s | oracle 1 core p/s |", "|---|---|---|---|---|---|---|---|"]
+    for r in out["table"]:
+        if r["config"] == "batched":
+            lines.append(f"| batched 512 | {r['n']} | | {r['fp32']['particles_per_s']:.3g} | | | | |")
+            continue
+        e = " / ".join(f"{r[k]['rel_l2_vs_oracle']['phi']:.1e}, {r[k]['rel_l2_vs_oracle']['force']:.1e}"
+                       for k in ("fp64", "fp32", "mixed_tc"))
+        lines.append(f"| {r['config']} | {r['n']} | {r['fp64']['particles_per_s']:.3g} | "
+                     f"{r['fp32']['particles_per_s']:.3g} | {r['mixed_tc']['particles_per_s']:.3g} | {e} | "
+                     f"{r['oracle_all_cores']:.3g} | {r['oracle_1_core']:.3g} |")
+    print("\n".join(lines), file=sys.stderr, flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "table":
+        run_table(args)
     else:
         run_ours(args)
 
