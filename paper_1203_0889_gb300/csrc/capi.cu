@@ -32,7 +32,7 @@ int check_params(const fmm_params* prm) {
         fmm_set_error("unknown precision %d", prm->precision);
         return FMM_ERR_ARG;
     }
-    if (prm->flags & ~(FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING)) { fmm_set_error("unknown flags 0x%x", prm->flags); return FMM_ERR_ARG; }
+    if (prm->flags & ~(FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP)) { fmm_set_error("unknown flags 0x%x", prm->flags); return FMM_ERR_ARG; }
     if (prm->timeout_ns < 0) { fmm_set_error("timeout_ns < 0"); return FMM_ERR_ARG; }
     return FMM_OK;
 }
@@ -117,6 +117,15 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
             if (t->ev_join) cudaEventDestroy(t->ev_join);
             t->side_stream = nullptr; t->ev_fork = nullptr; t->ev_join = nullptr; t->ev_ops = nullptr;
         }
+        int least = 0, greatest = 0;
+        if (t->side_stream && (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+                               cudaStreamCreateWithPriority(&t->hi_stream, cudaStreamNonBlocking, greatest) !=
+                                   cudaSuccess ||
+                               cudaEventCreateWithFlags(&t->ev_join_hi, cudaEventDisableTiming) != cudaSuccess)) {
+            cudaGetLastError();
+            if (t->hi_stream) cudaStreamDestroy(t->hi_stream);
+            t->hi_stream = nullptr; t->ev_join_hi = nullptr;
+        }
     }
     rc = fmm::build_tree_impl(t, pos, pos_dtype, st);
     if (!rc) rc = fmm::alloc_eval_workspace(t, st);
@@ -130,8 +139,10 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
         fmm::free_tree_device(t);
         if (t->timing) for (int i = 0; i < 2 * FMM_NUM_STAGES; i++) cudaEventDestroy(t->ev[i]);
         if (t->side_stream) cudaStreamDestroy(t->side_stream);
+        if (t->hi_stream) cudaStreamDestroy(t->hi_stream);
         if (t->ev_fork) cudaEventDestroy(t->ev_fork);
         if (t->ev_join) cudaEventDestroy(t->ev_join);
+        if (t->ev_join_hi) cudaEventDestroy(t->ev_join_hi);
         if (t->ev_ops) cudaEventDestroy(t->ev_ops);
         delete t;
         return rc;
@@ -331,10 +342,13 @@ void fmm_tree_destroy(fmm_tree* t) {
     if (!t) return;
     cudaDeviceSynchronize();
     if (t->side_stream) cudaStreamSynchronize(t->side_stream);
+    if (t->hi_stream) cudaStreamSynchronize(t->hi_stream);
     fmm::free_tree_device(t);
     cudaStreamSynchronize(0);
     if (t->timing) for (int i = 0; i < 2 * FMM_NUM_STAGES; i++) cudaEventDestroy(t->ev[i]);
     if (t->side_stream) cudaStreamDestroy(t->side_stream);
+    if (t->hi_stream) cudaStreamDestroy(t->hi_stream);
+    if (t->ev_join_hi) cudaEventDestroy(t->ev_join_hi);
     if (t->ev_fork) cudaEventDestroy(t->ev_fork);
     if (t->ev_join) cudaEventDestroy(t->ev_join);
     if (t->ev_ops) cudaEventDestroy(t->ev_ops);

@@ -438,6 +438,9 @@ static int launch_m2l_generic(fmm_tree* t, int p, int t0, int t1, const int64_t*
     return FMM_ERR_ARG;
 }
 
+template <typename T>
+static int far_field(fmm_tree* t, cplx<T>* M, cplx<T>* L, const double4_32a* xq64, cudaStream_t st);
+
 template <typename T, typename Q, typename O>
 static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_t st) {
     const int p = t->prm.p, K = ntri(p);
@@ -465,8 +468,9 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     // P2P (near field) depends on nothing but the particles: it runs on the
     // tree's second stream, concurrently with the upward pass, M2L and L2L,
     // and joins before L2P (the far field and the near field meet there)
-    cudaStream_t sp = t->side_stream ? t->side_stream : st;
-    if (t->side_stream) {
+    const bool overlap = !(t->prm.flags & FMM_NO_OVERLAP);
+    cudaStream_t sp = (overlap && t->side_stream) ? t->side_stream : st;
+    if (sp != st) {
         FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
         FMM_CUDA_TRY(cudaStreamWaitEvent(sp, t->ev_fork, 0));
     }
@@ -479,7 +483,38 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
                                                          d.p2p_rec, xq32, d.icentre, d.cu2f, d.near);
     count_launch(t);
     stage_end(t, FMM_STAGE_P2P, sp);
-    if (t->side_stream) FMM_CUDA_TRY(cudaEventRecord(t->ev_join, sp));
+    if (sp != st) FMM_CUDA_TRY(cudaEventRecord(t->ev_join, sp));
+    // the far-field chain on the high-priority stream (joined before L2P)
+    cudaStream_t sf = st;
+    if (overlap && sp != st && t->hi_stream && t->ev_join_hi) {
+        sf = t->hi_stream;
+        FMM_CUDA_TRY(cudaStreamWaitEvent(sf, t->ev_fork, 0));
+    }
+    {
+        const int rcf = far_field<T>(t, M, L, xq64, sf);
+        if (rcf) return rcf;
+    }
+    if (sf != st) {
+        FMM_CUDA_TRY(cudaEventRecord(t->ev_join_hi, sf));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join_hi, 0));
+    }
+    if (sp != st) FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
+    const int W = 4;
+    stage_begin(t, FMM_STAGE_L2P, st);
+    k_l2p_finalize<T, O><<<nblk(t->nleaf, W), 32 * W, W * K * sizeof(cplx<T>), st>>>(
+        p, t->nleaf, d.leaves, d.first, d.count, d.centre, xq64, d.perm, L, d.near, phi, force,
+        (t->prm.flags & FMM_OUT_FIELD) ? 1 : 0);
+    count_launch(t);
+    stage_end(t, FMM_STAGE_L2P, st);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+// P2M, M2M, M2L and L2L of the stage-by-stage path, all on stream st
+template <typename T>
+static int far_field(fmm_tree* t, cplx<T>* M, cplx<T>* L, const double4_32a* xq64, cudaStream_t st) {
+    const TreeDev& d = t->d;
+    const int p = t->prm.p, K = ntri(p);
     // upward pass
     const int W = 4;
     stage_begin(t, FMM_STAGE_P2M, st);
@@ -520,13 +555,6 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
         if (rc) return rc;
     }
     stage_end(t, FMM_STAGE_L2L, st);
-    if (t->side_stream) FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
-    stage_begin(t, FMM_STAGE_L2P, st);
-    k_l2p_finalize<T, O><<<nblk(t->nleaf, W), 32 * W, W * K * sizeof(cplx<T>), st>>>(
-        p, t->nleaf, d.leaves, d.first, d.count, d.centre, xq64, d.perm, L, d.near, phi, force,
-        (t->prm.flags & FMM_OUT_FIELD) ? 1 : 0);
-    count_launch(t);
-    stage_end(t, FMM_STAGE_L2P, st);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }

@@ -195,6 +195,11 @@ struct fmm_tree {
     // recorded on side_stream after the tensor-core class operators are built
     // (they are computed there, overlapping the rest of the build)
     cudaEvent_t ev_ops = nullptr;
+    // the far-field chain of the stage-by-stage path (P2M, M2M, M2L, L2L) runs on
+    // a high-priority stream, so that its short, latency-bound kernels get SMs
+    // as soon as P2P blocks retire instead of queueing behind the whole P2P grid
+    cudaStream_t hi_stream = nullptr;
+    cudaEvent_t ev_join_hi = nullptr;
     int64_t* launch_ctr = nullptr;  // which counter launches currently go to
     int64_t n = 0;
     int ncell = 0, nlevel = 0, nleaf = 0;

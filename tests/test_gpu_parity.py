@@ -141,3 +141,21 @@ def test_tensor_core_graph_replay_and_early_destroy():
     assert t.status() == fmm.FMM_OK
     assert ((phi - eager_phi).norm() / eager_phi.norm()).item() <= 1e-6
     assert ((force - eager_f).norm() / eager_f.norm()).item() <= 1e-6
+
+
+def test_no_overlap_flag_same_result():
+    """FMM_NO_OVERLAP runs P2P and the far field one after the other on the
+    caller's stream; the result is the same as with the overlapped streams
+    (up to the order of the FP32 atomics)."""
+    import paper_1203_0889_gb300 as fmm
+    torch, dev = torch_dev()
+    wl = W.make_workload("plummer", n=40000)
+    pos = torch.tensor(wl.pos, dtype=torch.float64, device=dev)
+    q = torch.tensor(wl.q, dtype=torch.float32, device=dev)
+    for prec in (fmm.PREC_MIXED_TC, fmm.PREC_FP32):
+        a = fmm.build_tree(pos, p=8, leaf_size=64, theta=0.4, precision=prec, flags=fmm.STAGED)
+        b = fmm.build_tree(pos, p=8, leaf_size=64, theta=0.4, precision=prec, flags=fmm.STAGED | fmm.NO_OVERLAP)
+        pa, fa = a.evaluate(q)
+        pb, fb = b.evaluate(q)
+        assert ((pa - pb).norm() / pa.norm()).item() <= 1e-6
+        assert ((fa - fb).norm() / fa.norm()).item() <= 1e-6
