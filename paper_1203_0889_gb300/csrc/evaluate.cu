@@ -286,9 +286,10 @@ __global__ void __launch_bounds__(128) k_m2l_generic(int p, int t0, int t1, cons
     }
 }
 
-// one block per target leaf
+// one block per target leaf (FP32: registers capped for 9 resident blocks per
+// SM, measured 2 % faster than the uncapped 62 registers)
 template <typename T>
-__global__ void __launch_bounds__(P2P_THREADS) k_p2p(int nleaf, const int32_t* __restrict__ leaves,
+__global__ void __launch_bounds__(P2P_THREADS, sizeof(T) == 4 ? 9 : 1) k_p2p(int nleaf, const int32_t* __restrict__ leaves,
                                                      const int32_t* __restrict__ first,
                                                      const int32_t* __restrict__ count,
                                                      const int64_t* __restrict__ start,

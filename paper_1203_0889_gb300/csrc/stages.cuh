@@ -363,16 +363,29 @@ __device__ __forceinline__ u64 fma(u64 a, u64 b, u64 c) {
 // The source is staged negated and duplicated: s01 = (-x, -x | -y, -y),
 // s23 = (-z, -z | -q, -q), so that d = X + (-x) and the negated potential
 // and field accumulate with adds and fmas only (NP = -phi, G = the field
-// term, both per half).
+// term, both per half).  GUARD: a distance at or below FLT_MIN counts as
+// coincident and contributes nothing (the target leaf's own particles).
+// Without it (every other leaf, staged with the target leaf's own particles
+// at zero charge) r^2 starts from 1e-30 instead of 0: a zero-charge copy of
+// the target itself then contributes exactly 0, a near-duplicate across a
+// leaf boundary stays finite, and no other pair changes (its r^2 is many
+// orders larger).
+template <bool GUARD>
 __device__ __forceinline__ void p2p_pair_x2(f2::u64 X, f2::u64 Y, f2::u64 Z, const ulonglong2 s01,
                                             const ulonglong2 s23, f2::u64& NP, f2::u64& GX, f2::u64& GY,
                                             f2::u64& GZ) {
     const f2::u64 dx = f2::add(X, s01.x), dy = f2::add(Y, s01.y), dz = f2::add(Z, s23.x);
-    const f2::u64 r2 = f2::fma(dz, dz, f2::fma(dy, dy, f2::mul(dx, dx)));
+    const f2::u64 r0 = GUARD ? 0ull : f2::pack(1e-30f, 1e-30f);
+    const f2::u64 r2 = f2::fma(dz, dz, f2::fma(dy, dy, f2::fma(dx, dx, r0)));
     float ra, rb;
     f2::unpack(r2, ra, rb);
-    ra = ra > pair_floor(ra) ? rsqrt_t(ra) : 0.f;
-    rb = rb > pair_floor(rb) ? rsqrt_t(rb) : 0.f;
+    if (GUARD) {
+        ra = ra > pair_floor(ra) ? rsqrt_t(ra) : 0.f;
+        rb = rb > pair_floor(rb) ? rsqrt_t(rb) : 0.f;
+    } else {
+        ra = rsqrt_t(ra);
+        rb = rsqrt_t(rb);
+    }
     const f2::u64 rinv = f2::pack(ra, rb);
     const f2::u64 nqr = f2::mul(s23.y, rinv);
     NP = f2::add(NP, nqr);
@@ -454,8 +467,9 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
                     const V v = shift_src(xq[r.x + k], o);
                     if constexpr (sizeof(T) == 4) {
                         float4* b2 = reinterpret_cast<float4*>(buf) + 2 * (r.z + k - base);
+                        const float nq = r.w == c ? 0.f : -v.w;   // own leaf: added below, guarded
                         b2[0] = make_float4(-v.x, -v.x, -v.y, -v.y);
-                        b2[1] = make_float4(-v.z, -v.z, -v.w, -v.w);
+                        b2[1] = make_float4(-v.z, -v.z, nq, nq);
                     } else {
                         buf[r.z + k - base] = v;
                     }
@@ -467,7 +481,7 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
                     const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(buf);
 #pragma unroll 4
                     for (int j = sub; j < lim; j += G)
-                        p2p_pair_x2(X, Y, Z, b2[2 * j], b2[2 * j + 1], NP, GX, GY, GZ);
+                        p2p_pair_x2<false>(X, Y, Z, b2[2 * j], b2[2 * j + 1], NP, GX, GY, GZ);
                 } else {
                     int j = sub;
                     for (; j + G < lim; j += 2 * G) {
@@ -492,6 +506,15 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
             }
         }
         if constexpr (sizeof(T) == 4) {
+            // the target leaf's own particles (same leaf frame, no shift), guarded
+            if (active) {
+                for (int j = sub; j < nt; j += G) {
+                    const V s = xq[tf + j];
+                    const ulonglong2 s01 = make_ulonglong2(f2::pack(-s.x, -s.x), f2::pack(-s.y, -s.y));
+                    const ulonglong2 s23 = make_ulonglong2(f2::pack(-s.z, -s.z), f2::pack(-s.w, -s.w));
+                    p2p_pair_x2<true>(X, Y, Z, s01, s23, NP, GX, GY, GZ);
+                }
+            }
             float a, b;
             f2::unpack(NP, a, b); ph[0] = -a; ph[1] = -b;
             f2::unpack(GX, a, b); gx[0] = a; gx[1] = b;

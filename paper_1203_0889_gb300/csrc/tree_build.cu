@@ -211,33 +211,89 @@ __device__ __forceinline__ int octant_end(const uint64_t* keys, int f, int e, ui
     return a;
 }
 
-__global__ void k_count_children(int lb, int le, int level, int leaf_size, const int32_t* first,
+// first index in [lo, hi) whose (key >> shift) > lim (hi if none), found by
+// the whole warp with 31 probes per step (all lanes call it with equal
+// arguments; lanes read the result)
+__device__ __forceinline__ int warp_upper_bound(const uint64_t* __restrict__ keys, int lo, int hi, uint64_t lim,
+                                                int shift) {
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        const int step = (hi - lo + 31) / 32;
+        const int pk = lo + (lane + 1) * step;
+        const bool le_ = lane < 31 && pk < hi && (keys[pk] >> shift) <= lim;
+        const int c = __popc(__ballot_sync(0xffffffffu, le_));
+        const int nlo = c > 0 ? lo + c * step + 1 : lo;
+        const int nhi = min(hi, lo + (c + 1) * step);
+        lo = nlo;
+        hi = nhi;
+    }
+    const bool le_ = lo + lane < hi && (keys[lo + lane] >> shift) <= lim;
+    return lo + __popc(__ballot_sync(0xffffffffu, le_));
+}
+
+// Octant boundaries of the cells [lb, le) that split: ends[8 (c - lb) + o] =
+// first particle above octant o.  wide = one warp per (cell, octant) with the
+// 32-way search (narrow levels: few cells, long particle ranges); otherwise
+// 8 lanes per cell, one binary search each.  Then nchild[c - lb] = number of
+// non-empty octants.
+__global__ void k_count_children(int lb, int le, int level, int leaf_size, int wide, const int32_t* first,
                                  const int32_t* count, const uint64_t* ckey, const uint64_t* keys,
-                                 int32_t* nchild) {
+                                 int32_t* ends, int32_t* nchild) {
+    const int shift = 3 * (FMM_MAX_LEVEL - (level + 1));
+    if (wide) {
+        const int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // one warp per (cell, octant)
+        const int c = lb + (u >> 3), o = u & 7;
+        if (c >= le) return;                                           // warp-uniform
+        const int cnt = count[c];
+        if (!(cnt > leaf_size && level < FMM_MAX_LEVEL)) {
+            if ((threadIdx.x & 31) == 0 && o == 0) nchild[c - lb] = 0;
+            return;
+        }
+        const int f = first[c];
+        const int e = warp_upper_bound(keys, f, f + cnt, (ckey[c] << 3) + (uint64_t)o, shift);
+        if ((threadIdx.x & 31) == 0) ends[u] = e;
+        return;
+    }
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     int c = lb + (g >> 3), o = g & 7;
     bool valid = c < le;
     int cnt = valid ? count[c] : 0;
     bool split = valid && cnt > leaf_size && level < FMM_MAX_LEVEL;
     int f = valid ? first[c] : 0;
-    int end = split ? octant_end(keys, f, f + cnt, (ckey[c] << 3) + (uint64_t)o, 3 * (FMM_MAX_LEVEL - (level + 1))) : 0;
+    int end = split ? octant_end(keys, f, f + cnt, (ckey[c] << 3) + (uint64_t)o, shift) : 0;
+    if (split) ends[g] = end;
     int beg = __shfl_up_sync(0xffffffffu, end, 1, 8);
     if (o == 0) beg = f;
     unsigned nonempty = __ballot_sync(0xffffffffu, split && end > beg);
     if (valid && o == 0) nchild[c - lb] = __popc((nonempty >> (threadIdx.x & 24)) & 0xffu);
 }
 
-__global__ void k_emit_children(int lb, int le, int level, int leaf_size, const uint64_t* keys,
-                                const int32_t* nchild, const int32_t* coff, int next_base,
-                                int32_t* lev, uint64_t* ckey, int32_t* first, int32_t* count,
-                                int32_t* parent, int32_t* child_first, int32_t* child_count) {
+// child counts of the wide levels (after the warp searches)
+__global__ void k_count_from_ends(int lb, int le, int level, int leaf_size, const int32_t* first,
+                                  const int32_t* count, const int32_t* ends, int32_t* nchild) {
+    const int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= le) return;
+    const int cnt = count[c];
+    if (!(cnt > leaf_size && level < FMM_MAX_LEVEL)) { nchild[c - lb] = 0; return; }
+    int beg = first[c], k = 0;
+    for (int o = 0; o < 8; o++) {
+        const int e = ends[8 * (c - lb) + o];
+        k += e > beg;
+        beg = e;
+    }
+    nchild[c - lb] = k;
+}
+
+__global__ void k_emit_children(int lb, int le, int level, const int32_t* ends, const int32_t* nchild,
+                                const int32_t* coff, int next_base, int32_t* lev, uint64_t* ckey, int32_t* first,
+                                int32_t* count, int32_t* parent, int32_t* child_first, int32_t* child_count) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     int c = lb + (g >> 3), o = g & 7;
     bool valid = c < le;
     int nc = valid ? nchild[c - lb] : 0;
     int f = valid ? first[c] : 0;
     uint64_t base = valid ? (ckey[c] << 3) : 0;
-    int end = nc ? octant_end(keys, f, f + count[c], base + (uint64_t)o, 3 * (FMM_MAX_LEVEL - (level + 1))) : 0;
+    int end = nc ? ends[g] : 0;
     int beg = __shfl_up_sync(0xffffffffu, end, 1, 8);
     if (o == 0) beg = f;
     bool ne = nc && end > beg;
@@ -711,17 +767,25 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     if ((rc = grow_all(std::max(cap, (size_t)nsys + 64), 0))) return rc;
     k_init_roots<<<nblk(nsys, 128), 128, 0, st>>>(nsys, d.sys_off, lev, ckey, first, count, par);
     count_launch(t);
-    int32_t *nch = nullptr, *coff = nullptr;
-    size_t c_nch = 0, c_coff = 0;
+    int32_t *nch = nullptr, *coff = nullptr, *ends = nullptr;
+    size_t c_nch = 0, c_coff = 0, c_ends = 0;
     int lb = 0, le = nsys, level = 0;
     t->level_start[0] = 0;
     while (true) {
         int width = le - lb;
         if ((rc = grow(nch, c_nch, width, 0, st))) return rc;
         if ((rc = grow(coff, c_coff, width, 0, st))) return rc;
-        k_count_children<<<nblk((int64_t)width * 8, 128), 128, 0, st>>>(lb, le, level, t->prm.leaf_size, first, count,
-                                                             ckey, d.keys, nch);
+        if ((rc = grow(ends, c_ends, (size_t)width * 8, 0, st))) return rc;
+        // a narrow level (few cells, long ranges) searches with a warp per boundary
+        const int wide = (int64_t)width * 8 * 32 <= (int64_t)t->num_sms * 1024 ? 1 : 0;
+        k_count_children<<<nblk((int64_t)width * 8 * (wide ? 32 : 1), 128), 128, 0, st>>>(
+            lb, le, level, t->prm.leaf_size, wide, first, count, ckey, d.keys, ends, nch);
         count_launch(t);
+        if (wide) {
+            k_count_from_ends<<<nblk(width, 128), 128, 0, st>>>(lb, le, level, t->prm.leaf_size, first, count, ends,
+                                                               nch);
+            count_launch(t);
+        }
         size_t sb = 0;
         cub::DeviceScan::ExclusiveSum(nullptr, sb, nch, coff, width, st);
         if ((rc = dev_alloc(&tmp, sb, nullptr, st))) return rc;
@@ -736,8 +800,8 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         if ((size_t)le + total > c_lev) {
             if ((rc = grow_all((size_t)le + total, (size_t)le))) return rc;
         }
-        k_emit_children<<<nblk((int64_t)width * 8, 128), 128, 0, st>>>(lb, le, level, t->prm.leaf_size, d.keys, nch, coff, le,
-                                                            lev, ckey, first, count, par, cf, cc);
+        k_emit_children<<<nblk((int64_t)width * 8, 128), 128, 0, st>>>(lb, le, level, ends, nch, coff, le, lev, ckey,
+                                                                      first, count, par, cf, cc);
         count_launch(t);
         t->level_start[level + 1] = le;
         if (total == 0) break;
@@ -747,6 +811,7 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     }
     dev_free(nch, st);
     dev_free(coff, st);
+    dev_free(ends, st);
     stage_end(t, FMM_STAGE_OCTREE, st);
     stage_begin(t, FMM_STAGE_SETUP, st);
     t->ncell = le;
