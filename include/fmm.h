@@ -59,6 +59,9 @@ extern "C" {
 #define FMM_NO_OVERLAP  8   /* stage-by-stage path: run P2P and the far field one after the other on
                                the caller's stream (by default P2P runs on a second stream and the
                                far-field chain on a high-priority one, joined before L2P) */
+#define FMM_BUILD_FALLBACKS 16 /* diagnostic: build with the paths otherwise taken only when a buffer
+                                  or table overflows (round-by-round traversal, tensor-core classes
+                                  grouped by sorting their keys); same tree and lists */
 
 /* stage indices for fmm_stage_times / fmm_stage_name */
 #define FMM_STAGE_KEYS      0   /* root cube, Morton keys, key sort */
@@ -86,7 +89,7 @@ typedef struct {
                             through M2L iff (s_i + s_j) < theta * |2 (c_i - c_j)|,
                             s = cell side, c = cell centre (Sections 2.1 and 4) */
     int32_t precision;   /* FMM_PREC_* */
-    int32_t flags;       /* FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP */
+    int32_t flags;       /* FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP | FMM_BUILD_FALLBACKS */
     int64_t timeout_ns;  /* budget of each bounded device-side wait; 0 = 2 s */
 } fmm_params;
 

@@ -32,7 +32,7 @@ int check_params(const fmm_params* prm) {
         fmm_set_error("unknown precision %d", prm->precision);
         return FMM_ERR_ARG;
     }
-    if (prm->flags & ~(FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP)) { fmm_set_error("unknown flags 0x%x", prm->flags); return FMM_ERR_ARG; }
+    if (prm->flags & ~(FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP | FMM_BUILD_FALLBACKS)) { fmm_set_error("unknown flags 0x%x", prm->flags); return FMM_ERR_ARG; }
     if (prm->timeout_ns < 0) { fmm_set_error("timeout_ns < 0"); return FMM_ERR_ARG; }
     return FMM_OK;
 }

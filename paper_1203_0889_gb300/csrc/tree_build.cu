@@ -895,6 +895,7 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
                   dev_alloc(&chpk, (size_t)t->ncell, nullptr, st) == FMM_OK &&
                   dev_alloc((char**)&stt, sizeof(TravState), nullptr, st) == FMM_OK;
         int per_sm = 0;
+        if (t->prm.flags & FMM_BUILD_FALLBACKS) ok = false;
         if (ok) ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_coop, TRAV_THREADS, 0) ==
                          cudaSuccess &&
                      per_sm > 0;

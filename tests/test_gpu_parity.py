@@ -159,3 +159,20 @@ def test_no_overlap_flag_same_result():
         pb, fb = b.evaluate(q)
         assert ((pa - pb).norm() / pa.norm()).item() <= 1e-6
         assert ((fa - fb).norm() / fa.norm()).item() <= 1e-6
+
+
+def test_tensor_core_fallback_grouping_same_result():
+    """Classes grouped by sorting their keys (the fallback of the hash grouping)
+    give the same tensor-core M2L result up to the order of the FP32 atomics."""
+    import paper_1203_0889_gb300 as fmm
+    torch, dev = torch_dev()
+    wl = W.make_workload("clustered", n=60000)
+    pos = torch.tensor(wl.pos, dtype=torch.float64, device=dev)
+    q = torch.tensor(wl.q, dtype=torch.float32, device=dev)
+    a = fmm.build_tree(pos, p=8, leaf_size=64, theta=0.5, precision=fmm.PREC_MIXED_TC)
+    b = fmm.build_tree(pos, p=8, leaf_size=64, theta=0.5, precision=fmm.PREC_MIXED_TC, flags=fmm.BUILD_FALLBACKS)
+    pa, fa = a.evaluate(q)
+    pb, fb = b.evaluate(q)
+    assert b.status() == fmm.FMM_OK
+    assert ((pa - pb).norm() / pa.norm()).item() <= 1e-6
+    assert ((fa - fb).norm() / fa.norm()).item() <= 1e-6

@@ -73,3 +73,21 @@ def test_non_finite_positions_rejected():
     with pytest.raises(fmm.FMMError) as e:
         fmm.build_tree(pos, p=3)
     assert e.value.code == fmm.FMM_ERR_ARG
+
+
+@pytest.mark.parametrize("name,n,leaf,theta,prec", [("plummer", 60000, 32, 0.4, 3), ("clustered", 50000, 16, 0.5, 3),
+                                                    ("uniform", 30000, 24, 0.5, 2)])
+def test_build_fallback_paths_bit_exact(name, n, leaf, theta, prec):
+    """FMM_BUILD_FALLBACKS forces the round-by-round traversal and (mixed mode)
+    the sort-based class grouping, which otherwise run only on overflow: the
+    tree and both lists still match the oracle bit for bit, and the class
+    structure matches the default build."""
+    import paper_1203_0889_gb300 as fmm
+    wl = W.make_workload(name, n=n)
+    ref = O.build_tree(wl.pos, leaf, theta)
+    a = gpu_tree(wl.pos, p=6, leaf_size=leaf, theta=theta, precision=prec, flags=fmm.BUILD_FALLBACKS)
+    b = gpu_tree(wl.pos, p=6, leaf_size=leaf, theta=theta, precision=prec)
+    assert_tree_equal(a.export(), ref)
+    assert_tree_equal(b.export(), ref)
+    ia, ib = a.info(), b.info()
+    assert (ia.tc_pairs, ia.tc_classes, ia.tc_items) == (ib.tc_pairs, ib.tc_classes, ib.tc_items)
