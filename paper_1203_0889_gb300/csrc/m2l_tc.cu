@@ -460,7 +460,7 @@ int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st) {
         return FMM_OK;
     }
     bool done = false;
-    if ((rc = classes_by_hash(t, pairs, &done, st))) return rc;
+    if (!(t->prm.flags & FMM_BUILD_FALLBACKS) && (rc = classes_by_hash(t, pairs, &done, st))) return rc;
     if (done) return FMM_OK;
     // grouping by sorting the class keys (tables too crowded for hashing)
     uint64_t *k0 = nullptr, *k1 = nullptr;
