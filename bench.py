@@ -168,7 +168,7 @@ FP64_TFLOPS_MEASURED = 1.256
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands (summaries in profiles/); None once the kernel has changed since.
-TRAFFIC = {"k_p2p": 89188608 + 15778048,        # profiles/k_p2p_plummer1m_p8_fp32.md
+TRAFFIC = {"k_p2p": 89276160 + 15623680,        # profiles/k_p2p_plummer1m_p8_fp32.md
            "k_m2l_tc": 535333376 + 10936832}    # profiles/k_m2l_tc_plummer1m_p8.md
 
 
