@@ -136,6 +136,7 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
     if (rc) {
         cudaStreamSynchronize(st);
         if (t->side_stream) cudaStreamSynchronize(t->side_stream);
+        if (t->hi_stream) cudaStreamSynchronize(t->hi_stream);
         fmm::free_tree_device(t);
         if (t->timing) for (int i = 0; i < 2 * FMM_NUM_STAGES; i++) cudaEventDestroy(t->ev[i]);
         if (t->side_stream) cudaStreamDestroy(t->side_stream);

@@ -947,6 +947,36 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     dev_free(front, st); dev_free(next, st); dev_free(ctr, st);
     t->nm2l = nm;
     t->np2p = npp;
+    // The P2P list and its records go on the second stream of the evaluation's
+    // far field (idle during the build), so they fill the GPU while the host
+    // waits on the M2L/class grouping below; joined before the task queue.
+    cudaStream_t sl = (t->hi_stream && t->ev_join_hi) ? t->hi_stream : st;
+    if (sl != st) {
+        FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(sl, t->ev_fork, 0));
+    }
+    int32_t* p2p_tgt = nullptr;
+    if ((rc = finish_list(t, p2p, npp, &d.p2p_start, &d.p2p_src, &p2p_tgt, sl))) return rc;
+    {
+        int64_t *cnt = nullptr, *gcum = nullptr;
+        if ((rc = dev_alloc(&cnt, (size_t)npp, nullptr, sl))) return rc;
+        if ((rc = dev_alloc(&gcum, (size_t)npp, nullptr, sl))) return rc;
+        if ((rc = dev_alloc(&d.p2p_rec, (size_t)npp, t, sl))) return rc;
+        if (npp) {
+            k_p2p_counts<<<nblk(npp, 256), 256, 0, sl>>>(npp, d.p2p_src, d.count, cnt);
+            size_t sb = 0;
+            cub::DeviceScan::ExclusiveSum(nullptr, sb, cnt, gcum, npp, sl);
+            if ((rc = dev_alloc(&tmp, sb, nullptr, sl))) return rc;
+            FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, cnt, gcum, npp, sl));
+            dev_free(tmp, sl);
+            k_p2p_records<<<nblk(npp, 256), 256, 0, sl>>>(npp, d.p2p_src, p2p_tgt, d.p2p_start, d.first, d.count,
+                                                            gcum, d.p2p_rec);
+            count_launch(t, 3);
+        }
+        dev_free(cnt, sl); dev_free(gcum, sl); dev_free(p2p_tgt, sl);
+    }
+    dev_free(p2p, sl);
+    if (sl != st) FMM_CUDA_TRY(cudaEventRecord(t->ev_join_hi, sl));
     const bool want_classes = t->prm.precision == FMM_PREC_MIXED_TC && tc_supported(t->prm.p);
     // with the tensor cores the M2L pairs are grouped by class straight from the
     // traversal output; no (target, source) order is needed on that path
@@ -955,27 +985,8 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     } else if ((rc = finish_list(t, m2l, nm, &d.m2l_start, &d.m2l_src, nullptr, st))) {
         return rc;
     }
-    int32_t* p2p_tgt = nullptr;
-    if ((rc = finish_list(t, p2p, npp, &d.p2p_start, &d.p2p_src, &p2p_tgt, st))) return rc;
-    {
-        int64_t *cnt = nullptr, *gcum = nullptr;
-        if ((rc = dev_alloc(&cnt, (size_t)npp, nullptr, st))) return rc;
-        if ((rc = dev_alloc(&gcum, (size_t)npp, nullptr, st))) return rc;
-        if ((rc = dev_alloc(&d.p2p_rec, (size_t)npp, t, st))) return rc;
-        if (npp) {
-            k_p2p_counts<<<nblk(npp, 256), 256, 0, st>>>(npp, d.p2p_src, d.count, cnt);
-            size_t sb = 0;
-            cub::DeviceScan::ExclusiveSum(nullptr, sb, cnt, gcum, npp, st);
-            if ((rc = dev_alloc(&tmp, sb, nullptr, st))) return rc;
-            FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, cnt, gcum, npp, st));
-            dev_free(tmp, st);
-            k_p2p_records<<<nblk(npp, 256), 256, 0, st>>>(npp, d.p2p_src, p2p_tgt, d.p2p_start, d.first, d.count,
-                                                            gcum, d.p2p_rec);
-            count_launch(t, 3);
-        }
-        dev_free(cnt, st); dev_free(gcum, st); dev_free(p2p_tgt, st);
-    }
-    dev_free(m2l, st); dev_free(p2p, st);
+    dev_free(m2l, st);
+    if (sl != st) FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join_hi, 0));
     if (queue_supported(t) && (rc = build_queue(t, st))) return rc;
     stage_end(t, FMM_STAGE_LISTS, st);
     FMM_CUDA_TRY(cudaGetLastError());
