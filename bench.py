@@ -60,9 +60,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=1 << 17)
-    ap.add_argument("--workload", default="plummer", choices=["plummer", "batched", "table"],
+    ap.add_argument("--workload", default="plummer", choices=["plummer", "batched", "table", "granularity"],
                     help="plummer: one 1M-particle system (default); batched: 512 systems of 1024..65536; "
-                         "table: every configuration against the oracle (context, several minutes)")
+                         "table: every configuration against the oracle (context, several minutes); "
+                         "granularity: task size against N on the task queue")
     return ap.parse_args()
 
 
@@ -228,6 +229,33 @@ def kernel_rooflines(stage_ms: dict, ex, prec: int, n_sm: int, info=None):
     return out
 
 
+def pass_rooflines(stage_ms: dict, ex, prec: int, info, n: int):
+    """The up- and downward passes against HBM, with the algorithmic bytes of
+    each (b = bytes per real coefficient, K = (p+1)^2 real coefficients, L =
+    leaves): P2M 16N + L K b, M2M sum over internal cells of (children + 1) K b,
+    L2L 3 K b per non-root cell, L2P 16N + L K b + 16N.  Times are the stage
+    events inside the timed region (latency-bound stages: small fractions)."""
+    pk, _ = peaks()
+    hbm = float(pk["hbm_gbs"])
+    K = (P + 1) ** 2
+    b = 8 if prec in (0, 1) else 4
+    cc = ex["child_count"]
+    nleaf = int((cc == 0).sum())
+    internal = cc > 0
+    ncell = len(cc)
+    algo = {"p2m": 16 * n + nleaf * K * b,
+            "m2m": int(((cc[internal] + 1) * K * b).sum()),
+            "l2l": 3 * K * b * (ncell - 1),
+            "l2p": 16 * n + nleaf * K * b + 16 * n}
+    out = []
+    for name, bytes_ in algo.items():
+        if name in stage_ms and stage_ms[name] > 0:
+            gbs = bytes_ / (stage_ms[name] * 1e-3) / 1e9
+            out.append({"stage": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                        "frac": gbs / hbm, "bytes": int(bytes_), "ms": stage_ms[name]})
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -281,10 +309,13 @@ def run_ours(args):
     stage_acc = {}
     launches = 0
     wall0 = time.perf_counter()
+    ev_mid = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for k in range(args.steps):
         flush.zero_()                       # evict L2 between steps (outside the event pair)
         ev[k][0].record(stream)
-        t = step()
+        t = fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=args.precision, flags=flags)
+        ev_mid[k].record(stream)            # build | evaluate
+        t.evaluate(q, phi=phi, force=force)
         ev[k][1].record(stream)
         for name, ms in t.stage_times().items():
             stage_acc[name] = stage_acc.get(name, 0.0) + ms
@@ -296,6 +327,8 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    build_ms = statistics.median(a.elapsed_time(m) for (a, _), m in zip(ev, ev_mid))
+    eval_ms = statistics.median(m.elapsed_time(b) for (_, b), m in zip(ev, ev_mid))
     total_s = sum(step_ms) * 1e-3
     total_s = max_over_ranks(total_s, dev)
     value = job_throughput(n, world, args.steps, total_s)
@@ -303,6 +336,18 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(dev)
     roofs = kernel_rooflines(stage_ms, ex, args.precision, props.multi_processor_count, info)
     roof = max(roofs, key=lambda r: r["ms"]) if roofs else None
+    passes = pass_rooflines(stage_ms, ex, args.precision, info, n)
+    for r in roofs:
+        if r["kernel"] == "k_p2p":
+            # the same pairs against the reciprocal-square-root (MUFU) bound, and both
+            # bounds at the median SM clock seen under load
+            f_load = clocks.get("sm_mhz") or 2070.0
+            pairs = p2p_pairs(ex)
+            nsm = props.multi_processor_count
+            r["mufu_bound_pairs_per_s"] = nsm * 16 * 2070e6
+            r["pairs_per_s"] = pairs / (r["ms"] * 1e-3)
+            r["frac_at_loaded_clock"] = r["achieved"] / (r["peak"] * f_load / 2070.0)
+            r["loaded_sm_mhz"] = f_load
     # the same kernels with nothing running beside them (FMM_NO_OVERLAP: P2P and
     # the far field one after the other), outside the timed region: the step
     # overlaps P2P with the far field, which stretches both kernels' event times
@@ -410,7 +455,11 @@ def run_ours(args):
                                                 if k in ("prepare", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p",
                                                          "queue")), 4),
                        "wall_s": wall},
-            "roofline": roof, "rooflines": roofs, "variants": variants, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "rooflines": roofs, "passes": passes, "variants": variants, "cpu_baseline": cpu,
+            "e2e": e2e,
+            "build_ms_per_step": build_ms, "evaluate_ms_per_step": eval_ms,
+            "evaluate_particles_per_s": n / (eval_ms * 1e-3),
+            "vs_fp64_gpu_path": (value / variants["fp64"]["value"]) if "fp64" in variants else None,
             "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(out), flush=True)
@@ -596,6 +645,8 @@ def run_table(args):
         row = {"config": name, "n": n, "p": p, "leaf": leaf, "theta": theta, "sampled_particles": int(len(idx))}
         for prec in (0, 2, 3):
             phi, f, dt = gpu_rate(pos, q, prec, p, leaf, theta, steps=2 if prec == 0 else 3)
+            if prec == 0:
+                row["_phi64"], row["_f64"] = phi, f
             row[PREC_NAMES[prec]] = {
                 "particles_per_s": n / dt, "ms_per_step": dt * 1e3,
                 "rel_l2_vs_oracle": {"phi": float(np.linalg.norm(phi[idx] - phi_ref) / np.linalg.norm(phi_ref)),
@@ -603,6 +654,23 @@ def run_table(args):
         del T
         row["oracle_all_cores"] = cpu_rate(name, min(n, 1 << 17), cores)
         row["oracle_1_core"] = cpu_rate(name, min(n, 1 << 14), 1)
+        # the oracle's direct sum (one core): all targets at N <= 16384, else 4096
+        # seeded targets against all sources, extrapolated to N targets
+        nt = min(n, 4096) if n > 16384 else n
+        tg = np.sort(np.random.default_rng(4096).choice(n, size=nt, replace=False)) if nt < n else np.arange(n)
+        t0 = time.perf_counter()
+        ph_d, gr_d = oracle.direct_targets(wl.pos, wl.q, tg)
+        dt_d = (time.perf_counter() - t0) * n / nt
+        row["oracle_direct_1_core_particles_per_s"] = n / dt_d
+        # the mixed form against the exact sum on those targets (FMM truncation included)
+        phi_m, f_m, _ = gpu_rate(pos, q, 3, p, leaf, theta, steps=1)
+        f_d = -wl.q[tg, None] * gr_d
+        row["mixed_tc"]["rel_l2_vs_direct_sum"] = {
+            "phi": float(np.linalg.norm(phi_m[tg] - ph_d) / np.linalg.norm(ph_d)),
+            "force": float(np.linalg.norm(f_m[tg] - f_d) / np.linalg.norm(f_d))}
+        row["fp64"]["rel_l2_vs_direct_sum"] = {
+            "phi": float(np.linalg.norm(row.pop("_phi64")[tg] - ph_d) / np.linalg.norm(ph_d)),
+            "force": float(np.linalg.norm(row.pop("_f64")[tg] - f_d) / np.linalg.norm(f_d))}
         if name == "gradient":
             # forward + backward through the autograd node (FP32), L = sum w phi
             fn = fmm.FMMFunction
@@ -657,6 +725,50 @@ def run_table(args):
     print("\n".join(lines), file=sys.stderr, flush=True)
 
 
+def run_granularity(args):
+    """Task granularity against problem size (the paper's queue threshold Q
+    versus N study, on the device queue): uniform particles, p = 6 and 9,
+    N = 1e5, 1e6, 1e7, leaf sizes 16..256; FP32 task-queue evaluation (one
+    persistent launch running the task DAG).  A leaf size fixes the number of
+    tasks (cells and leaves, about N / leaf each), so the sweep shows where
+    per-task scheduling stops being amortised.  Prints one JSON line."""
+    import torch
+
+    import paper_1203_0889_gb300 as fmm
+    import workloads as W
+
+    dev = torch.device("cuda", 0)
+    rows = []
+    for n in (100_000, 1_000_000, 10_000_000):
+        wl = W.make_workload("uniform", n=n, seed=12030889 * 10 + 6)
+        pos = torch.tensor(wl.pos, dtype=torch.float64, device=dev)
+        q = torch.tensor(wl.q, dtype=torch.float32, device=dev)
+        for p in (6, 9):
+            for leaf in (16, 32, 64, 128, 256):
+                t = fmm.build_tree(pos, p=p, leaf_size=leaf, theta=0.5, precision=fmm.PREC_FP32)
+                info = t.info()
+                t.evaluate(q)
+                torch.cuda.synchronize()
+                ts = []
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    t.evaluate(q)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ms = statistics.median(ts)
+                ntask = info.ncell + 2 * info.nleaf   # M2M/M2L/L2L per cell, P2M + P2P + L2P per leaf (P2M grouped)
+                rows.append({"n": n, "p": p, "leaf": leaf, "ncell": info.ncell, "nleaf": info.nleaf,
+                             "tasks": ntask, "n_over_tasks": n / ntask, "evaluate_ms": ms,
+                             "particles_per_s": n / (ms * 1e-3), "us_per_task": ms * 1e3 / ntask,
+                             "status": t.status()})
+                t.close()
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"study": "task granularity vs N (FP32 task queue, uniform, theta 0.5)", "rows": rows}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -665,6 +777,8 @@ def main():
         run_batched(args)
     elif args.workload == "table":
         run_table(args)
+    elif args.workload == "granularity":
+        run_granularity(args)
     else:
         run_ours(args)
 
