@@ -117,6 +117,11 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
             if (t->ev_join) cudaEventDestroy(t->ev_join);
             t->side_stream = nullptr; t->ev_fork = nullptr; t->ev_join = nullptr; t->ev_ops = nullptr;
         }
+        if (t->side_stream && t->prm.precision == FMM_PREC_MIXED_TC &&
+            cudaStreamCreateWithFlags(&t->ops_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            t->ops_stream = nullptr;
+        }
         int least = 0, greatest = 0;
         if (t->side_stream && (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
                                cudaStreamCreateWithPriority(&t->hi_stream, cudaStreamNonBlocking, greatest) !=
@@ -137,10 +142,12 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
         cudaStreamSynchronize(st);
         if (t->side_stream) cudaStreamSynchronize(t->side_stream);
         if (t->hi_stream) cudaStreamSynchronize(t->hi_stream);
+        if (t->ops_stream) cudaStreamSynchronize(t->ops_stream);
         fmm::free_tree_device(t);
         if (t->timing) for (int i = 0; i < 2 * FMM_NUM_STAGES; i++) cudaEventDestroy(t->ev[i]);
         if (t->side_stream) cudaStreamDestroy(t->side_stream);
         if (t->hi_stream) cudaStreamDestroy(t->hi_stream);
+        if (t->ops_stream) cudaStreamDestroy(t->ops_stream);
         if (t->ev_fork) cudaEventDestroy(t->ev_fork);
         if (t->ev_join) cudaEventDestroy(t->ev_join);
         if (t->ev_join_hi) cudaEventDestroy(t->ev_join_hi);
@@ -344,11 +351,13 @@ void fmm_tree_destroy(fmm_tree* t) {
     cudaDeviceSynchronize();
     if (t->side_stream) cudaStreamSynchronize(t->side_stream);
     if (t->hi_stream) cudaStreamSynchronize(t->hi_stream);
+    if (t->ops_stream) cudaStreamSynchronize(t->ops_stream);
     fmm::free_tree_device(t);
     cudaStreamSynchronize(0);
     if (t->timing) for (int i = 0; i < 2 * FMM_NUM_STAGES; i++) cudaEventDestroy(t->ev[i]);
     if (t->side_stream) cudaStreamDestroy(t->side_stream);
     if (t->hi_stream) cudaStreamDestroy(t->hi_stream);
+    if (t->ops_stream) cudaStreamDestroy(t->ops_stream);
     if (t->ev_join_hi) cudaEventDestroy(t->ev_join_hi);
     if (t->ev_fork) cudaEventDestroy(t->ev_fork);
     if (t->ev_join) cudaEventDestroy(t->ev_join);

@@ -200,6 +200,9 @@ struct fmm_tree {
     // as soon as P2P blocks retire instead of queueing behind the whole P2P grid
     cudaStream_t hi_stream = nullptr;
     cudaEvent_t ev_join_hi = nullptr;
+    // the tensor-core class operators are built on a stream of their own (they
+    // overlap the rest of the build and the start of the evaluation)
+    cudaStream_t ops_stream = nullptr;
     int64_t* launch_ctr = nullptr;  // which counter launches currently go to
     int64_t n = 0;
     int ncell = 0, nlevel = 0, nleaf = 0;

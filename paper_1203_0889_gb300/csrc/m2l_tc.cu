@@ -314,8 +314,8 @@ static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const in
     if ((rc = dev_alloc(&d.tc_keys, (size_t)nclass, t, st))) return rc;
     FMM_CUDA_TRY(cudaMemcpyAsync(d.tc_keys, ukeys, sizeof(uint64_t) * nclass, cudaMemcpyDeviceToDevice, st));
     cudaStream_t so = st;
-    if (t->side_stream && t->ev_ops) {
-        so = t->side_stream;
+    if ((t->ops_stream || t->side_stream) && t->ev_ops) {
+        so = t->ops_stream ? t->ops_stream : t->side_stream;
         FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
         FMM_CUDA_TRY(cudaStreamWaitEvent(so, t->ev_fork, 0));
     }
