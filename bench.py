@@ -168,9 +168,9 @@ def p2p_pairs(ex) -> int:
 FP64_TFLOPS_MEASURED = 1.256
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
-# stands (summaries in profiles/); None once the kernel has changed since.
-TRAFFIC = {"k_p2p": 89276160 + 15623680,        # profiles/k_p2p_plummer1m_p8_fp32.md
-           "k_m2l_tc": 535333376 + 10936832}    # profiles/k_m2l_tc_plummer1m_p8.md
+# stands; None once the kernel has changed since.
+TRAFFIC = {"k_p2p": 89276160 + 15623680,        # bench workload, one launch, dram__bytes_read + write
+           "k_m2l_tc": 535333376 + 10936832}
 
 
 def kernel_rooflines(stage_ms: dict, ex, prec: int, n_sm: int, info=None):

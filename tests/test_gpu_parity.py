@@ -176,3 +176,18 @@ def test_tensor_core_fallback_grouping_same_result():
     assert b.status() == fmm.FMM_OK
     assert ((pa - pb).norm() / pa.norm()).item() <= 1e-6
     assert ((fa - fb).norm() / fa.norm()).item() <= 1e-6
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 7, 9])
+def test_tensor_core_m2l_every_padding(p):
+    """Every K_p the tensor-core kernel meets (16 .. 112 columns: operator slots,
+    stage counts and drains differ) against the FP32 path on the same tree."""
+    import paper_1203_0889_gb300 as fmm
+    wl = W.make_workload("plummer", n=30000)
+    t32 = gpu_tree(wl.pos, p=p, leaf_size=32, theta=0.5, precision=fmm.PREC_FP32)
+    ttc = gpu_tree(wl.pos, p=p, leaf_size=32, theta=0.5, precision=fmm.PREC_MIXED_TC)
+    assert ttc.info().tc_pairs > 0
+    phi32, f32 = gpu_eval(t32, wl.q)
+    phitc, ftc = gpu_eval(ttc, wl.q)
+    assert ttc.status() == fmm.FMM_OK
+    assert O.rel_l2(phitc, phi32) <= 2e-5 and O.rel_l2(ftc, f32) <= 2e-5
