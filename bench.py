@@ -541,7 +541,8 @@ def run_batched(args):
     n = int(off[-1])
     k = 64
     leaf, tune = fmm.autotune_leaf_size(pos[:off[k]], q[:off[k]], offsets=off[:k + 1], repeats=2, p=6, theta=0.5,
-                                        precision=fmm.PREC_FP32)
+                                        precision=fmm.PREC_FP32,
+                                        candidates=(32, 48, 64, 96, 128, 192, 256, 384))
     prm = dict(p=6, leaf_size=leaf, theta=0.5, precision=fmm.PREC_FP32)
     phi = torch.empty(n, dtype=torch.float32, device=dev)
     force = torch.empty((n, 3), dtype=torch.float32, device=dev)
@@ -577,6 +578,25 @@ def run_batched(args):
         gt.append(e0.elapsed_time(e1))
     clocks = sampler.stop()
     info = t.info()
+    # the mixed tensor-core form on the same systems (stage-by-stage, not the
+    # queue): context for the configuration's FP32 queue form
+    mixed = None
+    prm_m = dict(prm, precision=fmm.PREC_MIXED_TC)
+    ts = []
+    for k_ in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tm = fmm.build_tree_batched(pos, off, **prm_m)
+        pm, fm = tm.evaluate(q)
+        e1.record()
+        torch.cuda.synchronize()
+        if k_ >= args.warmup:
+            ts.append(e0.elapsed_time(e1))
+        tm.close()
+    mixed = {"value": n / (statistics.median(ts) * 1e-3), "ms_per_step": statistics.median(ts),
+             "rel_l2_vs_fp32_queue": {"phi": float(((pm - phi).norm() / phi.norm()).item()),
+                                      "force": float(((fm - force).norm() / force.norm()).item())}}
     out = {
         "metric": METRIC, "value": n * args.steps / total_s, "unit": "particles/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
@@ -588,6 +608,7 @@ def run_batched(args):
                    "ncell": info.ncell, "nm2l": info.nm2l, "np2p": info.np2p,
                    "l2": "flushed between steps (512 MB write)"},
         "clocks": clocks, "gpu_launches": t.kernel_launches(build=True) + t.kernel_launches(build=False),
+        "variants": {"mixed_tc": mixed},
     }
     print(json.dumps(out), flush=True)
 
@@ -699,23 +720,28 @@ def run_table(args):
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     pos = torch.tensor(np.concatenate([s_[0] for s_ in systems]), dtype=torch.float64, device=dev)
     q = torch.tensor(np.concatenate([s_[1] for s_ in systems]), dtype=torch.float32, device=dev)
-    ts = []
-    for k in range(4):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        t = fmm.build_tree_batched(pos, off, p=6, leaf_size=32, theta=0.5, precision=fmm.PREC_FP32)
-        t.evaluate(q)
-        torch.cuda.synchronize()
-        ts.append(time.perf_counter() - t0)
-        t.close()
-    out["table"].append({"config": "batched", "n": int(off[-1]), "systems": 512, "p": 6,
-                         "fp32": {"particles_per_s": int(off[-1]) / statistics.median(ts[1:])}})
+    leaf_b, _ = fmm.autotune_leaf_size(pos[:off[64]], q[:off[64]], offsets=off[:65], repeats=2, p=6, theta=0.5,
+                                       precision=fmm.PREC_FP32, candidates=(32, 48, 64, 96, 128, 192, 256, 384))
+    rates = {}
+    for prec in (fmm.PREC_FP32, fmm.PREC_MIXED_TC):
+        ts = []
+        for k in range(4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            t = fmm.build_tree_batched(pos, off, p=6, leaf_size=leaf_b, theta=0.5, precision=prec)
+            t.evaluate(q)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            t.close()
+        rates[PREC_NAMES[prec]] = {"particles_per_s": int(off[-1]) / statistics.median(ts[1:])}
+    out["table"].append({"config": "batched", "n": int(off[-1]), "systems": 512, "p": 6, "leaf": leaf_b, **rates})
     print(json.dumps(out), flush=True)
     lines = ["| config | N | GPU FP64 p/s | GPU FP32 p/s | GPU mixed p/s | error FP64 / FP32 / mixed (phi, F) vs oracle "
              f"| oracle {cores} cores p/s | oracle 1 core p/s |", "|---|---|---|---|---|---|---|---|"]
     for r in out["table"]:
         if r["config"] == "batched":
-            lines.append(f"| batched 512 | {r['n']} | | {r['fp32']['particles_per_s']:.3g} | | | | |")
+            lines.append(f"| batched 512 (leaf {r['leaf']}) | {r['n']} | | {r['fp32']['particles_per_s']:.3g} | "
+                         f"{r['mixed_tc']['particles_per_s']:.3g} | | | |")
             continue
         e = " / ".join(f"{r[k]['rel_l2_vs_oracle']['phi']:.1e}, {r[k]['rel_l2_vs_oracle']['force']:.1e}"
                        for k in ("fp64", "fp32", "mixed_tc"))
