@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <vector>
 
 #include "fmm_internal.cuh"
@@ -43,6 +44,7 @@ template int dev_alloc<__nv_bfloat16>(__nv_bfloat16**, size_t, fmm_tree*, cudaSt
 template int dev_alloc<int2>(int2**, size_t, fmm_tree*, cudaStream_t);
 template int dev_alloc<double4_32a>(double4_32a**, size_t, fmm_tree*, cudaStream_t);
 template int dev_alloc<unsigned long long>(unsigned long long**, size_t, fmm_tree*, cudaStream_t);
+template int dev_alloc<char2>(char2**, size_t, fmm_tree*, cudaStream_t);
 
 template <typename T>
 static void dev_free(T*& p, cudaStream_t st) {
@@ -334,6 +336,206 @@ __global__ void k_centres(int ncell, const int32_t* lev, const uint64_t* ckey, c
     }
     icentre[c] = make_int4(ic[0], ic[1], ic[2], l);
     centre[c] = make_double4_32a(x[0], x[1], x[2], __dmul_rn((double)s, __ddiv_rn(g->side, 2097152.0)));
+}
+
+// ---------------------------------------------------------------------------
+// octree in one pass over the sorted keys
+// ---------------------------------------------------------------------------
+//
+// The cell of level L that holds particle a is the run of particles sharing
+// a's level-L key prefix.  It splits (Section 2.1) iff it holds more than
+// S = leaf_size particles and L < FMM_MAX_LEVEL, and it holds more than S
+// particles iff some window of S + 1 consecutive sorted particles containing a
+// shares that prefix.  With m(s) = number of levels particles s and s + S have
+// in common (-1 when they lie in different systems), M(a) = max m(s) over
+// s in [a - S, a] is the deepest level whose cell around a holds more than S
+// particles, so a's leaf is at level hi(a) = min(M(a) + 1, FMM_MAX_LEVEL)
+// (0 when M(a) < 0).  a is the first particle of its level-L cell iff L is
+// deeper than the levels it shares with particle a - 1, so the cells that
+// start at a are those of levels lo(a) .. hi(a).  Counting them per level and
+// block and scanning the counts places every cell in (level, position) order,
+// which is (level, system, key) order.
+
+constexpr int OCT_B = 256;                        // particles per block
+constexpr int OCT_NL = FMM_MAX_LEVEL + 1;         // levels 0 .. FMM_MAX_LEVEL
+
+// levels two keys have in common: prefixes key >> 3 (FMM_MAX_LEVEL - L) agree
+// for L <= 20 - (highest differing bit) / 3, and at every level when equal
+__device__ __forceinline__ int common_levels(uint64_t k1, uint64_t k2) {
+    const uint64_t x = k1 ^ k2;
+    return x ? 20 - (63 - __clzll((long long)x)) / 3 : FMM_MAX_LEVEL;
+}
+
+// per-block cell and leaf counts of every level of the particles of one block
+__device__ __forceinline__ void oct_warp_counts(int lo, int hi, int (*wc)[2 * OCT_NL]) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int L = 0; L < OCT_NL; L++) {
+        const bool in = lo <= L && L <= hi;
+        const unsigned mc = __ballot_sync(0xffffffffu, in);
+        const unsigned ml = __ballot_sync(0xffffffffu, in && L == hi);
+        if (lane == 0) { wc[w][L] = __popc(mc); wc[w][OCT_NL + L] = __popc(ml); }
+    }
+}
+
+// lo(a), hi(a) of every particle; cnt[j * nb + b] = cells (j < OCT_NL) or
+// leaves (j >= OCT_NL) of level j % OCT_NL starting in block b.
+// Dynamic shared memory: 2 (OCT_B + S) bytes.
+__global__ void __launch_bounds__(OCT_B) k_oct_levels(const uint64_t* __restrict__ keys, int64_t n,
+                                                      const int64_t* __restrict__ off, int nsys, int S, int nb,
+                                                      char2* __restrict__ lohi, int64_t* __restrict__ cnt) {
+    extern __shared__ signed char oct_sm[];
+    __shared__ int wc[OCT_B / 32][2 * OCT_NL];
+    const int Lb = OCT_B + S;
+    signed char* x = oct_sm;
+    signed char* y = oct_sm + Lb;
+    const int64_t A = (int64_t)blockIdx.x * OCT_B;
+    // x[j] = m(A - S + j)
+    for (int j = threadIdx.x; j < Lb; j += OCT_B) {
+        const int64_t s = A - S + j;
+        int v = -1;
+        if (s >= 0 && s + S < n) {
+            const int sy = nsys > 1 ? system_of(s, off, nsys) : 0;
+            if (s + S < off[sy + 1]) v = common_levels(keys[s], keys[s + S]);
+        }
+        x[j] = (signed char)v;
+    }
+    __syncthreads();
+    // doubling: after step k, x[j] = max of m over [A - S + j, A - S + j + 2^k)
+    int k = 0;
+    while ((2 << k) <= S + 1) k++;   // 2^k <= S + 1 < 2^(k+1)
+    for (int st = 0; st < k; st++) {
+        const int o = 1 << st;
+        for (int j = threadIdx.x; j < Lb; j += OCT_B) y[j] = j + o < Lb ? max(x[j], x[j + o]) : x[j];
+        __syncthreads();
+        signed char* tmp = x;
+        x = y;
+        y = tmp;
+    }
+    const int t = threadIdx.x;
+    const int64_t a = A + t;
+    int lo = 1, hi = 0;   // no cell starts here
+    if (a < n) {
+        // window [a - S, a] = [A - S + t, A - S + t + 2^k) u [.. , A + t]
+        const int M = max((int)x[t], (int)x[t + S + 1 - (1 << k)]);
+        hi = M < 0 ? 0 : min(FMM_MAX_LEVEL, M + 1);
+        const int sy = nsys > 1 ? system_of(a, off, nsys) : 0;
+        lo = off[sy] == a ? 0 : common_levels(keys[a - 1], keys[a]) + 1;
+        lohi[a] = make_char2((char)lo, (char)hi);
+    }
+    oct_warp_counts(lo, hi, wc);
+    __syncthreads();
+    if (t < 2 * OCT_NL) {
+        int s = 0;
+        for (int i = 0; i < OCT_B / 32; i++) s += wc[i][t];
+        cnt[(int64_t)t * nb + blockIdx.x] = s;
+    }
+}
+
+// hdr[L] = first cell of level L (L = 0 .. OCT_NL; hdr[OCT_NL] = cells),
+// hdr[OCT_NL + 1] = leaves; the systems' root cubes follow at geo_out
+__global__ void k_oct_summary(const int64_t* __restrict__ offs, const int64_t* __restrict__ cnt, int nb,
+                              const Geometry* __restrict__ geom, int nsys, int64_t* hdr, Geometry* geo_out) {
+    const int t = threadIdx.x;
+    if (t <= OCT_NL) hdr[t] = offs[(int64_t)t * nb];
+    if (t == 0) {
+        const int64_t last = (int64_t)2 * OCT_NL * nb - 1;
+        hdr[OCT_NL + 1] = offs[last] + cnt[last] - offs[(int64_t)OCT_NL * nb];
+    }
+    for (int s = t; s < nsys; s += blockDim.x) geo_out[s] = geom[s];
+}
+
+// writes level, key, first particle and count of every cell, and the leaf list
+__global__ void __launch_bounds__(OCT_B) k_oct_emit(const uint64_t* __restrict__ keys, int64_t n,
+                                                    const int64_t* __restrict__ off, int nsys, int nb,
+                                                    const char2* __restrict__ lohi,
+                                                    const int64_t* __restrict__ offs, int32_t* __restrict__ lev,
+                                                    uint64_t* __restrict__ ckey, int32_t* __restrict__ first,
+                                                    int32_t* __restrict__ count, int32_t* __restrict__ leaves) {
+    __shared__ int wc[OCT_B / 32][2 * OCT_NL];
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const int64_t a = (int64_t)blockIdx.x * OCT_B + t;
+    int lo = 1, hi = 0;
+    if (a < n) {
+        const char2 v = lohi[a];
+        lo = v.x;
+        hi = v.y;
+    }
+    oct_warp_counts(lo, hi, wc);
+    __syncthreads();
+    if (t < 2 * OCT_NL) {   // exclusive offsets of the warps within the block
+        int s = 0;
+        for (int i = 0; i < OCT_B / 32; i++) {
+            const int c = wc[i][t];
+            wc[i][t] = s;
+            s += c;
+        }
+    }
+    __syncthreads();
+    const int64_t ncell = offs[(int64_t)OCT_NL * nb];
+    const uint64_t key = a < n ? keys[a] : 0;
+    int64_t se = 0;
+    if (a < n && lo <= hi) se = off[(nsys > 1 ? system_of(a, off, nsys) : 0) + 1];
+    const unsigned lt = (1u << lane) - 1u;
+    int64_t good = a;   // last particle known to share a's prefix (the deeper level's run end - 1)
+    for (int L = FMM_MAX_LEVEL; L >= 0; L--) {
+        const bool in = lo <= L && L <= hi;
+        const unsigned mc = __ballot_sync(0xffffffffu, in);
+        const unsigned ml = __ballot_sync(0xffffffffu, in && L == hi);
+        if (!in) continue;
+        const int64_t idx = offs[(int64_t)L * nb + blockIdx.x] + wc[w][L] + __popc(mc & lt);
+        const int shift = 3 * (FMM_MAX_LEVEL - L);
+        const uint64_t pre = key >> shift;
+        // end of the run sharing the prefix: gallop from the deeper run's end, then bisect
+        int64_t step = 1;
+        while (good + step < se && (keys[good + step] >> shift) == pre) {
+            good += step;
+            step <<= 1;
+        }
+        int64_t bad = min(good + step, se);
+        while (bad - good > 1) {
+            const int64_t mid = (good + bad) >> 1;
+            if ((keys[mid] >> shift) == pre) good = mid; else bad = mid;
+        }
+        lev[idx] = L;
+        ckey[idx] = pre;
+        first[idx] = (int32_t)a;
+        count[idx] = (int32_t)(bad - a);
+        if (L == hi)
+            leaves[offs[(int64_t)(OCT_NL + L) * nb + blockIdx.x] - ncell + wc[w][OCT_NL + L] + __popc(ml & lt)] =
+                (int32_t)idx;
+    }
+}
+
+struct LevelStarts {
+    int32_t s[FMM_MAX_LEVEL + 2];
+};
+
+// first index in [lo, hi) of sorted v with v[i] >= x (hi if none)
+__device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ v, int lo, int hi, int64_t x) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (v[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// parent and children of every cell, by bisection over the first particles of
+// the neighbouring levels (ordered by position within a level)
+__global__ void k_oct_links(int ncell, LevelStarts ls, int S, const int32_t* __restrict__ lev,
+                            const int32_t* __restrict__ first, const int32_t* __restrict__ count, int32_t* parent,
+                            int32_t* child_first, int32_t* child_count) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int L = lev[c], a = first[c], n = count[c];
+    // the last cell of level L - 1 whose first particle is <= a holds a
+    parent[c] = L > 0 ? lower_bound_i32(first, ls.s[L - 1], ls.s[L], (int64_t)a + 1) - 1 : -1;
+    int cf = 0, cc = 0;
+    if (n > S && L < FMM_MAX_LEVEL) {
+        cf = lower_bound_i32(first, ls.s[L + 1], ls.s[L + 2], a);
+        cc = lower_bound_i32(first, cf, ls.s[L + 2], (int64_t)a + n) - cf;
+    }
+    child_first[c] = cf;
+    child_count[c] = cc;
 }
 
 // ---------------------------------------------------------------------------
@@ -647,6 +849,82 @@ static int finish_list(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, in
     return FMM_OK;
 }
 
+// a2 in one pass: leaf level of every particle, one scan of the per-level
+// counts, then every cell and its links (the level-by-level octree serves
+// FMM_BUILD_FALLBACKS).  One host round trip, which also brings back the
+// root cubes.
+template <class TakeGeometry>
+static int build_octree_onepass(fmm_tree* t, TakeGeometry&& take_geometry, cudaStream_t st) {
+    int rc;
+    TreeDev& d = t->d;
+    const int64_t n = t->n;
+    const int nsys = t->nsys, S = t->prm.leaf_size;
+    stage_begin(t, FMM_STAGE_OCTREE, st);
+    const int nb = (int)((n + OCT_B - 1) / OCT_B);
+    const size_t ncnt = (size_t)2 * OCT_NL * nb;
+    char2* lohi = nullptr;
+    int64_t *cnt = nullptr, *offs = nullptr, *hdr = nullptr;
+    char* tmp = nullptr;
+    auto release = [&]() {
+        dev_free(tmp, st);
+        dev_free(lohi, st);
+        dev_free(cnt, st);
+        dev_free(offs, st);
+        dev_free(hdr, st);
+    };
+    const size_t hdr_words = 32 + (sizeof(Geometry) * (size_t)nsys + 7) / 8;
+    if ((rc = dev_alloc(&lohi, (size_t)n, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&cnt, ncnt, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&offs, ncnt, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&hdr, hdr_words, nullptr, st))) return rc;
+    k_oct_levels<<<nb, OCT_B, 2 * (OCT_B + S), st>>>(d.keys, n, d.sys_off, nsys, S, nb, lohi, cnt);
+    count_launch(t);
+    size_t sb = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, sb, cnt, offs, (int64_t)ncnt, st);
+    if ((rc = dev_alloc(&tmp, sb, nullptr, st))) return rc;
+    FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, cnt, offs, (int64_t)ncnt, st));
+    count_launch(t);
+    k_oct_summary<<<1, 128, 0, st>>>(offs, cnt, nb, d.geom, nsys, hdr, (Geometry*)(hdr + 32));
+    count_launch(t);
+    std::vector<int64_t> h(hdr_words);
+    FMM_CUDA_TRY(cudaMemcpyAsync(h.data(), hdr, hdr_words * 8, cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if ((rc = take_geometry((const Geometry*)(h.data() + 32)))) { release(); return rc; }
+    const int64_t ncell = h[OCT_NL], nleaf = h[OCT_NL + 1];
+    if (ncell >= INT32_MAX) {
+        release();
+        fmm_set_error("fmm_build_tree: %lld cells exceed the 32-bit cell index", (long long)ncell);
+        return FMM_ERR_ARG;
+    }
+    t->ncell = (int)ncell;
+    t->nleaf = (int)nleaf;
+    LevelStarts ls;
+    int deepest = 0;
+    for (int L = 0; L <= OCT_NL; L++) t->level_start[L] = ls.s[L] = (int32_t)h[L];
+    for (int L = 0; L < OCT_NL; L++)
+        if (h[L + 1] > h[L]) deepest = L;
+    t->nlevel = deepest + 1;
+    const size_t nc = (size_t)ncell;
+    if ((rc = dev_alloc(&d.level, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.ckey, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.first, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.count, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.parent, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.child_first, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.child_count, nc, t, st))) return rc;
+    if ((rc = dev_alloc(&d.leaves, nc, t, st))) return rc;
+    k_oct_emit<<<nb, OCT_B, 0, st>>>(d.keys, n, d.sys_off, nsys, nb, lohi, offs, d.level, d.ckey, d.first, d.count,
+                                     d.leaves);
+    count_launch(t);
+    k_oct_links<<<nblk((int64_t)nc, 256), 256, 0, st>>>((int)nc, ls, S, d.level, d.first, d.count, d.parent,
+                                                         d.child_first, d.child_count);
+    count_launch(t);
+    release();
+    FMM_CUDA_TRY(cudaGetLastError());
+    stage_end(t, FMM_STAGE_OCTREE, st);
+    return FMM_OK;
+}
+
 int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st) {
     int rc;
     const int64_t n = t->n;
@@ -732,139 +1010,150 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         k_gather_pos<float><<<nblk(n, 256), 256, 0, st>>>((const float*)pos, d.perm, n, d.spos);
     count_launch(t);
     stage_end(t, FMM_STAGE_KEYS, st);
-    std::vector<Geometry> hg(nsys);
-    FMM_CUDA_TRY(cudaMemcpyAsync(hg.data(), d.geom, sizeof(Geometry) * nsys, cudaMemcpyDeviceToHost, st));
-    FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    t->h_geom.assign((size_t)nsys * 4, 0.0);
-    for (int s = 0; s < nsys; s++) {
-        if (hg[s].bad) {
-            fmm_set_error("fmm_build_tree: positions contain a non-finite value");
-            return FMM_ERR_ARG;
+    // root cubes on the host; a non-finite position fails the build
+    auto take_geometry = [&](const Geometry* hg) -> int {
+        t->h_geom.assign((size_t)nsys * 4, 0.0);
+        for (int s = 0; s < nsys; s++) {
+            if (hg[s].bad) {
+                fmm_set_error("fmm_build_tree: positions contain a non-finite value");
+                return FMM_ERR_ARG;
+            }
+            for (int k = 0; k < 3; k++) t->h_geom[4 * s + k] = hg[s].origin[k];
+            t->h_geom[4 * s + 3] = hg[s].side;
         }
-        for (int k = 0; k < 3; k++) t->h_geom[4 * s + k] = hg[s].origin[k];
-        t->h_geom[4 * s + 3] = hg[s].side;
-    }
-    for (int k = 0; k < 3; k++) t->origin[k] = hg[0].origin[k];
-    t->side = hg[0].side;
-
-    // --- a2: octree, level by level
-    stage_begin(t, FMM_STAGE_OCTREE, st);
-    size_t cap = (size_t)std::max<int64_t>(64, 4 * n / std::max(1, t->prm.leaf_size) + 64);
-    size_t c_lev = 0, c_key = 0, c_first = 0, c_count = 0, c_par = 0, c_cf = 0, c_cc = 0;
-    int32_t *lev = nullptr, *first = nullptr, *count = nullptr, *par = nullptr, *cf = nullptr, *cc = nullptr;
-    uint64_t* ckey = nullptr;
-    auto grow_all = [&](size_t need, size_t keep) -> int {
-        int r;
-        if ((r = grow(lev, c_lev, need, keep, st))) return r;
-        if ((r = grow(ckey, c_key, need, keep, st))) return r;
-        if ((r = grow(first, c_first, need, keep, st))) return r;
-        if ((r = grow(count, c_count, need, keep, st))) return r;
-        if ((r = grow(par, c_par, need, keep, st))) return r;
-        if ((r = grow(cf, c_cf, need, keep, st))) return r;
-        if ((r = grow(cc, c_cc, need, keep, st))) return r;
+        for (int k = 0; k < 3; k++) t->origin[k] = hg[0].origin[k];
+        t->side = hg[0].side;
         return FMM_OK;
     };
-    if ((rc = grow_all(std::max(cap, (size_t)nsys + 64), 0))) return rc;
-    k_init_roots<<<nblk(nsys, 128), 128, 0, st>>>(nsys, d.sys_off, lev, ckey, first, count, par);
-    count_launch(t);
-    int32_t *nch = nullptr, *coff = nullptr, *ends = nullptr;
-    size_t c_nch = 0, c_coff = 0, c_ends = 0;
-    int lb = 0, le = nsys, level = 0;
-    t->level_start[0] = 0;
-    while (true) {
-        int width = le - lb;
-        if ((rc = grow(nch, c_nch, width, 0, st))) return rc;
-        if ((rc = grow(coff, c_coff, width, 0, st))) return rc;
-        if ((rc = grow(ends, c_ends, (size_t)width * 8, 0, st))) return rc;
-        // a narrow level (few cells, long ranges) searches with a warp per boundary
-        const int wide = (int64_t)width * 8 * 32 <= (int64_t)t->num_sms * 1024 ? 1 : 0;
-        k_count_children<<<nblk((int64_t)width * 8 * (wide ? 32 : 1), 128), 128, 0, st>>>(
-            lb, le, level, t->prm.leaf_size, wide, first, count, ckey, d.keys, ends, nch);
-        count_launch(t);
-        if (wide) {
-            k_count_from_ends<<<nblk(width, 128), 128, 0, st>>>(lb, le, level, t->prm.leaf_size, first, count, ends,
-                                                               nch);
-            count_launch(t);
-        }
-        size_t sb = 0;
-        cub::DeviceScan::ExclusiveSum(nullptr, sb, nch, coff, width, st);
-        if ((rc = dev_alloc(&tmp, sb, nullptr, st))) return rc;
-        FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, nch, coff, width, st));
-        count_launch(t);
-        dev_free(tmp, st);
-        int32_t last_off = 0, last_n = 0;
-        FMM_CUDA_TRY(cudaMemcpyAsync(&last_off, coff + width - 1, 4, cudaMemcpyDeviceToHost, st));
-        FMM_CUDA_TRY(cudaMemcpyAsync(&last_n, nch + width - 1, 4, cudaMemcpyDeviceToHost, st));
+    if (!(t->prm.flags & FMM_BUILD_FALLBACKS)) {
+        if ((rc = build_octree_onepass(t, take_geometry, st))) return rc;
+        stage_begin(t, FMM_STAGE_SETUP, st);
+    } else {
+        std::vector<Geometry> hg(nsys);
+        FMM_CUDA_TRY(cudaMemcpyAsync(hg.data(), d.geom, sizeof(Geometry) * nsys, cudaMemcpyDeviceToHost, st));
         FMM_CUDA_TRY(cudaStreamSynchronize(st));
-        int total = last_off + last_n;
-        if ((size_t)le + total > c_lev) {
-            if ((rc = grow_all((size_t)le + total, (size_t)le))) return rc;
-        }
-        k_emit_children<<<nblk((int64_t)width * 8, 128), 128, 0, st>>>(lb, le, level, ends, nch, coff, le, lev, ckey,
-                                                                      first, count, par, cf, cc);
+        if ((rc = take_geometry(hg.data()))) return rc;
+        // --- a2: octree, level by level
+        stage_begin(t, FMM_STAGE_OCTREE, st);
+        size_t cap = (size_t)std::max<int64_t>(64, 4 * n / std::max(1, t->prm.leaf_size) + 64);
+        size_t c_lev = 0, c_key = 0, c_first = 0, c_count = 0, c_par = 0, c_cf = 0, c_cc = 0;
+        int32_t *lev = nullptr, *first = nullptr, *count = nullptr, *par = nullptr, *cf = nullptr, *cc = nullptr;
+        uint64_t* ckey = nullptr;
+        auto grow_all = [&](size_t need, size_t keep) -> int {
+            int r;
+            if ((r = grow(lev, c_lev, need, keep, st))) return r;
+            if ((r = grow(ckey, c_key, need, keep, st))) return r;
+            if ((r = grow(first, c_first, need, keep, st))) return r;
+            if ((r = grow(count, c_count, need, keep, st))) return r;
+            if ((r = grow(par, c_par, need, keep, st))) return r;
+            if ((r = grow(cf, c_cf, need, keep, st))) return r;
+            if ((r = grow(cc, c_cc, need, keep, st))) return r;
+            return FMM_OK;
+        };
+        if ((rc = grow_all(std::max(cap, (size_t)nsys + 64), 0))) return rc;
+        k_init_roots<<<nblk(nsys, 128), 128, 0, st>>>(nsys, d.sys_off, lev, ckey, first, count, par);
         count_launch(t);
-        t->level_start[level + 1] = le;
-        if (total == 0) break;
-        lb = le;
-        le += total;
-        level++;
+        int32_t *nch = nullptr, *coff = nullptr, *ends = nullptr;
+        size_t c_nch = 0, c_coff = 0, c_ends = 0;
+        int lb = 0, le = nsys, level = 0;
+        t->level_start[0] = 0;
+        while (true) {
+            int width = le - lb;
+            if ((rc = grow(nch, c_nch, width, 0, st))) return rc;
+            if ((rc = grow(coff, c_coff, width, 0, st))) return rc;
+            if ((rc = grow(ends, c_ends, (size_t)width * 8, 0, st))) return rc;
+            // a narrow level (few cells, long ranges) searches with a warp per boundary
+            const int wide = (int64_t)width * 8 * 32 <= (int64_t)t->num_sms * 1024 ? 1 : 0;
+            k_count_children<<<nblk((int64_t)width * 8 * (wide ? 32 : 1), 128), 128, 0, st>>>(
+                lb, le, level, t->prm.leaf_size, wide, first, count, ckey, d.keys, ends, nch);
+            count_launch(t);
+            if (wide) {
+                k_count_from_ends<<<nblk(width, 128), 128, 0, st>>>(lb, le, level, t->prm.leaf_size, first, count, ends,
+                                                                   nch);
+                count_launch(t);
+            }
+            size_t sb = 0;
+            cub::DeviceScan::ExclusiveSum(nullptr, sb, nch, coff, width, st);
+            if ((rc = dev_alloc(&tmp, sb, nullptr, st))) return rc;
+            FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, nch, coff, width, st));
+            count_launch(t);
+            dev_free(tmp, st);
+            int32_t last_off = 0, last_n = 0;
+            FMM_CUDA_TRY(cudaMemcpyAsync(&last_off, coff + width - 1, 4, cudaMemcpyDeviceToHost, st));
+            FMM_CUDA_TRY(cudaMemcpyAsync(&last_n, nch + width - 1, 4, cudaMemcpyDeviceToHost, st));
+            FMM_CUDA_TRY(cudaStreamSynchronize(st));
+            int total = last_off + last_n;
+            if ((size_t)le + total > c_lev) {
+                if ((rc = grow_all((size_t)le + total, (size_t)le))) return rc;
+            }
+            k_emit_children<<<nblk((int64_t)width * 8, 128), 128, 0, st>>>(lb, le, level, ends, nch, coff, le, lev, ckey,
+                                                                          first, count, par, cf, cc);
+            count_launch(t);
+            t->level_start[level + 1] = le;
+            if (total == 0) break;
+            lb = le;
+            le += total;
+            level++;
+        }
+        dev_free(nch, st);
+        dev_free(coff, st);
+        dev_free(ends, st);
+        stage_end(t, FMM_STAGE_OCTREE, st);
+        stage_begin(t, FMM_STAGE_SETUP, st);
+        t->ncell = le;
+        t->nlevel = level + 1;
+        for (int l = t->nlevel + 1; l <= FMM_MAX_LEVEL + 1; l++) t->level_start[l] = le;
+        // move the cell table into exactly sized, tree-owned arrays
+        const size_t nc = (size_t)t->ncell;
+        if ((rc = dev_alloc(&d.level, nc, t, st))) return rc;
+        if ((rc = dev_alloc(&d.ckey, nc, t, st))) return rc;
+        if ((rc = dev_alloc(&d.first, nc, t, st))) return rc;
+        if ((rc = dev_alloc(&d.count, nc, t, st))) return rc;
+        if ((rc = dev_alloc(&d.parent, nc, t, st))) return rc;
+        if ((rc = dev_alloc(&d.child_first, nc, t, st))) return rc;
+        if ((rc = dev_alloc(&d.child_count, nc, t, st))) return rc;
+        FMM_CUDA_TRY(cudaMemcpyAsync(d.level, lev, nc * 4, cudaMemcpyDeviceToDevice, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(d.ckey, ckey, nc * 8, cudaMemcpyDeviceToDevice, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(d.first, first, nc * 4, cudaMemcpyDeviceToDevice, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(d.count, count, nc * 4, cudaMemcpyDeviceToDevice, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(d.parent, par, nc * 4, cudaMemcpyDeviceToDevice, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(d.child_first, cf, nc * 4, cudaMemcpyDeviceToDevice, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(d.child_count, cc, nc * 4, cudaMemcpyDeviceToDevice, st));
+        dev_free(lev, st); dev_free(ckey, st); dev_free(first, st); dev_free(count, st);
+        dev_free(par, st); dev_free(cf, st); dev_free(cc, st);
+        // leaves
+        {
+            char* flag = nullptr;
+            int32_t *nsel = nullptr, *it = nullptr;
+            if ((rc = dev_alloc(&flag, nc, nullptr, st))) return rc;
+            if ((rc = dev_alloc(&it, nc, nullptr, st))) return rc;
+            if ((rc = dev_alloc(&nsel, 1, nullptr, st))) return rc;
+            if ((rc = dev_alloc(&d.leaves, nc, t, st))) return rc;
+            k_leaf_flags<<<nblk(nc, 256), 256, 0, st>>>((int)nc, d.child_count, flag, it);
+            count_launch(t);
+            size_t sb = 0;
+            cub::DeviceSelect::Flagged(nullptr, sb, it, flag, d.leaves, nsel, (int)nc, st);
+            if ((rc = dev_alloc(&tmp, sb, nullptr, st))) return rc;
+            FMM_CUDA_TRY(cub::DeviceSelect::Flagged(tmp, sb, it, flag, d.leaves, nsel, (int)nc, st));
+            count_launch(t);
+            int32_t h = 0;
+            FMM_CUDA_TRY(cudaMemcpyAsync(&h, nsel, 4, cudaMemcpyDeviceToHost, st));
+            FMM_CUDA_TRY(cudaStreamSynchronize(st));
+            t->nleaf = h;
+            dev_free(tmp, st); dev_free(flag, st); dev_free(nsel, st); dev_free(it, st);
+        }
     }
-    dev_free(nch, st);
-    dev_free(coff, st);
-    dev_free(ends, st);
-    stage_end(t, FMM_STAGE_OCTREE, st);
-    stage_begin(t, FMM_STAGE_SETUP, st);
-    t->ncell = le;
-    t->nlevel = level + 1;
-    for (int l = t->nlevel + 1; l <= FMM_MAX_LEVEL + 1; l++) t->level_start[l] = le;
-    // move the cell table into exactly sized, tree-owned arrays
     const size_t nc = (size_t)t->ncell;
-    if ((rc = dev_alloc(&d.level, nc, t, st))) return rc;
-    if ((rc = dev_alloc(&d.ckey, nc, t, st))) return rc;
-    if ((rc = dev_alloc(&d.first, nc, t, st))) return rc;
-    if ((rc = dev_alloc(&d.count, nc, t, st))) return rc;
-    if ((rc = dev_alloc(&d.parent, nc, t, st))) return rc;
-    if ((rc = dev_alloc(&d.child_first, nc, t, st))) return rc;
-    if ((rc = dev_alloc(&d.child_count, nc, t, st))) return rc;
-    FMM_CUDA_TRY(cudaMemcpyAsync(d.level, lev, nc * 4, cudaMemcpyDeviceToDevice, st));
-    FMM_CUDA_TRY(cudaMemcpyAsync(d.ckey, ckey, nc * 8, cudaMemcpyDeviceToDevice, st));
-    FMM_CUDA_TRY(cudaMemcpyAsync(d.first, first, nc * 4, cudaMemcpyDeviceToDevice, st));
-    FMM_CUDA_TRY(cudaMemcpyAsync(d.count, count, nc * 4, cudaMemcpyDeviceToDevice, st));
-    FMM_CUDA_TRY(cudaMemcpyAsync(d.parent, par, nc * 4, cudaMemcpyDeviceToDevice, st));
-    FMM_CUDA_TRY(cudaMemcpyAsync(d.child_first, cf, nc * 4, cudaMemcpyDeviceToDevice, st));
-    FMM_CUDA_TRY(cudaMemcpyAsync(d.child_count, cc, nc * 4, cudaMemcpyDeviceToDevice, st));
-    dev_free(lev, st); dev_free(ckey, st); dev_free(first, st); dev_free(count, st);
-    dev_free(par, st); dev_free(cf, st); dev_free(cc, st);
     if ((rc = dev_alloc(&d.centre, nc, t, st))) return rc;
     if ((rc = dev_alloc(&d.icentre, nc, t, st))) return rc;
     if ((rc = dev_alloc(&d.cu2f, nc, t, st))) return rc;
     k_centres<<<nblk(nc, 128), 128, 0, st>>>((int)nc, d.level, d.ckey, d.first, d.sys_off, nsys, d.geom, d.centre,
                                               d.icentre, d.cu2f);
     count_launch(t);
-    // leaves
-    {
-        char* flag = nullptr;
-        int32_t *nsel = nullptr, *it = nullptr;
-        if ((rc = dev_alloc(&flag, nc, nullptr, st))) return rc;
-        if ((rc = dev_alloc(&it, nc, nullptr, st))) return rc;
-        if ((rc = dev_alloc(&nsel, 1, nullptr, st))) return rc;
-        if ((rc = dev_alloc(&d.leaves, nc, t, st))) return rc;
-        k_leaf_flags<<<nblk(nc, 256), 256, 0, st>>>((int)nc, d.child_count, flag, it);
-        count_launch(t);
-        size_t sb = 0;
-        cub::DeviceSelect::Flagged(nullptr, sb, it, flag, d.leaves, nsel, (int)nc, st);
-        if ((rc = dev_alloc(&tmp, sb, nullptr, st))) return rc;
-        FMM_CUDA_TRY(cub::DeviceSelect::Flagged(tmp, sb, it, flag, d.leaves, nsel, (int)nc, st));
-        count_launch(t);
-        int32_t h = 0;
-        FMM_CUDA_TRY(cudaMemcpyAsync(&h, nsel, 4, cudaMemcpyDeviceToHost, st));
-        FMM_CUDA_TRY(cudaStreamSynchronize(st));
-        t->nleaf = h;
-        dev_free(tmp, st); dev_free(flag, st); dev_free(nsel, st); dev_free(it, st);
-        if ((rc = dev_alloc(&d.pleaf, (size_t)n, t, st))) return rc;
-        k_particle_leaf<<<nblk((int64_t)h * 32, 256), 256, 0, st>>>(h, d.leaves, d.first, d.count, d.pleaf);
-        count_launch(t);
-    }
+    if ((rc = dev_alloc(&d.pleaf, (size_t)n, t, st))) return rc;
+    k_particle_leaf<<<nblk((int64_t)t->nleaf * 32, 256), 256, 0, st>>>(t->nleaf, d.leaves, d.first, d.count,
+                                                                     d.pleaf);
+    count_launch(t);
 
     stage_end(t, FMM_STAGE_SETUP, st);
     // --- a3: breadth-first dual traversal from (root, root)

@@ -116,3 +116,17 @@ def test_autotuner_returns_a_candidate():
                                          torch.tensor(q, dtype=torch.float32, device=dev), offsets=off,
                                          candidates=(16, 32, 64), repeats=1, p=6, theta=0.5, precision=2)
     assert best in (16, 32, 64) and all(v > 0 for v in times.values())
+
+
+@pytest.mark.parametrize("leaf", [1, 16, 200])
+def test_batched_octree_paths_agree(leaf):
+    """The one-pass octree and the level-by-level one (FMM_BUILD_FALLBACKS)
+    give the same batched tree and lists, with systems of one particle and
+    systems below and above the leaf size (sizes 1 .. 1184)."""
+    import paper_1203_0889_gb300 as fmm
+    systems, pos, q, off = _systems(11, lo=1, hi=2500, seed=23)
+    assert np.diff(off).min() == 1
+    a = _batched(pos, off, p=2, leaf_size=leaf, theta=0.5).export()
+    b = _batched(pos, off, p=2, leaf_size=leaf, theta=0.5, flags=fmm.BUILD_FALLBACKS).export()
+    for k in a:
+        assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k

@@ -78,10 +78,11 @@ def test_non_finite_positions_rejected():
 @pytest.mark.parametrize("name,n,leaf,theta,prec", [("plummer", 60000, 32, 0.4, 3), ("clustered", 50000, 16, 0.5, 3),
                                                     ("uniform", 30000, 24, 0.5, 2)])
 def test_build_fallback_paths_bit_exact(name, n, leaf, theta, prec):
-    """FMM_BUILD_FALLBACKS forces the round-by-round traversal and (mixed mode)
-    the sort-based class grouping, which otherwise run only on overflow: the
-    tree and both lists still match the oracle bit for bit, and the class
-    structure matches the default build."""
+    """FMM_BUILD_FALLBACKS builds the octree level by level (instead of in one
+    pass) and forces the round-by-round traversal and (mixed mode) the
+    sort-based class grouping, which otherwise run only on overflow: the tree
+    and both lists still match the oracle bit for bit, and the class structure
+    matches the default build."""
     import paper_1203_0889_gb300 as fmm
     wl = W.make_workload(name, n=n)
     ref = O.build_tree(wl.pos, leaf, theta)
