@@ -79,7 +79,11 @@ extern "C" {
 #define FMM_STAGE_L2P      10   /* L2P + near field + output in input order */
 #define FMM_STAGE_QUEUE    11   /* persistent task-queue kernel (all evaluation stages) */
 #define FMM_STAGE_M2L_TC   12   /* tensor-core part of M2L (inside FMM_STAGE_M2L) */
-#define FMM_NUM_STAGES     13
+#define FMM_STAGE_TRAVERSAL 13  /* dual traversal and its size read-back (inside FMM_STAGE_LISTS) */
+#define FMM_STAGE_CLASSES  14   /* M2L list: class grouping, or sort and CSR (inside FMM_STAGE_LISTS) */
+#define FMM_STAGE_P2P_LIST 15   /* P2P list: sort, CSR, records; on the tree's second stream when it has
+                                   one (inside FMM_STAGE_LISTS) */
+#define FMM_NUM_STAGES     16
 
 typedef struct fmm_tree fmm_tree;   /* opaque, library-owned */
 
@@ -221,7 +225,7 @@ int fmm_tree_export(const fmm_tree* tree, uint64_t* keys, int64_t* perm, int32_t
  */
 int fmm_stage_times(const fmm_tree* tree, double* ms, int32_t max_stages);
 
-/* Name of stage i ("keys", "octree", ..., "queue"), or "" when out of range. */
+/* Name of stage i ("keys", "octree", ..., "p2p_list"), or "" when out of range. */
 const char* fmm_stage_name(int32_t i);
 
 /* Kernels this tree launched: in its build (build != 0) or in its last evaluation. */

@@ -33,7 +33,7 @@ F64, F32 = 0, 1
 PREC_FP64, PREC_FP32_P2P, PREC_FP32, PREC_MIXED_TC = 0, 1, 2, 3
 OUT_FIELD, STAGED, TIMING, NO_OVERLAP, BUILD_FALLBACKS = 1, 2, 4, 8, 16
 STAGE_NAMES = ("keys", "octree", "lists", "setup", "prepare", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p", "queue",
-               "m2l_tc")
+               "m2l_tc", "traversal", "classes", "p2p_list")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")

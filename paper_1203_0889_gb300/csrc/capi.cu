@@ -171,7 +171,7 @@ int fmm_evaluate(fmm_tree* tree, const void* q, void* phi, void* force, int dtyp
         cudaError_t e = cudaMemsetAsync(tree->d.status, 0, sizeof(int), (cudaStream_t)stream);
         if (e != cudaSuccess) { fmm_set_error("evaluate: %s", cudaGetErrorString(e)); return FMM_ERR_CUDA; }
     }
-    for (int s = FMM_STAGE_PREPARE; s < FMM_NUM_STAGES; s++) tree->ev_used[s] = false;
+    for (int s = FMM_STAGE_PREPARE; s <= FMM_STAGE_M2L_TC; s++) tree->ev_used[s] = false;   // evaluation stages
     int rc = fmm::evaluate_impl(tree, q, phi, force, dtype, (cudaStream_t)stream);
     tree->launch_ctr = nullptr;
     return rc;
@@ -365,8 +365,9 @@ void fmm_tree_destroy(fmm_tree* t) {
     delete t;
 }
 
-static const char* k_stage_names[FMM_NUM_STAGES] = {"keys", "octree", "lists", "setup", "prepare", "p2p",
-                                                     "p2m", "m2m", "m2l", "l2l", "l2p", "queue", "m2l_tc"};
+static const char* k_stage_names[FMM_NUM_STAGES] = {"keys", "octree", "lists",    "setup",     "prepare", "p2p",
+                                                     "p2m",  "m2m",    "m2l",      "l2l",       "l2p",     "queue",
+                                                     "m2l_tc", "traversal", "classes", "p2p_list"};
 
 const char* fmm_stage_name(int32_t i) { return (i >= 0 && i < FMM_NUM_STAGES) ? k_stage_names[i] : ""; }
 

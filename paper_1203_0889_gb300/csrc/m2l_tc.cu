@@ -207,8 +207,53 @@ __global__ void k_unpack_rem(int64_t n, const uint64_t* k, int32_t* tg, int32_t*
     if (i < n) { tg[i] = (int32_t)(k[i] >> 32); sr[i] = (int32_t)(k[i] & 0xffffffffu); }
 }
 
+// Entry (o, i) of a class operator: output coefficient o = (k, l, re|im),
+// input coefficient i = (n, m, re|im) of the scaled multipole; If holds the
+// irregular harmonics of the class offset, rpow[n] = rho^n.
+__device__ __forceinline__ float class_operator_entry(int o, int i, int K2, const int8_t* tk, const int8_t* tm,
+                                                      const float* rpow, const cplx<float>* If) {
+    if (o >= K2 || i >= K2) return 0.f;
+    const int k = tk[o >> 1], l = tm[o >> 1], pa = o & 1;
+    const int n = tk[i >> 1], m = tm[i >> 1], pb = i & 1;
+    const float s = (k & 1) ? -rpow[n] : rpow[n];
+    const cplx<float>* Ij = If + tri(n + k, 0);
+    if (m == 0) {
+        const cplx<float> x = Ij[l];
+        return pb ? 0.f : (pa ? -s * x.im : s * x.re);
+    }
+    const cplx<float> xa = Ij[m + l];
+    const float Ar = xa.re, Ai = -xa.im;
+    float Br, Bi;
+    if (l >= m) {
+        const cplx<float> xb = Ij[l - m];
+        const float sg = (m & 1) ? -1.f : 1.f;
+        Br = sg * xb.re;
+        Bi = -sg * xb.im;
+    } else {
+        const cplx<float> xb = Ij[m - l];
+        const float sg = (l & 1) ? -1.f : 1.f;
+        Br = sg * xb.re;
+        Bi = sg * xb.im;
+    }
+    if (!pa && !pb) return s * (Ar + Br);
+    if (!pa && pb) return s * (Bi - Ai);
+    if (pa && !pb) return s * (Ai + Bi);
+    return s * (Ar - Br);
+}
+
+// two FP32 values split into bf16 hi and lo parts, packed in pairs
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
+    const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
+    hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+    lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+}
+
 // Operator of one class, split into bf16 hi/lo, K-major core-matrix layout:
 // rows = output coefficients (k, l, re|im), columns = input (n, m, re|im).
+// Each thread writes whole 16-byte core-matrix rows (8 columns of one row),
+// consecutive threads consecutive rows in memory, for hi and for lo.
 __global__ void k_class_operators(int p, int Kp, const uint64_t* __restrict__ ukeys,
                                   __nv_bfloat16* __restrict__ ops) {
     // harmonics in FP64 (one column per thread), entries assembled in FP32
@@ -216,7 +261,7 @@ __global__ void k_class_operators(int p, int Kp, const uint64_t* __restrict__ uk
     extern __shared__ unsigned char smraw[];
     cplx<double>* I = reinterpret_cast<cplx<double>*>(smraw);
     cplx<float>* If = reinterpret_cast<cplx<float>*>(I + ntri(2 * p));
-    float* rpow = reinterpret_cast<float*>(If + ntri(2 * p));   // (-1)^k-free rho^n, n <= p
+    float* rpow = reinterpret_cast<float*>(If + ntri(2 * p));   // rho^n, n <= p
     int8_t* tk = reinterpret_cast<int8_t*>(rpow + 32);            // tri index -> (n, m)
     int8_t* tm = tk + 256;
     const int c = blockIdx.x;
@@ -226,53 +271,28 @@ __global__ void k_class_operators(int p, int Kp, const uint64_t* __restrict__ uk
     const double dx = (double)((int)((key >> 32) & 0xffff) - 32768) * scale;
     const double dy = (double)((int)((key >> 16) & 0xffff) - 32768) * scale;
     const double dz = (double)((int)(key & 0xffff) - 32768) * scale;
-    const double rho = dl >= 0 ? (double)(1 << dl) : 1.0 / (double)(1 << (-dl));
     for (int m = threadIdx.x; m <= 2 * p; m += blockDim.x) irregular_column<double>(2 * p, m, dx, dy, dz, I);
     for (int n = 0; n <= p; n++)
         for (int m = threadIdx.x; m <= n; m += blockDim.x) { tk[tri(n, m)] = (int8_t)n; tm[tri(n, m)] = (int8_t)m; }
-    if (threadIdx.x <= p) rpow[threadIdx.x] = (float)pow(rho, (double)threadIdx.x);
+    // rho = 2^dl exactly, so rho^n = 2^(dl n), rounded to FP32
+    if (threadIdx.x <= p) rpow[threadIdx.x] = ldexpf(1.0f, dl * (int)threadIdx.x);
     __syncthreads();
     for (int e = threadIdx.x; e < ntri(2 * p); e += blockDim.x) If[e] = cmk<float>((float)I[e].re, (float)I[e].im);
     __syncthreads();
-    const int K2 = 2 * ntri(p);
-    __nv_bfloat16* hi = ops + (size_t)c * 2 * Kp * Kp;
-    __nv_bfloat16* lo = hi + (size_t)Kp * Kp;
-    for (int e = threadIdx.x; e < Kp * Kp; e += blockDim.x) {
-        int o = e / Kp, i = e % Kp;
-        float v = 0.f;
-        if (o < K2 && i < K2) {
-            int k = tk[o >> 1], l = tm[o >> 1], pa = o & 1;
-            int n = tk[i >> 1], m = tm[i >> 1], pb = i & 1;
-            int j = n + k;
-            float s = (k & 1) ? -rpow[n] : rpow[n];
-            const cplx<float>* Ij = If + tri(j, 0);
-            if (m == 0) {
-                cplx<float> x = Ij[l];
-                v = pb ? 0.f : (pa ? -s * x.im : s * x.re);
-            } else {
-                cplx<float> xa = Ij[m + l];
-                float Ar = xa.re, Ai = -xa.im, Br, Bi;
-                if (l >= m) {
-                    cplx<float> xb = Ij[l - m];
-                    float sg = (m & 1) ? -1.f : 1.f;
-                    Br = sg * xb.re; Bi = -sg * xb.im;
-                } else {
-                    cplx<float> xb = Ij[m - l];
-                    float sg = (l & 1) ? -1.f : 1.f;
-                    Br = sg * xb.re; Bi = sg * xb.im;
-                }
-                if (!pa && !pb) v = s * (Ar + Br);
-                else if (!pa && pb) v = s * (Bi - Ai);
-                else if (pa && !pb) v = s * (Ai + Bi);
-                else v = s * (Ar - Br);
-            }
-        }
-        float f = v;
-        __nv_bfloat16 h = __float2bfloat16_rn(f);
-        __nv_bfloat16 r = __float2bfloat16_rn(f - __bfloat162float(h));
-        uint32_t off = tc::core_offset(o, i, Kp) >> 1;
-        hi[off] = h;
-        lo[off] = r;
+    const int K2 = 2 * ntri(p), kg = Kp >> 3, nchunk = Kp * kg;
+    uint4* hi = reinterpret_cast<uint4*>(ops + (size_t)c * 2 * Kp * Kp);
+    uint4* lo = hi + nchunk;
+    for (int q = threadIdx.x; q < nchunk; q += blockDim.x) {
+        // 16-byte chunk q = (core (row group, column group), row within the core)
+        const int core = q >> 3;
+        const int o = (core / kg) * 8 + (q & 7), i0 = (core % kg) * 8;
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            split2(class_operator_entry(o, i0 + 2 * u, K2, tk, tm, rpow, If),
+                   class_operator_entry(o, i0 + 2 * u + 1, K2, tk, tm, rpow, If), h[u], l[u]);
+        hi[q] = make_uint4(h[0], h[1], h[2], h[3]);
+        lo[q] = make_uint4(l[0], l[1], l[2], l[3]);
     }
 }
 

@@ -821,9 +821,10 @@ static int bits_for(int64_t v) {
     return b;
 }
 
-// sort (target, source) pairs and build the CSR arrays
-static int finish_list(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, int32_t** src,
-                       int32_t** tgt, cudaStream_t st) {
+// sort (target, source) pairs and build the CSR arrays: one radix sort of
+// the packed pairs (the FMM_BUILD_FALLBACKS path)
+static int finish_list_radix(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, int32_t** src,
+                             int32_t** tgt, cudaStream_t st) {
     int rc;
     uint64_t *k0 = nullptr, *k1 = nullptr;
     if ((rc = dev_alloc(&k0, np, nullptr, st))) return rc;
@@ -845,6 +846,68 @@ static int finish_list(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, in
     dev_free(tmp, st);
     dev_free(k0, st);
     dev_free(k1, st);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+__global__ void k_count_targets(const int2* __restrict__ pr, int64_t np, unsigned long long* cnt) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < np) atomicAdd(cnt + pr[e].x, 1ull);
+}
+
+// sources into their target's segment, in arrival order
+__global__ void k_scatter_sources(const int2* __restrict__ pr, int64_t np, const int64_t* __restrict__ start,
+                                  int32_t* fill, int32_t* src) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= np) return;
+    const int2 v = pr[e];
+    src[start[v.x] + atomicAdd(fill + v.x, 1)] = v.y;
+}
+
+// target of every entry of the CSR (one warp per cell)
+__global__ void k_fill_targets(int ncell, const int64_t* __restrict__ start, int32_t* tgt) {
+    const int c = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (c >= ncell) return;
+    for (int64_t i = start[c] + lane; i < start[c + 1]; i += 32) tgt[i] = c;
+}
+
+// The same CSR without a global sort: count the pairs of every target, scan,
+// scatter the sources into their target's segment, and sort each segment
+// (segments are short: a target's list).  Same arrays as finish_list_radix.
+static int finish_list(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, int32_t** src, int32_t** tgt,
+                       cudaStream_t st) {
+    if (t->prm.flags & FMM_BUILD_FALLBACKS) return finish_list_radix(t, pairs, np, start, src, tgt, st);
+    int rc;
+    const int nc = t->ncell;
+    unsigned long long* cnt = nullptr;
+    int32_t *fill = nullptr, *tmp_src = nullptr;
+    char* tmp = nullptr;
+    if ((rc = dev_alloc(&cnt, (size_t)nc + 1, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&fill, (size_t)nc, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&tmp_src, (size_t)np, nullptr, st))) return rc;
+    if ((rc = dev_alloc(src, np, t, st))) return rc;
+    if ((rc = dev_alloc(start, (size_t)nc + 1, t, st))) return rc;
+    if (tgt && (rc = dev_alloc(tgt, np, t, st))) return rc;
+    FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * ((size_t)nc + 1), st));
+    FMM_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)nc, st));
+    if (np) { k_count_targets<<<nblk(np, 256), 256, 0, st>>>(pairs, np, cnt); count_launch(t); }
+    size_t sb = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, sb, cnt, (unsigned long long*)*start, nc + 1, st);
+    size_t sb2 = 0;
+    cub::DeviceSegmentedSort::SortKeys(nullptr, sb2, tmp_src, *src, np, nc, *start, *start + 1, st);
+    if ((rc = dev_alloc(&tmp, std::max(sb, sb2), nullptr, st))) return rc;
+    FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, cnt, (unsigned long long*)*start, nc + 1, st));
+    count_launch(t);
+    if (np) {
+        k_scatter_sources<<<nblk(np, 256), 256, 0, st>>>(pairs, np, *start, fill, tmp_src);
+        FMM_CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(tmp, sb2, tmp_src, *src, np, nc, *start, *start + 1, st));
+        count_launch(t, 2);
+        if (tgt) { k_fill_targets<<<nblk((int64_t)nc * 32, 256), 256, 0, st>>>(nc, *start, *tgt); count_launch(t); }
+    }
+    dev_free(tmp, st);
+    dev_free(cnt, st);
+    dev_free(fill, st);
+    dev_free(tmp_src, st);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
@@ -1158,6 +1221,7 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     stage_end(t, FMM_STAGE_SETUP, st);
     // --- a3: breadth-first dual traversal from (root, root)
     stage_begin(t, FMM_STAGE_LISTS, st);
+    stage_begin(t, FMM_STAGE_TRAVERSAL, st);
     size_t c_front = 1024, c_next = 1024, c_m = 1024, c_p = 1024;
     int2 *front = nullptr, *next = nullptr, *m2l = nullptr, *p2p = nullptr;
     if ((rc = grow(front, c_front = 0, std::max<size_t>(1024, nsys), 0, st))) return rc;
@@ -1234,6 +1298,7 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         std::swap(c_front, c_next);
     }
     dev_free(front, st); dev_free(next, st); dev_free(ctr, st);
+    stage_end(t, FMM_STAGE_TRAVERSAL, st);
     t->nm2l = nm;
     t->np2p = npp;
     // The P2P list and its records go on the second stream of the evaluation's
@@ -1244,6 +1309,7 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
         FMM_CUDA_TRY(cudaStreamWaitEvent(sl, t->ev_fork, 0));
     }
+    stage_begin(t, FMM_STAGE_P2P_LIST, sl);
     int32_t* p2p_tgt = nullptr;
     if ((rc = finish_list(t, p2p, npp, &d.p2p_start, &d.p2p_src, &p2p_tgt, sl))) return rc;
     {
@@ -1265,16 +1331,19 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         dev_free(cnt, sl); dev_free(gcum, sl); dev_free(p2p_tgt, sl);
     }
     dev_free(p2p, sl);
+    stage_end(t, FMM_STAGE_P2P_LIST, sl);
     if (sl != st) FMM_CUDA_TRY(cudaEventRecord(t->ev_join_hi, sl));
     const bool want_classes = t->prm.precision == FMM_PREC_MIXED_TC && tc_supported(t->prm.p);
     // with the tensor cores the M2L pairs are grouped by class straight from the
     // traversal output; no (target, source) order is needed on that path
+    stage_begin(t, FMM_STAGE_CLASSES, st);
     if (want_classes) {
         if ((rc = build_m2l_classes(t, m2l, st))) return rc;
     } else if ((rc = finish_list(t, m2l, nm, &d.m2l_start, &d.m2l_src, nullptr, st))) {
         return rc;
     }
     dev_free(m2l, st);
+    stage_end(t, FMM_STAGE_CLASSES, st);
     if (sl != st) FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join_hi, 0));
     if (queue_supported(t) && (rc = build_queue(t, st))) return rc;
     stage_end(t, FMM_STAGE_LISTS, st);

@@ -65,6 +65,16 @@ def test_version_and_argument_errors(lib):
     lib.fmm_tree_destroy(None)
 
 
+def test_stage_names_agree(lib):
+    """Stage names of the library, the binding and the header's stage count."""
+    import paper_1203_0889_gb300 as fmm
+    txt = open(os.path.join(ROOT, "include", "fmm.h")).read()
+    nstage = int(re.search(r"#define FMM_NUM_STAGES\s+(\d+)", txt).group(1))
+    assert len(fmm.STAGE_NAMES) == nstage
+    assert [lib.fmm_stage_name(i).decode() for i in range(nstage)] == list(fmm.STAGE_NAMES)
+    assert lib.fmm_stage_name(nstage) == b"" and lib.fmm_stage_name(-1) == b""
+
+
 def test_binding_refuses_without_library(monkeypatch, tmp_path):
     import paper_1203_0889_gb300 as fmm
     monkeypatch.setattr(fmm, "_lib", None)

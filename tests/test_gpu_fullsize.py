@@ -44,6 +44,13 @@ def test_bench_workload(plummer, prec, tol):
     phi, force = t.evaluate(q)
     torch.cuda.synchronize()
     assert t.status() == fmm.FMM_OK
+    # stage timing: every build stage and the list sub-stages (nested in "lists")
+    ms = t.stage_times()
+    for name in ("keys", "octree", "setup", "lists", "traversal", "classes", "p2p_list", "prepare"):
+        assert name in ms and ms[name] >= 0.0, name
+    assert ("queue" in ms) != ("l2p" in ms)      # task-queue or stage-by-stage evaluation
+    for name in ("traversal", "classes", "p2p_list"):
+        assert ms[name] <= ms["lists"] + 1e-3, name
     phi, force = phi.cpu().numpy()[idx], force.cpu().numpy()[idx]
     assert O.rel_l2(phi, ref_phi) <= tol
     assert O.rel_l2(force, ref_f) <= tol
