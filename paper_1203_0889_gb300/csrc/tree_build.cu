@@ -821,10 +821,9 @@ static int bits_for(int64_t v) {
     return b;
 }
 
-// sort (target, source) pairs and build the CSR arrays: one radix sort of
-// the packed pairs (the FMM_BUILD_FALLBACKS path)
-static int finish_list_radix(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, int32_t** src,
-                             int32_t** tgt, cudaStream_t st) {
+// sort (target, source) pairs and build the CSR arrays
+static int finish_list(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, int32_t** src,
+                       int32_t** tgt, cudaStream_t st) {
     int rc;
     uint64_t *k0 = nullptr, *k1 = nullptr;
     if ((rc = dev_alloc(&k0, np, nullptr, st))) return rc;
@@ -850,67 +849,6 @@ static int finish_list_radix(fmm_tree* t, int2* pairs, int64_t np, int64_t** sta
     return FMM_OK;
 }
 
-__global__ void k_count_targets(const int2* __restrict__ pr, int64_t np, unsigned long long* cnt) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e < np) atomicAdd(cnt + pr[e].x, 1ull);
-}
-
-// sources into their target's segment, in arrival order
-__global__ void k_scatter_sources(const int2* __restrict__ pr, int64_t np, const int64_t* __restrict__ start,
-                                  int32_t* fill, int32_t* src) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= np) return;
-    const int2 v = pr[e];
-    src[start[v.x] + atomicAdd(fill + v.x, 1)] = v.y;
-}
-
-// target of every entry of the CSR (one warp per cell)
-__global__ void k_fill_targets(int ncell, const int64_t* __restrict__ start, int32_t* tgt) {
-    const int c = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (c >= ncell) return;
-    for (int64_t i = start[c] + lane; i < start[c + 1]; i += 32) tgt[i] = c;
-}
-
-// The same CSR without a global sort: count the pairs of every target, scan,
-// scatter the sources into their target's segment, and sort each segment
-// (segments are short: a target's list).  Same arrays as finish_list_radix.
-static int finish_list(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, int32_t** src, int32_t** tgt,
-                       cudaStream_t st) {
-    if (t->prm.flags & FMM_BUILD_FALLBACKS) return finish_list_radix(t, pairs, np, start, src, tgt, st);
-    int rc;
-    const int nc = t->ncell;
-    unsigned long long* cnt = nullptr;
-    int32_t *fill = nullptr, *tmp_src = nullptr;
-    char* tmp = nullptr;
-    if ((rc = dev_alloc(&cnt, (size_t)nc + 1, nullptr, st))) return rc;
-    if ((rc = dev_alloc(&fill, (size_t)nc, nullptr, st))) return rc;
-    if ((rc = dev_alloc(&tmp_src, (size_t)np, nullptr, st))) return rc;
-    if ((rc = dev_alloc(src, np, t, st))) return rc;
-    if ((rc = dev_alloc(start, (size_t)nc + 1, t, st))) return rc;
-    if (tgt && (rc = dev_alloc(tgt, np, t, st))) return rc;
-    FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * ((size_t)nc + 1), st));
-    FMM_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)nc, st));
-    if (np) { k_count_targets<<<nblk(np, 256), 256, 0, st>>>(pairs, np, cnt); count_launch(t); }
-    size_t sb = 0;
-    cub::DeviceScan::ExclusiveSum(nullptr, sb, cnt, (unsigned long long*)*start, nc + 1, st);
-    size_t sb2 = 0;
-    cub::DeviceSegmentedSort::SortKeys(nullptr, sb2, tmp_src, *src, np, nc, *start, *start + 1, st);
-    if ((rc = dev_alloc(&tmp, std::max(sb, sb2), nullptr, st))) return rc;
-    FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, cnt, (unsigned long long*)*start, nc + 1, st));
-    count_launch(t);
-    if (np) {
-        k_scatter_sources<<<nblk(np, 256), 256, 0, st>>>(pairs, np, *start, fill, tmp_src);
-        FMM_CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(tmp, sb2, tmp_src, *src, np, nc, *start, *start + 1, st));
-        count_launch(t, 2);
-        if (tgt) { k_fill_targets<<<nblk((int64_t)nc * 32, 256), 256, 0, st>>>(nc, *start, *tgt); count_launch(t); }
-    }
-    dev_free(tmp, st);
-    dev_free(cnt, st);
-    dev_free(fill, st);
-    dev_free(tmp_src, st);
-    FMM_CUDA_TRY(cudaGetLastError());
-    return FMM_OK;
-}
 
 // a2 in one pass: leaf level of every particle, one scan of the per-level
 // counts, then every cell and its links (the level-by-level octree serves
