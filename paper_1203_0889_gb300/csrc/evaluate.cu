@@ -303,24 +303,33 @@ __global__ void __launch_bounds__(P2P_THREADS, sizeof(T) == 4 ? 9 : 1) k_p2p(int
     p2p_leaf<T>(leaves[blockIdx.x], first, count, start, rec, xq, icentre, cu2f, near, buf, part);
 }
 
-// one warp per leaf: L2P + near field + output in input order
+// L2P + near field + output in input order, one thread per sorted particle
+// (its leaf from pleaf; the leaf's local expansion read through L1, shared by
+// the leaf's particles), with the recurrence's reciprocals from tables
+constexpr int L2P_THREADS = 256;
 template <typename T, typename O>
-__global__ void k_l2p_finalize(int p, int nleaf, const int32_t* __restrict__ leaves,
-                               const int32_t* __restrict__ first, const int32_t* __restrict__ count,
-                               const double4_32a* __restrict__ centre, const double4_32a* __restrict__ xq,
-                               const int32_t* __restrict__ perm, const cplx<T>* __restrict__ L,
-                               const double* __restrict__ near, O* __restrict__ phi_out, O* __restrict__ force_out,
-                               int field) {
-    extern __shared__ unsigned char smem_raw[];
-    const int K = ntri(p), KS = kstride(p);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cplx<T>* Ls = reinterpret_cast<cplx<T>*>(smem_raw) + warp * K;
-    const int li = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (li >= nleaf) return;
-    const int c = leaves[li];
-    for (int j = lane; j < K; j += 32) Ls[j] = L[(int64_t)c * KS + j];
-    __syncwarp();
-    l2p_particles<T, O, false>(p, c, lane, 32, Ls, first, count, centre, xq, perm, near, phi_out, force_out, field);
+__global__ void __launch_bounds__(L2P_THREADS) k_l2p_points(int p, int64_t n, const int32_t* __restrict__ pleaf,
+                                                            const double4_32a* __restrict__ centre,
+                                                            const double4_32a* __restrict__ xq,
+                                                            const int32_t* __restrict__ perm,
+                                                            const cplx<T>* __restrict__ L,
+                                                            const double* __restrict__ near, O* __restrict__ phi_out,
+                                                            O* __restrict__ force_out, int field) {
+    __shared__ T rm[FMM_MAX_P + 1], rt[(FMM_MAX_P + 1) * (FMM_MAX_P + 2) / 2];
+    for (int m = threadIdx.x; m <= p; m += blockDim.x) rm[m] = m > 0 ? T(1) / T(2 * m) : T(0);
+    for (int n = 0; n <= p; n++)
+        for (int m = threadIdx.x; m <= n; m += blockDim.x) rt[tri(n, m)] = n >= m + 2 ? T(1) / T((n + m) * (n - m)) : T(0);
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = pleaf[i];
+    const double4_32a cc = centre[c];
+    const double invh = 1.0 / cc.w;
+    const double4_32a a = xq[i];
+    const T ux = (T)((a.x - cc.x) * invh), uy = (T)((a.y - cc.y) * invh), uz = (T)((a.z - cc.z) * invh);
+    T fp, gx, gy, gz;
+    l2p_point<T, true>(p, ux, uy, uz, L + (int64_t)c * kstride(p), rm, rt, fp, gx, gy, gz);
+    l2p_store<T, O, false>(i, invh, a.w, fp, gx, gy, gz, perm, near, phi_out, force_out, field);
 }
 
 // ---------------------------------------------------------------------------
@@ -502,9 +511,8 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     if (sp != st) FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
     const int W = 4;
     stage_begin(t, FMM_STAGE_L2P, st);
-    k_l2p_finalize<T, O><<<nblk(t->nleaf, W), 32 * W, W * K * sizeof(cplx<T>), st>>>(
-        p, t->nleaf, d.leaves, d.first, d.count, d.centre, xq64, d.perm, L, d.near, phi, force,
-        (t->prm.flags & FMM_OUT_FIELD) ? 1 : 0);
+    k_l2p_points<T, O><<<nblk(n, L2P_THREADS), L2P_THREADS, 0, st>>>(p, n, d.pleaf, d.centre, xq64, d.perm, L, d.near,
+                                                                   phi, force, (t->prm.flags & FMM_OUT_FIELD) ? 1 : 0);
     count_launch(t);
     stage_end(t, FMM_STAGE_L2P, st);
     FMM_CUDA_TRY(cudaGetLastError());

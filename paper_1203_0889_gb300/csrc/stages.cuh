@@ -543,6 +543,71 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
 }
 
 // ---------------------------------------------------------------- L2P
+// Lt(c) and its gradient at u = (x - centre) / h: the regular harmonics of u
+// by the recurrence in n for each m, accumulated against Ls.  TAB: the
+// reciprocals 1/(2m) and 1/((n+m)(n-m)) come from tables (rm[m],
+// rt[tri(n, m)]) holding the values the divisions give, so both forms agree
+// bit for bit.
+template <typename T, bool TAB>
+__device__ __forceinline__ void l2p_point(int p, T ux, T uy, T uz, const cplx<T>* Ls, const T* rm, const T* rt,
+                                          T& fp, T& gx, T& gy, T& gz) {
+    const T r2 = ux * ux + uy * uy + uz * uz;
+    fp = 0; gx = 0; gy = 0; gz = 0;
+    cplx<T> rmm = cmk<T>(1, 0);
+    for (int m = 0; m <= p; m++) {
+        if (m > 0) rmm = cscale(cmul(rmm, cmk<T>(ux, uy)), TAB ? rm[m] : T(1) / T(2 * m));
+        cplx<T> a0 = rmm, b0 = cscale(rmm, uz);
+        const T w = m == 0 ? T(1) : T(2);
+        for (int n = m; n <= p; n++) {
+            cplx<T> S;
+            if (n == m) S = a0;
+            else if (n == m + 1) S = b0;
+            else {
+                const T inv = TAB ? rt[tri(n, m)] : T(1) / T((n + m) * (n - m));
+                S = cmk<T>((T(2 * n - 1) * uz * b0.re - r2 * a0.re) * inv, (T(2 * n - 1) * uz * b0.im - r2 * a0.im) * inv);
+                a0 = b0; b0 = S;
+            }
+            const cplx<T> Lnm = Ls[tri(n, m)];
+            fp += w * (Lnm.re * S.re - Lnm.im * S.im);
+            if (n + 1 <= p) {
+                const cplx<T>* L1 = Ls + tri(n + 1, 0);
+                const cplx<T> lz = L1[m];
+                gz += w * (lz.re * S.re - lz.im * S.im);
+                if (m == 0) {
+                    gx += L1[1].re * S.re;
+                    gy -= L1[1].im * S.re;
+                } else {
+                    const cplx<T> up = L1[m + 1], dn = L1[m - 1];
+                    const cplx<T> A = csub(up, dn), B = cadd(up, dn);
+                    gx += A.re * S.re - A.im * S.im;
+                    gy += -(B.im * S.re + B.re * S.im);  // Re(i B S)
+                }
+            }
+        }
+    }
+}
+
+// sorted particle gi: far field (scaled by the leaf's 1/h) plus near field,
+// written in input order
+template <typename T, typename O, bool COH>
+__device__ __forceinline__ void l2p_store(int64_t gi, double invh, double qi, T fp, T gx, T gy, T gz,
+                                          const int32_t* __restrict__ perm, const double* __restrict__ near,
+                                          O* __restrict__ phi_out, O* __restrict__ force_out, int field) {
+    const double ph = (double)fp * invh + ldx<COH>(near + 4 * gi);
+    const double ih2 = invh * invh;
+    const double ex = -((double)gx * ih2 + ldx<COH>(near + 4 * gi + 1));
+    const double ey = -((double)gy * ih2 + ldx<COH>(near + 4 * gi + 2));
+    const double ez = -((double)gz * ih2 + ldx<COH>(near + 4 * gi + 3));
+    const int64_t o = perm[gi];
+    if (phi_out) phi_out[o] = (O)ph;
+    if (force_out) {
+        const double s = field ? 1.0 : qi;
+        force_out[3 * o] = (O)(s * ex);
+        force_out[3 * o + 1] = (O)(s * ey);
+        force_out[3 * o + 2] = (O)(s * ez);
+    }
+}
+
 // Particles tid, tid + nthr, ... of leaf c, with Lt(c) already in Ls; adds the
 // near field and writes the outputs in input order.
 template <typename T, typename O, bool COH>
@@ -557,54 +622,9 @@ __device__ void l2p_particles(int p, int c, int tid, int nthr, const cplx<T>* Ls
     for (int i = tid; i < cnt; i += nthr) {
         const double4_32a a = xq[f + i];
         const T ux = (T)((a.x - cc.x) * invh), uy = (T)((a.y - cc.y) * invh), uz = (T)((a.z - cc.z) * invh);
-        const T r2 = ux * ux + uy * uy + uz * uz;
-        T fp = 0, gx = 0, gy = 0, gz = 0;
-        cplx<T> rmm = cmk<T>(1, 0);
-        for (int m = 0; m <= p; m++) {
-            if (m > 0) rmm = cscale(cmul(rmm, cmk<T>(ux, uy)), T(1) / T(2 * m));
-            cplx<T> a0 = rmm, b0 = cscale(rmm, uz);
-            const T w = m == 0 ? T(1) : T(2);
-            for (int n = m; n <= p; n++) {
-                cplx<T> S;
-                if (n == m) S = a0;
-                else if (n == m + 1) S = b0;
-                else {
-                    const T inv = T(1) / T((n + m) * (n - m));
-                    S = cmk<T>((T(2 * n - 1) * uz * b0.re - r2 * a0.re) * inv, (T(2 * n - 1) * uz * b0.im - r2 * a0.im) * inv);
-                    a0 = b0; b0 = S;
-                }
-                const cplx<T> Lnm = Ls[tri(n, m)];
-                fp += w * (Lnm.re * S.re - Lnm.im * S.im);
-                if (n + 1 <= p) {
-                    const cplx<T>* L1 = Ls + tri(n + 1, 0);
-                    const cplx<T> lz = L1[m];
-                    gz += w * (lz.re * S.re - lz.im * S.im);
-                    if (m == 0) {
-                        gx += L1[1].re * S.re;
-                        gy -= L1[1].im * S.re;
-                    } else {
-                        const cplx<T> up = L1[m + 1], dn = L1[m - 1];
-                        const cplx<T> A = csub(up, dn), B = cadd(up, dn);
-                        gx += A.re * S.re - A.im * S.im;
-                        gy += -(B.im * S.re + B.re * S.im);  // Re(i B S)
-                    }
-                }
-            }
-        }
-        const int64_t gi = f + i;
-        const double ph = (double)fp * invh + ldx<COH>(near + 4 * gi);
-        const double ih2 = invh * invh;
-        const double ex = -((double)gx * ih2 + ldx<COH>(near + 4 * gi + 1));
-        const double ey = -((double)gy * ih2 + ldx<COH>(near + 4 * gi + 2));
-        const double ez = -((double)gz * ih2 + ldx<COH>(near + 4 * gi + 3));
-        const int64_t o = perm[gi];
-        if (phi_out) phi_out[o] = (O)ph;
-        if (force_out) {
-            const double s = field ? 1.0 : a.w;
-            force_out[3 * o] = (O)(s * ex);
-            force_out[3 * o + 1] = (O)(s * ey);
-            force_out[3 * o + 2] = (O)(s * ez);
-        }
+        T fp, gx, gy, gz;
+        l2p_point<T, false>(p, ux, uy, uz, Ls, nullptr, nullptr, fp, gx, gy, gz);
+        l2p_store<T, O, COH>(f + i, invh, a.w, fp, gx, gy, gz, perm, near, phi_out, force_out, field);
     }
 }
 
