@@ -207,19 +207,19 @@ __global__ void k_unpack_rem(int64_t n, const uint64_t* k, int32_t* tg, int32_t*
     if (i < n) { tg[i] = (int32_t)(k[i] >> 32); sr[i] = (int32_t)(k[i] & 0xffffffffu); }
 }
 
-// Entry (o, i) of a class operator: output coefficient o = (k, l, re|im),
-// input coefficient i = (n, m, re|im) of the scaled multipole; If holds the
-// irregular harmonics of the class offset, rpow[n] = rho^n.
-__device__ __forceinline__ float class_operator_entry(int o, int i, int K2, const int8_t* tk, const int8_t* tm,
-                                                      const float* rpow, const cplx<float>* If) {
-    if (o >= K2 || i >= K2) return 0.f;
-    const int k = tk[o >> 1], l = tm[o >> 1], pa = o & 1;
-    const int n = tk[i >> 1], m = tm[i >> 1], pb = i & 1;
+// The 2 x 2 real block of a class operator for output complex coefficient
+// (k, l) and input (n, m): v[pa][pb], pa / pb = re|im of output / input;
+// If holds the irregular harmonics of the class offset, rpow[n] = rho^n.
+__device__ __forceinline__ void class_operator_block(int k, int l, int n, int m, const float* rpow,
+                                                     const cplx<float>* If, float (&v)[2][2]) {
     const float s = (k & 1) ? -rpow[n] : rpow[n];
     const cplx<float>* Ij = If + tri(n + k, 0);
     if (m == 0) {
         const cplx<float> x = Ij[l];
-        return pb ? 0.f : (pa ? -s * x.im : s * x.re);
+        v[0][0] = s * x.re;
+        v[1][0] = -s * x.im;
+        v[0][1] = v[1][1] = 0.f;
+        return;
     }
     const cplx<float> xa = Ij[m + l];
     const float Ar = xa.re, Ai = -xa.im;
@@ -235,10 +235,10 @@ __device__ __forceinline__ float class_operator_entry(int o, int i, int K2, cons
         Br = sg * xb.re;
         Bi = sg * xb.im;
     }
-    if (!pa && !pb) return s * (Ar + Br);
-    if (!pa && pb) return s * (Bi - Ai);
-    if (pa && !pb) return s * (Ai + Bi);
-    return s * (Ar - Br);
+    v[0][0] = s * (Ar + Br);
+    v[0][1] = s * (Bi - Ai);
+    v[1][0] = s * (Ai + Bi);
+    v[1][1] = s * (Ar - Br);
 }
 
 // two FP32 values split into bf16 hi and lo parts, packed in pairs
@@ -252,8 +252,9 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
 
 // Operator of one class, split into bf16 hi/lo, K-major core-matrix layout:
 // rows = output coefficients (k, l, re|im), columns = input (n, m, re|im).
-// Each thread writes whole 16-byte core-matrix rows (8 columns of one row),
-// consecutive threads consecutive rows in memory, for hi and for lo.
+// A thread takes the two rows of one output complex coefficient against four
+// input complex coefficients: two 16-byte core-matrix rows, adjacent in
+// memory, for hi and for lo (consecutive threads, consecutive rows).
 __global__ void k_class_operators(int p, int Kp, const uint64_t* __restrict__ ukeys,
                                   __nv_bfloat16* __restrict__ ops) {
     // harmonics in FP64 (one column per thread), entries assembled in FP32
@@ -279,20 +280,33 @@ __global__ void k_class_operators(int p, int Kp, const uint64_t* __restrict__ uk
     __syncthreads();
     for (int e = threadIdx.x; e < ntri(2 * p); e += blockDim.x) If[e] = cmk<float>((float)I[e].re, (float)I[e].im);
     __syncthreads();
-    const int K2 = 2 * ntri(p), kg = Kp >> 3, nchunk = Kp * kg;
+    const int K = ntri(p), kg = Kp >> 3, nchunk = Kp * kg;
     uint4* hi = reinterpret_cast<uint4*>(ops + (size_t)c * 2 * Kp * Kp);
     uint4* lo = hi + nchunk;
-    for (int q = threadIdx.x; q < nchunk; q += blockDim.x) {
-        // 16-byte chunk q = (core (row group, column group), row within the core)
-        const int core = q >> 3;
-        const int o = (core / kg) * 8 + (q & 7), i0 = (core % kg) * 8;
-        uint32_t h[4], l[4];
+    for (int u = threadIdx.x; u < nchunk / 2; u += blockDim.x) {
+        // 16-byte chunks 2u, 2u + 1 = rows o0, o0 + 1 of one core matrix, columns i0 .. i0 + 7
+        const int core = u >> 2;
+        const int o0 = (core / kg) * 8 + 2 * (u & 3), i0 = (core % kg) * 8;
+        const int ko = o0 >> 1;
+        float v[2][8];   // [re|im of the output][column - i0]
 #pragma unroll
-        for (int u = 0; u < 4; u++)
-            split2(class_operator_entry(o, i0 + 2 * u, K2, tk, tm, rpow, If),
-                   class_operator_entry(o, i0 + 2 * u + 1, K2, tk, tm, rpow, If), h[u], l[u]);
-        hi[q] = make_uint4(h[0], h[1], h[2], h[3]);
-        lo[q] = make_uint4(l[0], l[1], l[2], l[3]);
+        for (int q = 0; q < 4; q++) {
+            const int ki = (i0 >> 1) + q;
+            float b[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+            if (ko < K && ki < K) class_operator_block(tk[ko], tm[ko], tk[ki], tm[ki], rpow, If, b);
+            v[0][2 * q] = b[0][0];
+            v[0][2 * q + 1] = b[0][1];
+            v[1][2 * q] = b[1][0];
+            v[1][2 * q + 1] = b[1][1];
+        }
+#pragma unroll
+        for (int pa = 0; pa < 2; pa++) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int w = 0; w < 4; w++) split2(v[pa][2 * w], v[pa][2 * w + 1], h[w], l[w]);
+            hi[2 * u + pa] = make_uint4(h[0], h[1], h[2], h[3]);
+            lo[2 * u + pa] = make_uint4(l[0], l[1], l[2], l[3]);
+        }
     }
 }
 
