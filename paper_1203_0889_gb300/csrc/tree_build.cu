@@ -785,6 +785,52 @@ __global__ void k_csr_start(const uint64_t* key, int64_t np, int ncell, int B, i
     start[c] = a;
 }
 
+// P2P pairs join two leaves, and leaves in cell order are leaves in rank
+// order, so the list sorts on (target rank, source rank): 2 bits_for(nleaf)
+// bits, 32-bit keys while they fit, instead of two cell indices.
+__global__ void k_leaf_rank(int nleaf, const int32_t* __restrict__ leaves, int32_t* lrank) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nleaf) lrank[leaves[i]] = i;
+}
+template <typename K>
+__global__ void k_pack_leaf_pairs(const int2* __restrict__ pr, int64_t np, int B, const int32_t* __restrict__ lrank,
+                                  K* key) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < np) key[i] = ((K)(uint32_t)lrank[pr[i].x] << B) | (K)(uint32_t)lrank[pr[i].y];
+}
+// sorted keys back to cells; cnt[e] = particles of the source (for the records)
+template <typename K>
+__global__ void k_unpack_leaf_pairs(const K* __restrict__ key, int64_t np, int B, const int32_t* __restrict__ leaves,
+                                    const int32_t* __restrict__ count, int32_t* src, int32_t* tgt, int64_t* cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const K k = key[i];
+    const int s = leaves[(int)(k & (((K)1 << B) - 1))];
+    src[i] = s;
+    tgt[i] = leaves[(int)(k >> B)];
+    cnt[i] = count[s];
+}
+// start[c] = first entry whose target rank is at least the number of leaves
+// before cell c (cells that are not leaves get empty ranges), c = 0..ncell
+template <typename K>
+__global__ void k_csr_start_leaf(const K* __restrict__ key, int64_t np, int ncell, int nleaf, int B,
+                                 const int32_t* __restrict__ leaves, int64_t* start) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > ncell) return;
+    int a = 0, b = nleaf;
+    while (a < b) {
+        const int mid = (a + b) >> 1;
+        if (leaves[mid] < c) a = mid + 1; else b = mid;
+    }
+    const K lim = (K)(uint32_t)a << B;
+    int64_t lo = 0, hi = np;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (key[mid] < lim) lo = mid + 1; else hi = mid;
+    }
+    start[c] = lo;
+}
+
 // P2P records: source range and where its particles start in the target's
 // concatenated source stream (exclusive prefix of counts within the target)
 __global__ void k_p2p_counts(int64_t np, const int32_t* src, const int32_t* count, int64_t* cnt) {
@@ -849,6 +895,82 @@ static int finish_list(fmm_tree* t, int2* pairs, int64_t np, int64_t** start, in
     return FMM_OK;
 }
 
+
+// The P2P list as CSR by target with its records (source range, offset of its
+// particles in the target's source stream).  *tgt receives the target of each
+// entry (freed by the caller).
+template <typename K>
+static int p2p_list_sorted(fmm_tree* t, int2* pairs, int64_t np, int B, int32_t* tgt, int64_t* cnt,
+                           cudaStream_t st) {
+    TreeDev& d = t->d;
+    int rc;
+    K *k0 = nullptr, *k1 = nullptr;
+    int32_t* lrank = nullptr;
+    char* tmp = nullptr;
+    if ((rc = dev_alloc((char**)&k0, sizeof(K) * (size_t)np, nullptr, st))) return rc;
+    if ((rc = dev_alloc((char**)&k1, sizeof(K) * (size_t)np, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&lrank, (size_t)t->ncell, nullptr, st))) return rc;
+    k_leaf_rank<<<nblk(t->nleaf, 256), 256, 0, st>>>(t->nleaf, d.leaves, lrank);
+    k_pack_leaf_pairs<K><<<nblk(np, 256), 256, 0, st>>>(pairs, np, B, lrank, k0);
+    size_t tb = 0;
+    cub::DeviceRadixSort::SortKeys(nullptr, tb, k0, k1, np, 0, 2 * B, st);
+    if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
+    FMM_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tb, k0, k1, np, 0, 2 * B, st));
+    k_unpack_leaf_pairs<K><<<nblk(np, 256), 256, 0, st>>>(k1, np, B, d.leaves, d.count, d.p2p_src, tgt, cnt);
+    k_csr_start_leaf<K><<<nblk(t->ncell + 1, 256), 256, 0, st>>>(k1, np, t->ncell, t->nleaf, B, d.leaves,
+                                                                 d.p2p_start);
+    count_launch(t, 5);
+    dev_free(tmp, st);
+    dev_free(k0, st);
+    dev_free(k1, st);
+    dev_free(lrank, st);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+static int finish_p2p_list(fmm_tree* t, int2* pairs, int64_t np, cudaStream_t st) {
+    TreeDev& d = t->d;
+    int rc;
+    int32_t* tgt = nullptr;
+    int64_t *cnt = nullptr, *gcum = nullptr;
+    char* tmp = nullptr;
+    if (t->prm.flags & FMM_BUILD_FALLBACKS) {
+        // the generic list (cell-index keys), counts by a separate pass
+        if ((rc = finish_list(t, pairs, np, &d.p2p_start, &d.p2p_src, &tgt, st))) return rc;
+        if ((rc = dev_alloc(&cnt, (size_t)np, nullptr, st))) return rc;
+        if (np) { k_p2p_counts<<<nblk(np, 256), 256, 0, st>>>(np, d.p2p_src, d.count, cnt); count_launch(t); }
+    } else {
+        if ((rc = dev_alloc(&d.p2p_src, (size_t)np, t, st))) return rc;
+        if ((rc = dev_alloc(&d.p2p_start, (size_t)t->ncell + 1, t, st))) return rc;
+        if ((rc = dev_alloc(&tgt, (size_t)np, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&cnt, (size_t)np, nullptr, st))) return rc;
+        const int B = bits_for(t->nleaf);
+        if (np == 0) {
+            FMM_CUDA_TRY(cudaMemsetAsync(d.p2p_start, 0, sizeof(int64_t) * ((size_t)t->ncell + 1), st));
+        } else if (2 * B <= 32) {
+            if ((rc = p2p_list_sorted<uint32_t>(t, pairs, np, B, tgt, cnt, st))) return rc;
+        } else {
+            if ((rc = p2p_list_sorted<uint64_t>(t, pairs, np, B, tgt, cnt, st))) return rc;
+        }
+    }
+    if ((rc = dev_alloc(&gcum, (size_t)np, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&d.p2p_rec, (size_t)np, t, st))) return rc;
+    if (np) {
+        size_t sb = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, sb, cnt, gcum, np, st);
+        if ((rc = dev_alloc(&tmp, sb, nullptr, st))) return rc;
+        FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, cnt, gcum, np, st));
+        dev_free(tmp, st);
+        k_p2p_records<<<nblk(np, 256), 256, 0, st>>>(np, d.p2p_src, tgt, d.p2p_start, d.first, d.count, gcum,
+                                                        d.p2p_rec);
+        count_launch(t, 2);
+    }
+    dev_free(cnt, st);
+    dev_free(gcum, st);
+    dev_free(tgt, st);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
 
 // a2 in one pass: leaf level of every particle, one scan of the per-level
 // counts, then every cell and its links (the level-by-level octree serves
@@ -1248,26 +1370,7 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
         FMM_CUDA_TRY(cudaStreamWaitEvent(sl, t->ev_fork, 0));
     }
     stage_begin(t, FMM_STAGE_P2P_LIST, sl);
-    int32_t* p2p_tgt = nullptr;
-    if ((rc = finish_list(t, p2p, npp, &d.p2p_start, &d.p2p_src, &p2p_tgt, sl))) return rc;
-    {
-        int64_t *cnt = nullptr, *gcum = nullptr;
-        if ((rc = dev_alloc(&cnt, (size_t)npp, nullptr, sl))) return rc;
-        if ((rc = dev_alloc(&gcum, (size_t)npp, nullptr, sl))) return rc;
-        if ((rc = dev_alloc(&d.p2p_rec, (size_t)npp, t, sl))) return rc;
-        if (npp) {
-            k_p2p_counts<<<nblk(npp, 256), 256, 0, sl>>>(npp, d.p2p_src, d.count, cnt);
-            size_t sb = 0;
-            cub::DeviceScan::ExclusiveSum(nullptr, sb, cnt, gcum, npp, sl);
-            if ((rc = dev_alloc(&tmp, sb, nullptr, sl))) return rc;
-            FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, cnt, gcum, npp, sl));
-            dev_free(tmp, sl);
-            k_p2p_records<<<nblk(npp, 256), 256, 0, sl>>>(npp, d.p2p_src, p2p_tgt, d.p2p_start, d.first, d.count,
-                                                            gcum, d.p2p_rec);
-            count_launch(t, 3);
-        }
-        dev_free(cnt, sl); dev_free(gcum, sl); dev_free(p2p_tgt, sl);
-    }
+    if ((rc = finish_p2p_list(t, p2p, npp, sl))) return rc;
     dev_free(p2p, sl);
     stage_end(t, FMM_STAGE_P2P_LIST, sl);
     if (sl != st) FMM_CUDA_TRY(cudaEventRecord(t->ev_join_hi, sl));
