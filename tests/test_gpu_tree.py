@@ -17,6 +17,15 @@ def test_tree_bit_exact(name, n, leaf, theta):
     assert_tree_equal(t.export(), O.build_tree(wl.pos, leaf, theta))
 
 
+@pytest.mark.parametrize("name,n,leaf", [("uniform", 40000, 4096), ("clustered", 30000, 1000), ("plummer", 25000, 257)])
+def test_tree_large_leaves(name, n, leaf):
+    """Leaf sizes far above the usual: the one-pass octree's window of
+    leaf + 1 particles spans many blocks of the level pass."""
+    wl = W.make_workload(name, n=n)
+    t = gpu_tree(wl.pos, p=2, leaf_size=leaf, theta=0.5)
+    assert_tree_equal(t.export(), O.build_tree(wl.pos, leaf, 0.5))
+
+
 def test_tree_fp32_positions():
     torch, _ = torch_dev()
     wl = W.make_workload("plummer", n=10000)
