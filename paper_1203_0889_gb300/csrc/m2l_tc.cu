@@ -748,13 +748,16 @@ struct TcShape {
 // Stages and operator slots that fit `cap` bytes of shared memory, and TMEM
 // accumulators that fit the 512 columns of one SM (one block per SM).  With
 // `bulk`, each epilogue warp also gets a 32-row staging tile for the bulk
-// reductions, if two stages and one operator slot still fit.
-static TcShape tc_shape(int Kp, size_t cap, bool bulk) {
+// reductions, if two stages and one operator slot still fit.  The tile's row
+// stride is 8 mod 16 floats, so that the 8-byte stores of a half-warp (four
+// rows of eight words) fall on distinct banks, unless that padding costs a
+// pipeline stage (then 4 mod 16).
+static TcShape tc_shape_stride(int Kp, size_t cap, int stride) {
     const size_t stage = (size_t)2 * TC_ROWS * Kp * 2 + TC_ROWS * sizeof(int), slot = (size_t)2 * Kp * Kp * 2;
     TcShape sh{};
     size_t stg = 0;
-    if (bulk) {
-        sh.stg_stride = 16 * ((Kp / 16 + 1) / 2) + 4;
+    if (stride > 0) {
+        sh.stg_stride = stride;
         stg = (size_t)TC_EPI_WARPS * 32 * sh.stg_stride * 4;
         if (stg + 2 * stage + slot > cap) { sh.stg_stride = 0; stg = 0; }
     }
@@ -763,6 +766,12 @@ static TcShape tc_shape(int Kp, size_t cap, bool bulk) {
     sh.nacc = std::min(TC_MAX_ACC, TC_TMEM_COLS / Kp);
     sh.smem = sh.stages * stage + sh.nslots * slot + stg;
     return sh;
+}
+static TcShape tc_shape(int Kp, size_t cap, bool bulk) {
+    if (!bulk) return tc_shape_stride(Kp, cap, 0);
+    const int w = 16 * ((Kp / 16 + 1) / 2);   // half a row (the columns of one epilogue warp)
+    const TcShape a = tc_shape_stride(Kp, cap, w + 8), b = tc_shape_stride(Kp, cap, w + 4);
+    return (a.stages >= b.stages && a.nslots >= b.nslots && a.stg_stride > 0) ? a : b;
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
