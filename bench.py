@@ -170,7 +170,7 @@ FP64_TFLOPS_MEASURED = 1.256
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands; None once the kernel has changed since.
 TRAFFIC = {"k_p2p": 89276160 + 15623680,        # bench workload, one launch, dram__bytes_read + write
-           "k_m2l_tc": 535333376 + 10936832}
+           "k_m2l_tc": 530205440 + 14841344}
 
 
 def kernel_rooflines(stage_ms: dict, ex, prec: int, n_sm: int, info=None):
