@@ -60,10 +60,10 @@ extern "C" {
                                the caller's stream (by default P2P runs on a second stream and the
                                far-field chain on a high-priority one, joined before L2P) */
 #define FMM_BUILD_FALLBACKS 16 /* diagnostic: build with the alternative paths (the octree level by
-                                  level with a host round trip per level; the paths otherwise taken
-                                  only when a buffer or table overflows: round-by-round traversal,
-                                  tensor-core classes grouped by sorting their keys); same tree and
-                                  lists */
+                                  level with a host round trip per level, the P2P list sorted on
+                                  cell indices; the paths otherwise taken only when a buffer or
+                                  table overflows: round-by-round traversal, tensor-core classes
+                                  grouped by sorting their keys); same tree and lists */
 
 /* stage indices for fmm_stage_times / fmm_stage_name */
 #define FMM_STAGE_KEYS      0   /* root cube, Morton keys, key sort */
