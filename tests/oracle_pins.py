@@ -412,3 +412,71 @@ def pin_fmm_gradient_fixed_tree():
             fd = (loss(xp) - loss(xm)) / (2 * h)
             assert abs(fd - dx[j, d]) <= 1e-5 * np.abs(dx).max()
     T.pos = pos
+
+
+# ---------------------------------------------------------------- hand-worked tree cases
+
+def pin_root_cube_centred():
+    """Root cube of two particles with unequal extents, worked by hand.
+
+    Points (0, 0, 0) and (4, 2, 1): extents 4, 2, 1, so side = 4 (the longest)
+    and the cube is centred on the bounding box in every axis: origin =
+    (lo + hi)/2 - side/2 = (0, -1, -1.5).  With u = side / 2^21 = 2^-19:
+      (0, 0, 0): k = (0, 1 / 2^-19, 1.5 / 2^-19) = (0, 2^19, 2^19 + 2^18);
+      (4, 2, 1): k = (2^21 clamped to 2^21 - 1, 3 * 2^19, 2.5 * 2^19)
+                   = (2^21 - 1, 2^20 + 2^19, 2^20 + 2^18).
+    Morton key bits: x bit b at 3b, y bit b at 3b + 1, z bit b at 3b + 2, so
+      key(0,0,0) = 2^(3*19+1) + 2^(3*19+2) + 2^(3*18+2) = 2^58 + 2^59 + 2^56,
+      key(4,2,1) = sum_b 2^(3b) (b = 0..20) + 2^61 + 2^58 + 2^62 + 2^56.
+    A cube anchored at the low corner (origin = lo) or sides per axis would
+    give other origins and keys."""
+    T = O.build_tree(np.array([[0.0, 0.0, 0.0], [4.0, 2.0, 1.0]]), 1, 0.5)
+    assert T.side == 4.0
+    assert np.array_equal(T.origin, np.array([0.0, -1.0, -1.5]))
+    k0 = (1 << 58) + (1 << 59) + (1 << 56)
+    k1 = sum(1 << (3 * b) for b in range(21)) + (1 << 61) + (1 << 58) + (1 << 62) + (1 << 56)
+    assert sorted(int(k) for k in T.keys) == sorted([k0, k1])
+    # octants at level 1 (key bits 62, 61, 60): 0 for the first point, 7 for the second
+    assert T.ncell == 3 and np.array_equal(T.level, [0, 1, 1])
+    assert np.array_equal(T.cell_key, np.array([0, 0, 7], np.uint64))
+
+
+def pin_traversal_tie_break():
+    """Lists of four particles, worked by hand (leaf size 1, theta = 0.5).
+
+    p0 = (0,0,0), p1 = (3/8)(1,1,1), p2 = (5/8)(1,1,1), p3 = (1,1,1): the root
+    cube is [0,1]^3; cells in (level, key) order are the root 0, its octants
+    c0 = [0,1/2]^3 (cell 1) and c7 = [1/2,1]^3 (cell 2), and the level-2
+    leaves x000 = [0,1/4]^3 (3, holds p0), x111 = [1/4,1/2]^3 (4, p1),
+    y000 = [1/2,3/4]^3 (5, p2), y111 = [3/4,1]^3 (6, p3).  Accept iff
+    (s_i + s_j)^2 < theta^2 |2 (c_i - c_j)|^2 (sides s, in root units).
+    (root, root) and (c0, c7) are rejected; cells of equal size split the
+    target, so (c0, c7) becomes (x000, c7) -- accepted: 0.75^2 < 0.25 * 3 *
+    1.25^2 -- and (x111, c7), rejected (0.25 * 3 * 0.75^2 < 0.75^2) with a leaf
+    target, so the source splits: (x111, y111) is accepted (0.5^2 < 0.25 * 3)
+    and (x111, y000) is P2P.  Symmetrically (y111, c0) is accepted and
+    (y000, x000) too.  Splitting the source on equal size would give (c0, y111)
+    and (c7, x000) instead."""
+    pos = np.array([[0.0] * 3, [0.375] * 3, [0.625] * 3, [1.0] * 3])
+    T = O.build_tree(pos, 1, 0.5)
+    assert T.ncell == 7
+    assert np.array_equal(T.level, [0, 1, 1, 2, 2, 2, 2])
+    assert np.array_equal(T.count, [4, 2, 2, 1, 1, 1, 1])
+    assert np.array_equal(T.m2l, np.array([[3, 2], [4, 6], [5, 3], [6, 1]], np.int32))
+    assert np.array_equal(T.p2p, np.array([[3, 3], [3, 4], [4, 3], [4, 4], [4, 5], [5, 4], [5, 5], [5, 6],
+                                           [6, 5], [6, 6]], np.int32))
+
+
+def pin_split_rule_invariants(pos, leaf_size=8, theta=0.5):
+    """Consequences of the split rule (split the larger cell; the target on
+    equal size or when the source is a leaf): a pair whose source is finer than
+    its target has a leaf target, and a pair whose target is more than one
+    level finer than its source has a leaf source."""
+    T = O.build_tree(pos, leaf_size, theta)
+    leaf = T.is_leaf
+    for lst in (T.m2l, T.p2p):
+        if len(lst) == 0:
+            continue
+        lt, ls = T.level[lst[:, 0]], T.level[lst[:, 1]]
+        assert np.all(leaf[lst[ls > lt, 0]])
+        assert np.all(leaf[lst[lt > ls + 1, 1]])

@@ -48,14 +48,21 @@ MUTANTS = {
     "p2p_target_charge": ("f += e->sq[j] / r;", "f += e->sq[i] / r;"),
     "p2p_skips_leaf_self": ("if (j == i) continue;\n                double dx = e->spos",
                             "if (s == c) continue;\n                double dx = e->spos"),
+    "split_source_on_tie": ("if (lj || (!li && t->level[ci] <= t->level[cj])) {",
+                            "if (lj || (!li && t->level[ci] < t->level[cj])) {"),
+    "split_smaller_cell": ("if (lj || (!li && t->level[ci] <= t->level[cj])) {",
+                           "if (lj || (!li && t->level[ci] >= t->level[cj])) {"),
+    "root_cube_at_low_corner": ("origin[d] = (lo[d] + hi[d]) * 0.5 - s * 0.5;", "origin[d] = lo[d];"),
+    "root_cube_high_anchor": ("origin[d] = (lo[d] + hi[d]) * 0.5 - s * 0.5;", "origin[d] = hi[d] - s;"),
 }
 
 PINS_CHEAP_FIRST = [
-    P.pin_direct_two_charges, P.pin_direct_cube_corners, P.pin_multipole_on_axis,
+    P.pin_root_cube_centred, P.pin_traversal_tie_break, P.pin_direct_two_charges, P.pin_direct_cube_corners, P.pin_multipole_on_axis,
     P.pin_multipole_single_charge, P.pin_m2m_exact, P.pin_l2l_exact, P.pin_m2l_order_zero,
     P.pin_m2l_single_charge, P.pin_l2p_gradient_fd, P.pin_direct_coincident_and_third_law,
     lambda: P.pin_tree_invariants(W.make_workload("plummer", n=1500).pos, 16, 0.5),
     lambda: P.pin_lists_cover_every_pair_once(W.make_workload("uniform", n=1000).pos, 16, 0.5),
+    lambda: P.pin_split_rule_invariants(W.make_workload("plummer", n=2000).pos, 8, 0.5),
     P.pin_fmm_equals_direct_without_far_field, P.pin_fmm_high_order_matches_direct,
     P.pin_fmm_error_decays_with_p,
 ]

@@ -14,6 +14,7 @@ from tests import oracle_pins as P
     P.pin_scaling_invariance, P.pin_fmm_equals_direct_without_far_field,
     P.pin_fmm_error_decays_with_p, P.pin_fmm_high_order_matches_direct, P.pin_fmm_net_force,
     P.pin_fmm_sampled_matches_full, P.pin_direct_gradient_formulas, P.pin_fmm_gradient_fixed_tree,
+    P.pin_root_cube_centred, P.pin_traversal_tie_break,
 ], ids=lambda f: f.__name__)
 def test_pin(pin):
     pin()
@@ -73,3 +74,9 @@ def test_threads_do_not_change_results():
     f1, g1 = T.evaluate(6, wl.q, nthreads=1)
     f4, g4 = T.evaluate(6, wl.q, nthreads=4)
     assert np.array_equal(f1, f4) and np.array_equal(g1, g4)
+
+
+@pytest.mark.parametrize("name", ["uniform", "plummer", "clustered"])
+@pytest.mark.parametrize("leaf,theta", [(8, 0.5), (1, 0.4), (32, 0.7)])
+def test_split_rule_invariants(name, leaf, theta):
+    P.pin_split_rule_invariants(W.make_workload(name, n=2000).pos, leaf, theta)
