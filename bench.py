@@ -3,16 +3,20 @@
 
 A step is one pass of the whole hot path on one synthetic system: the device
 tree build (root cube, Morton keys, octree, dual traversal, lists) followed by
-one evaluation (P2M, M2M, M2L, L2L, L2P, P2P).  The workload is the irregular
-configuration: N = 1,048,576 particles from a Plummer sphere (scale radius 1,
-truncated at r = 50), charges 1/N, order p = 8, leaf size 64, theta = 0.4.
+one evaluation (P2M, M2M, M2L, L2L, L2P, P2P).  The default workload is the
+mixed-precision configuration: N = 4,194,304 particles in 64 isotropic Gaussian
+clusters (sigma = 0.01, centres uniform in the unit cube), charges U[-1, 1],
+order p = 10, leaf size 64, theta = 0.5.  `--workload plummer` runs the
+irregular configuration instead (N = 1,048,576 from a Plummer sphere of scale
+radius 1 truncated at r = 50, charges 1/N, p = 8, leaf 64, theta = 0.4).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 The headline is the mixed form (tensor-core M2L from split bf16 products,
 FP32 elsewhere), whose error against the plain FP64 GPU path is measured in
 the same run and printed beside it; the FP64, FP32-P2P/FP64-expansion and
-FP32 forms are timed on the same system as context ("variants").
+FP32 forms are timed on the same system as context ("variants"), and the
+mixed form of the Plummer configuration with its own error.
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own system
 (replicas: the single-system path has no exchange step) and the value is the
@@ -37,9 +41,30 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "FMM particles/sec at rel-L2 err <=1e-4 vs plain FP64 GPU path; % roofline"
-WORKLOAD = "plummer"
-N_DEFAULT = 1 << 20
-P, LEAF, THETA = 8, 64, 0.4
+# single-system workloads: description, default N, p, leaf size, theta
+SYSTEMS = {
+    "clustered": ("clustered: 64 Gaussian clusters sigma=0.01, centres U[0,1)^3, q~U[-1,1]", 1 << 22, 10, 64, 0.5),
+    "plummer": ("plummer a=1 rmax=50, q=1/N", 1 << 20, 8, 64, 0.4),
+}
+WORKLOAD = "clustered"
+DESC, N_DEFAULT, P, LEAF, THETA = SYSTEMS[WORKLOAD]
+
+
+def select_workload(name: str) -> None:
+    """Make `name` the single-system workload of this run (sets the module's
+    WORKLOAD, DESC, N_DEFAULT, P, LEAF, THETA)."""
+    global WORKLOAD, DESC, N_DEFAULT, P, LEAF, THETA
+    WORKLOAD = name
+    DESC, N_DEFAULT, P, LEAF, THETA = SYSTEMS[name]
+
+
+def workload_line(n: int) -> str:
+    return f"{DESC}, N={n}, p={P}, leaf={LEAF}, theta={THETA}"
+
+
+def workload_seed(rank: int = 0) -> int:
+    import workloads as W
+    return 12030889 * 10 + W.WORKLOADS[WORKLOAD][0] + 1000 * rank
 L2_FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2
 P2P_FLOPS_PER_PAIR = 20             # convention for the near-field direct sum
 PREC_NAMES = {0: "fp64", 1: "fp32_p2p", 2: "fp32", 3: "mixed_tc"}
@@ -52,16 +77,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--n", type=int, default=None, help="particles (default: the workload's N)")
     ap.add_argument("--precision", type=int, default=3,
                     help="0 fp64, 1 fp32 P2P + fp64 expansions, 2 fp32, 3 mixed: bf16x3 tensor-core M2L + fp32")
     ap.add_argument("--no-variants", action="store_true", help="skip the other precisions' context timings")
     ap.add_argument("--staged", action="store_true", help="one kernel per stage instead of the task queue")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-n", type=int, default=1 << 17)
-    ap.add_argument("--workload", default="plummer", choices=["plummer", "batched", "table", "granularity"],
-                    help="plummer: one 1M-particle system (default); batched: 512 systems of 1024..65536; "
+    ap.add_argument("--cpu-sample-n", type=int, default=1 << 21,
+                    help="particles of the oracle's timed sample (about 10-20 s on 16 host cores)")
+    ap.add_argument("--workload", default="clustered",
+                    choices=["clustered", "plummer", "batched", "table", "granularity"],
+                    help="clustered: one 4M-particle clustered system at p=10 (default); plummer: one 1M-particle "
+                         "Plummer system at p=8; batched: 512 systems of 1024..65536; "
                          "table: every configuration against the oracle (context, several minutes); "
                          "granularity: task size against N on the task queue")
     return ap.parse_args()
@@ -169,8 +197,13 @@ FP64_TFLOPS_MEASURED = 1.256
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands; None once the kernel has changed since.
-TRAFFIC = {"k_p2p": 89276160 + 15623680,        # bench workload, one launch, dram__bytes_read + write
-           "k_m2l_tc": 530205440 + 14841344}
+TRAFFIC = {"plummer": {"k_p2p": 89276160 + 15623680,       # one launch, dram__bytes_read + write
+                       "k_m2l_tc": 530205440 + 14841344},
+           "clustered": {"k_p2p": None, "k_m2l_tc": None}}
+
+
+def traffic(kernel: str):
+    return TRAFFIC.get(WORKLOAD, {}).get(kernel)
 
 
 def kernel_rooflines(stage_ms: dict, ex, prec: int, n_sm: int, info=None):
@@ -201,18 +234,21 @@ def kernel_rooflines(stage_ms: dict, ex, prec: int, n_sm: int, info=None):
         flops = pairs * float(P2P_FLOPS_PER_PAIR)
         peak = FP64_TFLOPS_MEASURED if prec == 0 else fp32_peak
         out.append({"kernel": "k_p2p", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
-                    "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": TRAFFIC["k_p2p"],
+                    "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": traffic("k_p2p"),
                     "ms": stage_ms["p2p"],
                     "algorithmic": f"{pairs} pair interactions x {P2P_FLOPS_PER_PAIR} flops",
                     "peak_source": fp64_src if prec == 0 else fp32_src})
     if prec == 3 and info is not None and info.tc_pairs > 0 and "m2l_tc" in stage_ms:
         t = stage_ms["m2l_tc"] * 1e-3
-        kp = ((P + 1) * (P + 2) + 15) // 16 * 16
+        # issued: per 128-pair item, three bf16 products of the 128-row operator
+        # (outputs padded to 128) by 128 columns (pairs) over KI inputs, KI = K
+        # rounded up to whole 64-coefficient swizzle atoms
+        ki = (K + 63) // 64 * 64
         useful = info.tc_pairs * 2.0 * K * K
-        issued = info.tc_items * 128 * 2.0 * kp * kp * 3
+        issued = info.tc_items * 3 * 2.0 * 128 * 128 * ki
         peak = float(pk["bf16_tflops"])
         out.append({"kernel": "k_m2l_tc", "bound": "tensor", "achieved": useful / t / 1e12, "peak": peak,
-                    "unit": "TFLOP/s", "frac": useful / t / 1e12 / peak, "traffic": TRAFFIC["k_m2l_tc"],
+                    "unit": "TFLOP/s", "frac": useful / t / 1e12 / peak, "traffic": traffic("k_m2l_tc"),
                     "ms": stage_ms["m2l_tc"],
                     "algorithmic": f"{info.tc_pairs} M2L pairs x 2K^2 flops, K=(p+1)^2={K}",
                     "issued_frac": issued / t / 1e12 / peak,
@@ -256,6 +292,54 @@ def pass_rooflines(stage_ms: dict, ex, prec: int, info, n: int):
     return out
 
 
+def fp64_roofline_ratio(value: float, n: int, ex, v64):
+    """The headline against the plain FP64 GPU path as it would run at its
+    FP64-pipe roofline: the FP64 evaluation's algorithmic flops (M2L pairs x 2K^2
+    + P2P pairs x 20) at the measured FP64 FMA rate, the tree build free.  A
+    ratio against an ideal denominator (the measured one is vs_fp64_gpu_path)."""
+    if not v64:
+        return None
+    K = (P + 1) ** 2
+    flops = len(ex["m2l"]) * 2.0 * K * K + p2p_pairs(ex) * float(P2P_FLOPS_PER_PAIR)
+    ideal_s = flops / (FP64_TFLOPS_MEASURED * 1e12)
+    return {"ratio": value / (n / ideal_s), "fp64_ideal_ms": ideal_s * 1e3,
+            "fp64_measured_ms": v64["ms_per_step"],
+            "fp64_frac_of_roofline": ideal_s * 1e3 / v64["ms_per_step"]}
+
+
+def plummer_variant(fmm, torch, dev, flush, stream, steps: int = 3):
+    """The mixed form on the Plummer configuration (1M particles, p = 8, leaf 64,
+    theta = 0.4): particles/s of build + evaluation and its error against the
+    plain FP64 GPU path on the same system."""
+    import workloads as W
+    _, n0, p, leaf, theta = SYSTEMS["plummer"]
+    wl = W.make_workload("plummer")
+    pos = torch.tensor(wl.pos, dtype=torch.float64, device=dev)
+    q = torch.tensor(wl.q, dtype=torch.float64, device=dev)
+    t64 = fmm.build_tree(pos, p=p, leaf_size=leaf, theta=theta, precision=fmm.PREC_FP64)
+    phi64, f64 = t64.evaluate(q)
+    t64.close()
+    phi = torch.empty_like(phi64)
+    force = torch.empty_like(f64)
+    ts = []
+    for k in range(steps + 2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t = fmm.build_tree(pos, p=p, leaf_size=leaf, theta=theta, precision=fmm.PREC_MIXED_TC)
+        t.evaluate(q, phi=phi, force=force)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t.close()
+        if k >= 2:
+            ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    return {"workload": f"{SYSTEMS['plummer'][0]}, N={wl.n}, p={p}, leaf={leaf}, theta={theta}",
+            "value": wl.n / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "dtype": PREC_DTYPE[3],
+            "rel_l2_vs_fp64_gpu": {"phi": float(((phi - phi64).norm() / phi64.norm()).item()),
+                                   "force": float(((force - f64).norm() / f64.norm()).item())}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -269,7 +353,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream()
-    wl = W.make_workload(WORKLOAD, n=args.n, seed=12030889 * 10 + 2 + 1000 * rank)
+    wl = W.make_workload(WORKLOAD, n=args.n, seed=workload_seed(rank))
     n = wl.n
     pos = torch.tensor(wl.pos, dtype=torch.float64, device=dev)
     q = torch.tensor(wl.q, dtype=torch.float64, device=dev)
@@ -377,12 +461,14 @@ def run_ours(args):
             if vp == args.precision:
                 continue
             vsteps = 2 if vp in (0, 1) else 3
-            step_v = lambda: fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=vp)  # noqa: E731
+            step_v = lambda: fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=vp,  # noqa: E731
+                                            flags=fmm.TIMING)
             tv = step_v()
             pv, fv = tv.evaluate(q)
             tv.close()
             torch.cuda.synchronize()
             ms = 0.0
+            vstage = {}
             for _ in range(vsteps):
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -392,12 +478,20 @@ def run_ours(args):
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ms += e0.elapsed_time(e1) / vsteps
+                for name, sms in tv.stage_times().items():
+                    vstage[name] = vstage.get(name, 0.0) + sms / vsteps
+                vinfo = tv.info()
                 tv.close()
+            vroofs = kernel_rooflines(vstage, ex, vp, props.multi_processor_count, vinfo)
             variants[PREC_NAMES[vp]] = {
                 "value": n / (ms * 1e-3), "ms_per_step": ms, "steps": vsteps, "dtype": PREC_DTYPE[vp],
                 "rel_l2_vs_fp64_gpu": {"phi": float(((pv - phi64).norm() / phi64.norm()).item()),
-                                       "force": float(((fv - f64).norm() / f64.norm()).item())}}
+                                       "force": float(((fv - f64).norm() / f64.norm()).item())},
+                "roofline": max(vroofs, key=lambda r: r["ms"]) if vroofs else None,
+                "stage_ms": {k: round(v, 4) for k, v in vstage.items()}}
             del pv, fv
+        if WORKLOAD != "plummer":
+            variants["plummer_mixed_tc"] = plummer_variant(fmm, torch, dev, flush, stream)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -442,7 +536,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": PREC_DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": f"plummer N={n} a=1 rmax=50, q=1/N, p={P}, leaf={LEAF}, theta={THETA}",
+            "config": {"workload": workload_line(n),
                        "step": "fmm_build_tree + fmm_evaluate (potentials and forces)",
                        "precision": PREC_NAMES[args.precision], "l2": "flushed between steps (512 MB write)",
                        "execution": "staged kernels" if (args.staged or args.precision == 3) else "persistent task queue",
@@ -460,6 +554,7 @@ def run_ours(args):
             "build_ms_per_step": build_ms, "evaluate_ms_per_step": eval_ms,
             "evaluate_particles_per_s": n / (eval_ms * 1e-3),
             "vs_fp64_gpu_path": (value / variants["fp64"]["value"]) if "fp64" in variants else None,
+            "vs_fp64_roofline": fp64_roofline_ratio(value, n, ex, variants.get("fp64")),
             "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(out), flush=True)
@@ -481,7 +576,7 @@ def cpu_baseline(sample_n: int):
     T.evaluate(P, wl.q, nthreads=cores)
     dt = time.perf_counter() - t0
     return {"value": sample_n / dt, "unit": "particles/s", "cores": cores, "kind": "oracle",
-            "sample": f"oracle tree build + FP64 FMM of a Plummer system of N={sample_n} "
+            "sample": f"oracle tree build + FP64 FMM of a {WORKLOAD} system of N={sample_n} "
                       f"(same recipe, p={P}, leaf={LEAF}, theta={THETA}), {dt:.2f} s"}
 
 
@@ -509,14 +604,13 @@ def run_reference(args):
         ts.append(time.perf_counter() - t0)
     tot = sum(ts)
     value = n * args.steps / tot
-    sample = (f"oracle tree build + FP64 FMM per step on a Plummer system of N={n} (same recipe, p={P}, "
+    sample = (f"oracle tree build + FP64 FMM per step on a {WORKLOAD} system of N={n} (same recipe, p={P}, "
               f"leaf={LEAF}, theta={THETA})")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"plummer N={N_DEFAULT} a=1 rmax=50, q=1/N, p={P}, leaf={LEAF}, theta={THETA}",
-                   "sample_n": n},
+        "config": {"workload": workload_line(N_DEFAULT), "sample_n": n},
         "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -797,6 +891,8 @@ def run_granularity(args):
 
 def main():
     args = parse()
+    if args.workload in SYSTEMS:
+        select_workload(args.workload)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":

@@ -263,7 +263,9 @@ void fmm_tree_destroy(fmm_tree* tree);
  * Scratch: a static 1 MiB device array inside the library, held by every GPU
  * that loads it until the process exits; no cudaMalloc/cudaFree is called.
  * The first call on a device looks up the array's device address (once per
- * device) -- make that first call before any stream capture.  Every call
+ * device) -- make that first call before any stream capture.  The address is
+ * kept for the life of the process: after cudaDeviceReset on a device it is
+ * stale, so do not call this entry point on that device again.  Every call
  * shares the one array (the accumulators are cleared at the start of each
  * call), so calls that overlap on the GPU -- on different streams, or from
  * different threads -- race and must be serialised by the caller.

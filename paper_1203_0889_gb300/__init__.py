@@ -147,6 +147,7 @@ class Tree:
         lib = load()
         if not (pos.is_cuda and pos.dim() == 2 and pos.shape[1] == 3):
             raise ValueError("pos must be a CUDA tensor of shape (n, 3)")
+        self._pos_key = _tensor_key(pos)
         pos = pos.contiguous()
         self.params = Params(int(p), int(leaf_size), float(theta), int(precision), int(flags), int(timeout_ns))
         self.n = int(pos.shape[0])
@@ -316,11 +317,17 @@ def version() -> str:
     return load().fmm_version().decode()
 
 
+def _tensor_key(t):
+    """Identity of a tensor's contents: storage address, shape and in-place version."""
+    return (t.data_ptr(), tuple(t.shape), t.dtype, t._version)
+
+
 def _set_positions(self, pos, stream=None):
     """Move the particles without rebuilding the tree (cells and lists stay)."""
     torch = _torch()
     if not (pos.is_cuda and pos.shape == (self.n, 3)):
         raise ValueError("pos must be a CUDA tensor of shape (n, 3)")
+    self._pos_key = _tensor_key(pos)
     pos = pos.contiguous()
     with torch.cuda.device(pos.device):
         _check(load().fmm_tree_set_positions(self._h, C.c_void_p(pos.data_ptr()), _dtype_code(pos),
@@ -354,12 +361,20 @@ def _fmm_function():
         field for the backward).  The backward runs one more FMM pass with the
         upstream gradient as charges (the kernel is symmetric) and returns
         dL/dpos and dL/dq; the tree is held fixed, so positions are treated as
-        moving inside their cells."""
+        moving inside their cells.  ``pos`` must have the tree's shape; when it
+        is not the tensor the tree was built on (another tensor, or the same one
+        changed in place since), the tree takes its values first
+        (``Tree.set_positions``: same cells and lists, particles moved), so phi
+        and the gradients are always those of ``pos``."""
 
         @staticmethod
         def forward(ctx, pos, q, tree):
             if not (tree.params.flags & OUT_FIELD):
                 raise ValueError("FMMFunction needs a tree built with flags=OUT_FIELD")
+            if tuple(pos.shape) != (tree.n, 3) or tuple(q.shape) != (tree.n,):
+                raise ValueError(f"pos must be ({tree.n}, 3) and q ({tree.n},) for this tree")
+            if _tensor_key(pos) != tree._pos_key:
+                tree.set_positions(pos.detach())
             phi, field = tree.evaluate(q)
             ctx.tree = tree
             ctx.save_for_backward(q, field)

@@ -286,6 +286,50 @@ __global__ void __launch_bounds__(128) k_m2l_generic(int p, int t0, int t1, cons
     }
 }
 
+// CUDA-core M2L over chunks of at most M2L_CHUNK list entries of one target
+// (chunks[c] = (target, first entry)), one warp per chunk, results added into
+// L with FP32 atomics (L zeroed beforehand): a target with thousands of
+// entries is spread over many warps.  Used for the pairs the tensor cores do
+// not take in the mixed form, which concentrate on a few coarse targets.
+template <int RMAX>
+__global__ void __launch_bounds__(128) k_m2l_chunks(int p, int64_t nchunk, const int2* __restrict__ chunks,
+                                                    const int64_t* __restrict__ start, const int32_t* __restrict__ src,
+                                                    const double4_32a* __restrict__ centre,
+                                                    const cplx<float>* __restrict__ M, float* __restrict__ L) {
+    extern __shared__ unsigned char smem_raw[];
+    const int K = ntri(p), KI = ntri(2 * p), KS = kstride(p);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    cplx<float>* Ms = reinterpret_cast<cplx<float>*>(smem_raw) + (warp * 2 + half) * (K + KI);
+    cplx<float>* Is = Ms + K;
+    const int64_t c = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
+    if (c >= nchunk) return;
+    const int2 ch = chunks[c];
+    const int t = ch.x;
+    const int64_t s0 = ch.y, s1 = min(start[t + 1], s0 + (int64_t)M2L_CHUNK);
+    int kk[RMAX], ll[RMAX];
+    cplx<float> acc[RMAX];
+    m2l_output_index<RMAX>(p, hl, kk, ll);
+#pragma unroll
+    for (int r = 0; r < RMAX; r++) acc[r] = cmk<float>(0, 0);
+    m2l_range<float, RMAX, false>(p, t, s0, s1, half, 2, hl, src, centre, M, Ms, Is, kk, ll, acc);
+#pragma unroll
+    for (int r = 0; r < RMAX; r++) {
+        acc[r].re += __shfl_xor_sync(0xffffffffu, acc[r].re, 16);
+        acc[r].im += __shfl_xor_sync(0xffffffffu, acc[r].im, 16);
+    }
+    if (half == 0) {
+#pragma unroll
+        for (int r = 0; r < RMAX; r++) {
+            const int j = hl + 16 * r;
+            if (j < K) {
+                const float sg = (kk[r] & 1) ? -1.f : 1.f;
+                atomicAdd(L + 2 * ((int64_t)t * KS + j), sg * acc[r].re);
+                atomicAdd(L + 2 * ((int64_t)t * KS + j) + 1, sg * acc[r].im);
+            }
+        }
+    }
+}
+
 // one block per target leaf (FP32: registers capped for 9 resident blocks per
 // SM, measured 2 % faster than the uncapped 62 registers)
 template <typename T>
@@ -370,7 +414,7 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st) {
     }
     if (t->prm.precision == FMM_PREC_MIXED_TC && t->tc_nitems > 0) {
         char* ms = nullptr;
-        if ((rc = dev_alloc(&ms, (size_t)t->ncell * 2 * tc_kpad(t->prm.p) * 2, t, st))) return rc;
+        if ((rc = dev_alloc(&ms, (size_t)t->ncell * 2 * tc_kin(t->prm.p) * 2, t, st))) return rc;
         d.tc_msplit = ms;
     }
     FMM_CUDA_TRY(cudaGetLastError());
@@ -444,6 +488,27 @@ static int launch_m2l_generic(fmm_tree* t, int p, int t0, int t1, const int64_t*
     }
     M2L_CASE(2) M2L_CASE(4) M2L_CASE(6) M2L_CASE(8) M2L_CASE(12) M2L_CASE(16)
 #undef M2L_CASE
+    fmm_set_error("order too high for the M2L kernel");
+    return FMM_ERR_ARG;
+}
+
+static int launch_m2l_chunks(fmm_tree* t, int p, const TreeDev& d, const cplx<float>* M, float* L, cudaStream_t st) {
+    const int K = ntri(p), KI = ntri(2 * p);
+    const size_t smem = (size_t)4 * 2 * (K + KI) * sizeof(cplx<float>);
+    const int rmax = (K + 15) / 16;
+    const unsigned grid = nblk(t->rem_nchunk, 4);
+    const int32_t* src = d.tc_src + t->tc_npairs;
+#define M2LC_CASE(R)                                                                                       \
+    if (rmax <= R) {                                                                                       \
+        if (smem > 48 * 1024)                                                                              \
+            FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_chunks<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        k_m2l_chunks<R><<<grid, 128, smem, st>>>(p, t->rem_nchunk, d.rem_chunks, d.rem_start, src, d.centre, M, L); \
+        count_launch(t);                                                                                   \
+        FMM_CUDA_TRY(cudaGetLastError());                                                                  \
+        return FMM_OK;                                                                                     \
+    }
+    M2LC_CASE(2) M2LC_CASE(4) M2LC_CASE(6) M2LC_CASE(8) M2LC_CASE(12) M2LC_CASE(16)
+#undef M2LC_CASE
     fmm_set_error("order too high for the M2L kernel");
     return FMM_ERR_ARG;
 }
@@ -547,9 +612,14 @@ static int far_field(fmm_tree* t, cplx<T>* M, cplx<T>* L, const double4_32a* xq6
     stage_begin(t, FMM_STAGE_M2L, st);
     int rc;
     if (d.rem_start) {
-        // class-less pairs on the CUDA cores (this also initialises every L), then
-        // the classes on the tensor cores, accumulated into L
-        rc = launch_m2l_generic<T>(t, p, 0, t->ncell, d.rem_start, d.tc_src + t->tc_npairs, d, M, L, st);
+        // every L from zero, then the pairs the tensor cores do not take on the
+        // CUDA cores in chunks, then the classes on the tensor cores; both add
+        // into L
+        FMM_CUDA_TRY(cudaMemsetAsync(L, 0, sizeof(cplx<T>) * (size_t)t->ncell * kstride(p), st));
+        rc = FMM_OK;
+        if constexpr (sizeof(T) == 4) {
+            if (t->rem_nchunk > 0) rc = launch_m2l_chunks(t, p, d, (const cplx<float>*)M, (float*)L, st);
+        }
         if (rc) return rc;
         rc = m2l_tensor_cores(t, (const float*)M, (float*)L, st);
     } else {

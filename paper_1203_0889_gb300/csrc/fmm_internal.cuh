@@ -12,6 +12,7 @@
 // offset in target-cell units and on the size ratio.  Every value then stays
 // inside FP32 range for any tree depth.
 #pragma once
+#include <cuda.h>            // CUtensorMap (a type only: no driver-API symbol is linked)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,6 +21,7 @@
 #include "fmm.h"
 
 #define FMM_MAX_P 20
+#define M2L_CHUNK 16   // list entries per warp in the chunked CUDA-core M2L
 #define FMM_MAX_LEVEL 21
 
 namespace fmm {
@@ -153,12 +155,14 @@ struct TreeDev {
     int4* p2p_rec = nullptr;      // [np2p] (first, count, particle offset within the target's sources, source)
     // tensor-core M2L (FMM_PREC_MIXED_TC): pairs grouped by translation class
     int4* tc_items = nullptr;     // [tc_nitems] (class, first pair, rows, -)
-    void* tc_ops = nullptr;       // [nclass][hi|lo][Kp x Kp] bf16 operators
+    int32_t* tc_block_first = nullptr;  // [tc_nblocks + 1] item range of each tensor-core block
+    void* tc_harm = nullptr;      // [nclass][ntri(2p)] cplx<float>: irregular harmonics of each class offset
     uint64_t* tc_keys = nullptr;  // [nclass] class keys, in class order
     int32_t* tc_tgt = nullptr;    // [nm2l] targets in class order (class-less pairs last)
     int32_t* tc_src = nullptr;
     int64_t* rem_start = nullptr; // CSR of the class-less pairs by target
-    void* tc_msplit = nullptr;    // [ncell][hi|lo][Kp] bf16 multipoles
+    int2* rem_chunks = nullptr;   // (target, first entry) chunks of at most M2L_CHUNK class-less pairs
+    void* tc_msplit = nullptr;    // [ncell][hi | lo][KI] bf16 multipoles in the real basis (tc_kin)
     Geometry* geom = nullptr;     // [nsys] root cube of each system
     int64_t* sys_off = nullptr;   // [nsys+1] particle offsets of the systems
     float* cu2f = nullptr;        // [ncell] side/2^22 of the cell's system (FP32 P2P offsets)
@@ -215,6 +219,12 @@ struct fmm_tree {
     std::vector<double> h_geom;       // per system: origin x, y, z, side
     int num_sms = 148;
     int64_t tc_nclass = 0, tc_nitems = 0, tc_npairs = 0, tc_nrem = 0;
+    int tc_nblocks = 0;
+    int64_t rem_nchunk = 0;
+    // TMA map of d.tc_msplit (row gathers of the tensor-core M2L), encoded once
+    // the table is allocated
+    CUtensorMap tc_tmap;   // (the type is 64-byte aligned)
+    bool tc_tmap_ok = false;
     int64_t q_n_hi = 0, q_n0 = 0, q_n_tasks = 0;
     fmm::TreeDev d;
 };
@@ -251,7 +261,7 @@ int grad_combine(fmm_tree* t, const void* q, const void* w, const void* eq, cons
                  cudaStream_t st);
 int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st);
 int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st);
-int tc_kpad(int p);
+int tc_kin(int p);
 bool queue_supported(const fmm_tree* t);
 int build_queue(fmm_tree* t, cudaStream_t st);
 template <typename T, typename TP, typename O>

@@ -6,21 +6,29 @@
 // real matrix per class:
 //   Lt(t) += T_c Mt(s),   T_c[(k,l), (n,m)] from (-1)^k rho^n conj(I_{n+k}^{m+l}(D/h_t)),
 //   D/h_t = V / 2^(1 + max(0, -dl)),  rho = h_s / h_t = 2^dl,
-// so all pairs of a class form one dense product
-//   C[pairs x K] = A[pairs x K] * T_c^T,  A rows = Mt of the sources (gathered).
-// This is the paper's M2L (Section 2.1) regrouped: classes replace the
-// per-pair operator, and the tensor cores run the products.
+// so all pairs of a class form one dense product.  This is the paper's M2L
+// (Section 2.1) regrouped: classes replace the per-pair operator, and the
+// tensor cores run the products.
 //
-// Precision: A and T_c are split into bf16 hi + lo parts and the product is
-// accumulated in FP32 in tensor memory as A_hi T_hi + A_hi T_lo + A_lo T_hi
-// (about 16 significant bits per product).  Each result row is added into the
-// target's local expansion with 16-byte vector atomics; pairs of rarer classes
-// (level gap above ten) go through the CUDA-core kernel first, which also
-// initialises every local expansion.
+// The product is taken transposed, C^T = T_c A^T (M = output coefficients,
+// N = 128 pairs, K = input coefficients), in the real basis of (p+1)^2
+// coefficients: the class operator is the MMA's A operand and lives in tensor
+// memory, assembled there by the kernel from the class's irregular harmonics
+// (no operator table in HBM); the pairs' source multipoles are the B operand,
+// gathered row by row from HBM into shared memory by TMA (tile::gather4).
+//
+// Precision: operator and multipoles are split into bf16 hi + lo parts and the
+// product is accumulated in FP32 in tensor memory as A_hi T_hi + A_hi T_lo +
+// A_lo T_hi (about 16 significant bits per product).  Each result column (one
+// pair) is added into the target's local expansion with coalesced FP32
+// reductions; pairs of rarer classes (level gap above ten) go through the
+// CUDA-core kernel first, which also initialises every local expansion.
 #include <cub/cub.cuh>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "fmm_internal.cuh"
 #include "tc_sm100.cuh"
@@ -30,15 +38,19 @@ namespace fmm {
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 constexpr int TC_MAX_DL = 10;
-constexpr int TC_ROWS = 128;                 // MMA M: pairs per work item
+constexpr int TC_ROWS = 128;                 // pairs per work item: the N of the transposed product
 // Class keys use 53 bits: (level gap + 16) in bits 48..52, each offset component
 // + 32768 in 16 bits.  A pair outside every class gets NOT_TC | target, so such
 // pairs sort after all classes and by target.
 constexpr uint64_t NOT_TC = 1ull << 53;
 constexpr int CLASS_KEY_BITS = 54;
 
-int tc_kpad(int p) { return ((2 * ntri(p)) + 15) & ~15; }
-bool tc_supported(int p) { return tc_kpad(p) <= 144; }
+// Real coefficients of an expansion truncated at degree p, and the width of a
+// gathered row: K = (p+1)^2 rounded up to whole 64-element swizzle atoms.
+static inline int tc_kreal(int p) { return (p + 1) * (p + 1); }
+int tc_kin(int p) { return (tc_kreal(p) + 63) & ~63; }
+// the operator (K <= 128 rows) must fit the 128 lanes of tensor memory
+bool tc_supported(int p) { return tc_kreal(p) <= 128; }
 
 // ---------------------------------------------------------------------------
 // build: class keys, grouping, operators, work items
@@ -84,6 +96,30 @@ __global__ void k_emit_items(int nclass, const int32_t* counts, const int32_t* c
     if (c >= nclass) return;
     int n = counts[c], f = class_first[c], w = tile_first[c];
     for (int r = 0; r < n; r += TC_ROWS) items[w++] = make_int4(c, f + r, min(TC_ROWS, n - r), 0);
+}
+
+// Partition of the work items over the blocks of the tensor-core kernel by
+// cost: an item costs one unit, plus TC_RUN_COST when it starts a class run
+// (the block assembles that class's operator).  Item ranges stay contiguous.
+constexpr int TC_RUN_COST = 4;
+__global__ void k_item_cost(int64_t nitems, const int4* __restrict__ items, int32_t* cost) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nitems) return;
+    cost[i] = 1 + ((i == 0 || items[i].x != items[i - 1].x) ? TC_RUN_COST : 0);
+}
+// first[b] = first item of block b: the first item whose inclusive cost prefix
+// exceeds b / nb of the total; first[nb] = nitems
+__global__ void k_block_ranges(int64_t nitems, const int32_t* __restrict__ prefix, int nb, int32_t* first) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nb) return;
+    if (b == 0 || b == nb) { first[b] = b == 0 ? 0 : (int32_t)nitems; return; }
+    const int64_t target = (int64_t)prefix[nitems - 1] * b / nb;
+    int64_t lo = 0, hi = nitems;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (prefix[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    first[b] = (int32_t)lo;
 }
 
 __global__ void k_gather_pairs(int64_t np, const int32_t* __restrict__ order, const int2* __restrict__ pairs,
@@ -207,116 +243,43 @@ __global__ void k_unpack_rem(int64_t n, const uint64_t* k, int32_t* tg, int32_t*
     if (i < n) { tg[i] = (int32_t)(k[i] >> 32); sr[i] = (int32_t)(k[i] & 0xffffffffu); }
 }
 
-// The 2 x 2 real block of a class operator for output complex coefficient
-// (k, l) and input (n, m): v[pa][pb], pa / pb = re|im of output / input;
-// If holds the irregular harmonics of the class offset, rpow[n] = rho^n.
-__device__ __forceinline__ void class_operator_block(int k, int l, int n, int m, const float* rpow,
-                                                     const cplx<float>* If, float (&v)[2][2]) {
-    const float s = (k & 1) ? -rpow[n] : rpow[n];
-    const cplx<float>* Ij = If + tri(n + k, 0);
-    if (m == 0) {
-        const cplx<float> x = Ij[l];
-        v[0][0] = s * x.re;
-        v[1][0] = -s * x.im;
-        v[0][1] = v[1][1] = 0.f;
-        return;
-    }
-    const cplx<float> xa = Ij[m + l];
-    const float Ar = xa.re, Ai = -xa.im;
-    float Br, Bi;
-    if (l >= m) {
-        const cplx<float> xb = Ij[l - m];
-        const float sg = (m & 1) ? -1.f : 1.f;
-        Br = sg * xb.re;
-        Bi = -sg * xb.im;
-    } else {
-        const cplx<float> xb = Ij[m - l];
-        const float sg = (l & 1) ? -1.f : 1.f;
-        Br = sg * xb.re;
-        Bi = sg * xb.im;
-    }
-    v[0][0] = s * (Ar + Br);
-    v[0][1] = s * (Bi - Ai);
-    v[1][0] = s * (Ai + Bi);
-    v[1][1] = s * (Ar - Br);
-}
-
-// two FP32 values split into bf16 hi and lo parts, packed in pairs
-__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
-    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-    const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
-    const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
-    hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
-    lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
-}
-
-// Operator of one class, split into bf16 hi/lo, K-major core-matrix layout:
-// rows = output coefficients (k, l, re|im), columns = input (n, m, re|im).
-// A thread takes the two rows of one output complex coefficient against four
-// input complex coefficients: two 16-byte core-matrix rows, adjacent in
-// memory, for hi and for lo (consecutive threads, consecutive rows).
-__global__ void k_class_operators(int p, int Kp, const uint64_t* __restrict__ ukeys,
-                                  __nv_bfloat16* __restrict__ ops) {
-    // harmonics in FP64 (one column per thread), entries assembled in FP32
-    // (each entry is rounded to FP32 and split to bf16 anyway)
-    extern __shared__ unsigned char smraw[];
-    cplx<double>* I = reinterpret_cast<cplx<double>*>(smraw);
-    cplx<float>* If = reinterpret_cast<cplx<float>*>(I + ntri(2 * p));
-    float* rpow = reinterpret_cast<float*>(If + ntri(2 * p));   // rho^n, n <= p
-    int8_t* tk = reinterpret_cast<int8_t*>(rpow + 32);            // tri index -> (n, m)
-    int8_t* tm = tk + 256;
-    const int c = blockIdx.x;
-    const uint64_t key = ukeys[c];
-    const int dl = (int)((key >> 48) & 0x1f) - 16;
+// Offset of a class in units of the target cell: D / h_t, from the class key.
+__device__ __forceinline__ void class_offset(uint64_t key, int& dl, double& dx, double& dy, double& dz) {
+    dl = (int)((key >> 48) & 0x1f) - 16;
     const double scale = 1.0 / (double)(2 << max(0, -dl));
-    const double dx = (double)((int)((key >> 32) & 0xffff) - 32768) * scale;
-    const double dy = (double)((int)((key >> 16) & 0xffff) - 32768) * scale;
-    const double dz = (double)((int)(key & 0xffff) - 32768) * scale;
-    for (int m = threadIdx.x; m <= 2 * p; m += blockDim.x) irregular_column<double>(2 * p, m, dx, dy, dz, I);
-    for (int n = 0; n <= p; n++)
-        for (int m = threadIdx.x; m <= n; m += blockDim.x) { tk[tri(n, m)] = (int8_t)n; tm[tri(n, m)] = (int8_t)m; }
-    // rho = 2^dl exactly, so rho^n = 2^(dl n), rounded to FP32
-    if (threadIdx.x <= p) rpow[threadIdx.x] = ldexpf(1.0f, dl * (int)threadIdx.x);
-    __syncthreads();
-    for (int e = threadIdx.x; e < ntri(2 * p); e += blockDim.x) If[e] = cmk<float>((float)I[e].re, (float)I[e].im);
-    __syncthreads();
-    const int K = ntri(p), kg = Kp >> 3, nchunk = Kp * kg;
-    uint4* hi = reinterpret_cast<uint4*>(ops + (size_t)c * 2 * Kp * Kp);
-    uint4* lo = hi + nchunk;
-    for (int u = threadIdx.x; u < nchunk / 2; u += blockDim.x) {
-        // 16-byte chunks 2u, 2u + 1 = rows o0, o0 + 1 of one core matrix, columns i0 .. i0 + 7
-        const int core = u >> 2;
-        const int o0 = (core / kg) * 8 + 2 * (u & 3), i0 = (core % kg) * 8;
-        const int ko = o0 >> 1;
-        float v[2][8];   // [re|im of the output][column - i0]
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int ki = (i0 >> 1) + q;
-            float b[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-            if (ko < K && ki < K) class_operator_block(tk[ko], tm[ko], tk[ki], tm[ki], rpow, If, b);
-            v[0][2 * q] = b[0][0];
-            v[0][2 * q + 1] = b[0][1];
-            v[1][2 * q] = b[1][0];
-            v[1][2 * q + 1] = b[1][1];
-        }
-#pragma unroll
-        for (int pa = 0; pa < 2; pa++) {
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int w = 0; w < 4; w++) split2(v[pa][2 * w], v[pa][2 * w + 1], h[w], l[w]);
-            hi[2 * u + pa] = make_uint4(h[0], h[1], h[2], h[3]);
-            lo[2 * u + pa] = make_uint4(l[0], l[1], l[2], l[3]);
-        }
-    }
+    dx = (double)((int)((key >> 32) & 0xffff) - 32768) * scale;
+    dy = (double)((int)((key >> 16) & 0xffff) - 32768) * scale;
+    dz = (double)((int)(key & 0xffff) - 32768) * scale;
 }
 
-// Work items and operators of nclass classes with sizes counts[] and keys
-// ukeys[] (both in class order); cfirst[c] receives the first pair of class c.
+// Irregular harmonics I_j^m(D / h_t), j <= 2p, of each class offset: computed
+// in FP64, stored in FP32 (the operator is split to bf16 hi + lo anyway).  The
+// tensor-core kernel assembles each class operator from these.  One warp per
+// class, one column m per lane.
+__global__ void k_class_harmonics(int p, int nclass, const uint64_t* __restrict__ ukeys,
+                                  cplx<float>* __restrict__ harm) {
+    extern __shared__ unsigned char smraw[];
+    const int P = 2 * p, nh = ntri(P);
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (c >= nclass) return;
+    cplx<double>* I = reinterpret_cast<cplx<double>*>(smraw) + (size_t)wib * nh;
+    int dl;
+    double dx, dy, dz;
+    class_offset(ukeys[c], dl, dx, dy, dz);
+    for (int m = lane; m <= P; m += 32) irregular_column<double>(P, m, dx, dy, dz, I);
+    __syncwarp();
+    for (int e = lane; e < nh; e += 32) harm[(size_t)c * nh + e] = cmk<float>((float)I[e].re, (float)I[e].im);
+}
+
+// Work items and class harmonics of nclass classes with sizes counts[] and
+// keys ukeys[] (both in class order); cfirst[c] receives the first pair of
+// class c.
 static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const int32_t* counts, int32_t* cfirst,
                         int64_t* items_out, cudaStream_t st) {
     TreeDev& d = t->d;
     int rc;
-    const int p = t->prm.p, Kp = tc_kpad(p);
+    const int p = t->prm.p;
     *items_out = 0;
     if (nclass == 0) return FMM_OK;
     int32_t *tiles = nullptr, *tfirst = nullptr;
@@ -339,12 +302,32 @@ static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const in
     if ((rc = dev_alloc(&d.tc_items, (size_t)h_items, t, st))) return rc;
     k_emit_items<<<nblk(nclass, 256), 256, 0, st>>>(nclass, counts, cfirst, tfirst, d.tc_items);
     count_launch(t);
-    // operators: on the side stream, so that they overlap the rest of the
+    // block ranges of the tensor-core kernel (one block per SM), balanced by cost
+    {
+        const int nb = (int)std::min<int64_t>(h_items, (int64_t)t->num_sms);
+        int32_t *cost = nullptr, *pre = nullptr;
+        if ((rc = dev_alloc(&cost, (size_t)h_items, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&pre, (size_t)h_items, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&d.tc_block_first, (size_t)nb + 1, t, st))) return rc;
+        k_item_cost<<<nblk(h_items, 256), 256, 0, st>>>(h_items, d.tc_items, cost);
+        size_t sb = 0;
+        char* stmp = nullptr;
+        cub::DeviceScan::InclusiveSum(nullptr, sb, cost, pre, h_items, st);
+        if ((rc = dev_alloc(&stmp, sb, nullptr, st))) return rc;
+        FMM_CUDA_TRY(cub::DeviceScan::InclusiveSum(stmp, sb, cost, pre, h_items, st));
+        k_block_ranges<<<nblk(nb + 1, 256), 256, 0, st>>>(h_items, pre, nb, d.tc_block_first);
+        count_launch(t, 3);
+        cudaFreeAsync(stmp, st);
+        cudaFreeAsync(cost, st);
+        cudaFreeAsync(pre, st);
+        t->tc_nblocks = nb;
+    }
+    // harmonics: on the side stream, so that they overlap the rest of the
     // build and the upward pass; the tensor-core M2L waits for ev_ops
-    size_t ob = (size_t)nclass * 2 * Kp * Kp;
-    __nv_bfloat16* ops = nullptr;
-    if ((rc = dev_alloc(&ops, ob, t, st))) return rc;
-    d.tc_ops = ops;
+    const int nh = ntri(2 * p);
+    cplx<float>* harm = nullptr;
+    if ((rc = dev_alloc(&harm, (size_t)nclass * nh, t, st))) return rc;
+    d.tc_harm = harm;
     if ((rc = dev_alloc(&d.tc_keys, (size_t)nclass, t, st))) return rc;
     FMM_CUDA_TRY(cudaMemcpyAsync(d.tc_keys, ukeys, sizeof(uint64_t) * nclass, cudaMemcpyDeviceToDevice, st));
     cudaStream_t so = st;
@@ -353,8 +336,9 @@ static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const in
         FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
         FMM_CUDA_TRY(cudaStreamWaitEvent(so, t->ev_fork, 0));
     }
-    size_t smem = ntri(2 * p) * (sizeof(cplx<double>) + sizeof(cplx<float>)) + 32 * 4 + 512;
-    k_class_operators<<<nclass, 256, smem, so>>>(p, Kp, d.tc_keys, ops);
+    constexpr int HW = 4;   // classes (warps) per block
+    k_class_harmonics<<<nblk(nclass, HW), 32 * HW, HW * nh * sizeof(cplx<double>), so>>>(p, nclass, d.tc_keys,
+                                                                                        harm);
     count_launch(t);
     FMM_CUDA_TRY(cudaGetLastError());
     if (so != st) FMM_CUDA_TRY(cudaEventRecord(t->ev_ops, so));
@@ -362,6 +346,94 @@ static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const in
     cudaFreeAsync(tfirst, st);
     *items_out = h_items;
     return FMM_OK;
+}
+
+// A class with at most TC_MIN_PAIRS pairs is left to the CUDA-core kernel: the
+// tensor-core kernel assembles one operator per class, which does not pay for
+// a handful of pairs (on a clustered 4M-particle tree, 97 % of the classes hold
+// under 1 % of the pairs).
+constexpr int TC_MIN_PAIRS = 64;
+
+// flag[i] = pair i (of `order`, classes in class order first) belongs to a kept class
+__global__ void k_pair_keep(int64_t np, int64_t ntc, int nclass, const int32_t* __restrict__ cfirst,
+                            const int32_t* __restrict__ counts, char* __restrict__ flag) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    char f = 0;
+    if (i < ntc) {
+        int lo = 0, hi = nclass;   // last class with cfirst <= i
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (cfirst[mid] <= i) lo = mid; else hi = mid;
+        }
+        f = counts[lo] > TC_MIN_PAIRS;
+    }
+    flag[i] = f;
+}
+__global__ void k_class_keep(int nclass, const int32_t* __restrict__ counts, char* __restrict__ keep) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < nclass) keep[c] = counts[c] > TC_MIN_PAIRS;
+}
+
+// Drops the classes of at most TC_MIN_PAIRS pairs: order[np] (pair indices, the
+// ntc classed ones in class order first) is partitioned stably into the kept
+// classes' pairs followed by all others; ukeys and counts are compacted to the
+// kept classes; nclass and ntc are updated.
+static int drop_small_classes(fmm_tree* t, int64_t np, int32_t* order, int& nclass, uint64_t* ukeys, int32_t* counts,
+                              int64_t& ntc, cudaStream_t st) {
+    int rc;
+    if (nclass == 0) return FMM_OK;
+    int32_t *cfirst = nullptr, *order2 = nullptr, *counts2 = nullptr;
+    uint64_t* ukeys2 = nullptr;
+    char *flag = nullptr, *keep = nullptr;
+    int64_t* nsel = nullptr;
+    if ((rc = dev_alloc(&cfirst, (size_t)nclass, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&order2, (size_t)np, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&counts2, (size_t)nclass, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&ukeys2, (size_t)nclass, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&flag, (size_t)np, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&keep, (size_t)nclass, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&nsel, 3, nullptr, st))) return rc;
+    size_t tb = 0, tb2 = 0;
+    char* tmp = nullptr;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb, counts, cfirst, nclass, st);
+    cub::DevicePartition::Flagged(nullptr, tb2, order, flag, order2, nsel, np, st);
+    tb = std::max(tb, tb2);
+    cub::DeviceSelect::Flagged(nullptr, tb2, ukeys, keep, ukeys2, nsel + 1, nclass, st);
+    tb = std::max(tb, tb2);
+    cub::DeviceSelect::Flagged(nullptr, tb2, counts, keep, counts2, nsel + 2, nclass, st);
+    tb = std::max(tb, tb2);
+    if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
+    FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, counts, cfirst, nclass, st));
+    k_pair_keep<<<nblk(np, 256), 256, 0, st>>>(np, ntc, nclass, cfirst, counts, flag);
+    k_class_keep<<<nblk(nclass, 256), 256, 0, st>>>(nclass, counts, keep);
+    FMM_CUDA_TRY(cub::DevicePartition::Flagged(tmp, tb, order, flag, order2, nsel, np, st));
+    FMM_CUDA_TRY(cub::DeviceSelect::Flagged(tmp, tb, ukeys, keep, ukeys2, nsel + 1, nclass, st));
+    FMM_CUDA_TRY(cub::DeviceSelect::Flagged(tmp, tb, counts, keep, counts2, nsel + 2, nclass, st));
+    count_launch(t, 6);
+    int64_t h[3] = {0, 0, 0};
+    FMM_CUDA_TRY(cudaMemcpyAsync(h, nsel, sizeof(h), cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(order, order2, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(ukeys, ukeys2, sizeof(uint64_t) * h[1], cudaMemcpyDeviceToDevice, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(counts, counts2, sizeof(int32_t) * h[2], cudaMemcpyDeviceToDevice, st));
+    ntc = h[0];
+    nclass = (int)h[1];
+    cudaFreeAsync(tmp, st); cudaFreeAsync(cfirst, st); cudaFreeAsync(order2, st); cudaFreeAsync(counts2, st);
+    cudaFreeAsync(ukeys2, st); cudaFreeAsync(flag, st); cudaFreeAsync(keep, st); cudaFreeAsync(nsel, st);
+    return FMM_OK;
+}
+
+// chunks of at most M2L_CHUNK entries of each target's class-less list
+__global__ void k_rem_nchunks(int ncell, const int64_t* __restrict__ start, int32_t* nch) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) nch[c] = (int32_t)((start[c + 1] - start[c] + M2L_CHUNK - 1) / M2L_CHUNK);
+}
+__global__ void k_rem_fill(int ncell, const int64_t* __restrict__ start, const int32_t* __restrict__ off, int2* chunks) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int k = off[c];
+    for (int64_t e = start[c]; e < start[c + 1]; e += M2L_CHUNK) chunks[k++] = make_int2(c, (int)e);
 }
 
 // The pairs without a class, tc_tgt/tc_src[ntc, np), sorted by (target,
@@ -388,6 +460,31 @@ static int finish_remainder(fmm_tree* t, int64_t ntc, int64_t nrem, cudaStream_t
     if ((rc = dev_alloc(&d.rem_start, (size_t)t->ncell + 1, t, st))) return rc;
     k_csr_from_targets<<<nblk(t->ncell + 1, 256), 256, 0, st>>>(d.tc_tgt + ntc, nrem, t->ncell, d.rem_start);
     count_launch(t);
+    // chunks of at most M2L_CHUNK pairs per target for the chunked CUDA-core M2L
+    t->rem_nchunk = 0;
+    if (nrem > 0) {
+        const int nc = t->ncell;
+        int32_t *nch = nullptr, *off = nullptr;
+        if ((rc = dev_alloc(&nch, (size_t)nc, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&off, (size_t)nc, nullptr, st))) return rc;
+        k_rem_nchunks<<<nblk(nc, 256), 256, 0, st>>>(nc, d.rem_start, nch);
+        size_t tb = 0;
+        char* tmp = nullptr;
+        cub::DeviceScan::ExclusiveSum(nullptr, tb, nch, off, nc, st);
+        if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
+        FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, nch, off, nc, st));
+        int32_t h[2] = {0, 0};
+        FMM_CUDA_TRY(cudaMemcpyAsync(h, off + nc - 1, 4, cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(h + 1, nch + nc - 1, 4, cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+        t->rem_nchunk = (int64_t)h[0] + h[1];
+        if ((rc = dev_alloc(&d.rem_chunks, (size_t)std::max<int64_t>(1, t->rem_nchunk), t, st))) return rc;
+        k_rem_fill<<<nblk(nc, 256), 256, 0, st>>>(nc, d.rem_start, off, d.rem_chunks);
+        count_launch(t, 3);
+        cudaFreeAsync(tmp, st);
+        cudaFreeAsync(nch, st);
+        cudaFreeAsync(off, st);
+    }
     return FMM_OK;
 }
 
@@ -435,8 +532,8 @@ static int classes_by_hash(fmm_tree* t, const int2* pairs, bool* done, cudaStrea
         release();
         return FMM_OK;
     }
-    const int nclass = (int)nclass64;
-    const int64_t nrem = (int64_t)hc[0], ntc = np - nrem;
+    int nclass = (int)nclass64;
+    int64_t ntc = np - (int64_t)hc[0];
     // stable sort of the pairs by class id (a few bits: nclass + 1 ids)
     int32_t *class_of_slot = nullptr, *cid0 = nullptr, *cid1 = nullptr, *idx0 = nullptr, *idx1 = nullptr;
     int32_t *counts = nullptr, *cfirst = nullptr;
@@ -461,6 +558,8 @@ static int classes_by_hash(fmm_tree* t, const int2* pairs, bool* done, cudaStrea
     cudaFreeAsync(tmp, st);
     k_class_bounds<<<nblk(nclass + 1, 256), 256, 0, st>>>(nclass, cid1, np, counts);
     count_launch(t, 3);
+    if ((rc = drop_small_classes(t, np, idx1, nclass, skeys, counts, ntc, st))) return rc;
+    const int64_t nrem = np - ntc;
     int64_t h_items = 0;
     if ((rc = emit_classes(t, nclass, skeys, counts, cfirst, &h_items, st))) return rc;
     if ((rc = dev_alloc(&d.tc_tgt, (size_t)np, t, st))) return rc;
@@ -537,22 +636,24 @@ int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st) {
         FMM_CUDA_TRY(cudaMemcpyAsync(&h_nruns, nruns, 4, cudaMemcpyDeviceToHost, st));
         FMM_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    const int nclass = h_nruns;
+    int nclass = h_nruns;
+    if ((rc = drop_small_classes(t, np, i1, nclass, ukeys, counts, ntc, st))) return rc;
+    const int64_t nrem2 = np - ntc;
     int32_t* cfirst = nullptr;
     if ((rc = dev_alloc(&cfirst, (size_t)nclass + 1, nullptr, st))) return rc;
     int64_t h_items = 0;
     if ((rc = emit_classes(t, nclass, ukeys, counts, cfirst, &h_items, st))) return rc;
-    // pairs in class order; the tail (no class) is in target order already
+    // pairs in class order, then the rest (sorted by target below)
     if ((rc = dev_alloc(&d.tc_tgt, (size_t)np, t, st))) return rc;
     if ((rc = dev_alloc(&d.tc_src, (size_t)np, t, st))) return rc;
     k_gather_pairs<<<nblk(np, 256), 256, 0, st>>>(np, i1, pairs, d.tc_tgt, d.tc_src);
     count_launch(t);
-    if ((rc = finish_remainder(t, ntc, nrem, st))) return rc;
+    if ((rc = finish_remainder(t, ntc, nrem2, st))) return rc;
     FMM_CUDA_TRY(cudaGetLastError());
     t->tc_nclass = nclass;
     t->tc_nitems = h_items;
     t->tc_npairs = ntc;
-    t->tc_nrem = nrem;
+    t->tc_nrem = nrem2;
     cudaFreeAsync(k0, st); cudaFreeAsync(k1, st); cudaFreeAsync(i0, st); cudaFreeAsync(i1, st);
     cudaFreeAsync(ukeys, st); cudaFreeAsync(counts, st); cudaFreeAsync(nruns, st);
     cudaFreeAsync(cfirst, st);
@@ -560,45 +661,86 @@ int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// evaluate: split multipoles, tensor-core product, vector-atomic accumulation
+// evaluate: real-basis split of the multipoles, transposed class product
 // ---------------------------------------------------------------------------
 
-// Mt (FP32 complex, row stride KS) -> [cell][hi: Kp | lo: Kp] bf16, real layout (re, im)
-__global__ void k_split_multipoles(int ncell, int K2, int KS, int Kp, const float* __restrict__ M,
-                                   __nv_bfloat16* __restrict__ Ms) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= (int64_t)ncell * Kp) return;
-    int c = (int)(e / Kp), j = (int)(e % Kp);
-    float v = j < K2 ? M[(int64_t)c * 2 * KS + j] : 0.f;
-    __nv_bfloat16 h = __float2bfloat16_rn(v);
-    Ms[(int64_t)c * 2 * Kp + j] = h;
-    Ms[(int64_t)c * 2 * Kp + Kp + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+// Real basis of an expansion truncated at degree p: index c runs over, for
+// n = 0..p, (n, 0) re, then (n, m) re, (n, m) im for m = 1..n, so there are
+// (p+1)^2 of them (the imaginary parts of the m = 0 terms vanish for real
+// charges and are left out).  Decoded as n | m << 8 | im << 16.
+__host__ __device__ inline int real_index_decode(int c) {
+    int n = 0;
+    while ((n + 1) * (n + 1) <= c) n++;
+    const int r = c - n * n;
+    if (r == 0) return n;
+    const int m = (r + 1) >> 1;
+    return n | (m << 8) | ((r & 1) ? 0 : (1 << 16));
+}
+// float offset of real coefficient c in a complex (m >= 0, triangular) row
+__host__ __device__ inline int real_index_offset(int c) {
+    const int d = real_index_decode(c);
+    return 2 * tri(d & 0xff, (d >> 8) & 0xff) + (d >> 16);
 }
 
-// One persistent block per SM runs its range of work items as a
-// warp-specialised pipeline:
-//   producer warps (4)  gather the 128 source rows of an item (hi and lo
-//                       bf16 halves) into one of `stages` shared-memory stages
-//                       with cp.async, plus the class operator into one of
-//                       `nslots` operator slots when the class changes;
-//   MMA warp (1)        one thread issues the 3 x Kp/16 tcgen05.mma of an item
-//                       into one of `nacc` TMEM accumulators (Kp columns each)
-//                       and commits them to mbarriers;
-//   epilogue warps (8)  drain a finished accumulator into the targets' rows
-//                       of L with float2 reductions, two warps per TMEM lane
-//                       quarter, each taking half of the column blocks.
-// mbarriers: full[s] (producers -> MMA), empty[s] (MMA completion ->
-// producers), accf[a] (MMA completion -> epilogue), acce[a] (epilogue ->
-// MMA), opfree[o] (MMA completion of a class run -> producers).  Every wait is
-// bounded; a wait that runs out raises a block-wide abort flag, every role
-// leaves its loop, and the kernel reports FMM_ERR_TIMEOUT through *status.
-constexpr int TC_EPI_WARPS = 8, TC_PROD_WARPS = 4;
-constexpr int TC_MMA_WARP = TC_EPI_WARPS + TC_PROD_WARPS;
-constexpr int TC_THREADS = 32 * (TC_EPI_WARPS + TC_PROD_WARPS + 1);
-constexpr int TC_PROD_THREADS = 32 * TC_PROD_WARPS;
-constexpr int TC_MAX_STAGES = 4, TC_MAX_ACC = 4, TC_TMEM_COLS = 512;
-// drain accumulators with TMA bulk reductions where the staging tiles fit
-constexpr bool TC_BULK_DRAIN = true;
+// Mt (FP32 complex rows, ldM floats apart) -> [cell][hi: KI | lo: KI] bf16 in
+// the real basis, zero beyond KR = (p+1)^2
+__global__ void k_split_real(int ncell, int KR, int KI, int ldM, const float* __restrict__ M,
+                             __nv_bfloat16* __restrict__ Ms) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)ncell * KI) return;
+    const int c = (int)(e % KI);
+    const int64_t cell = e / KI;
+    const float v = c < KR ? M[cell * ldM + real_index_offset(c)] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    Ms[cell * 2 * KI + c] = h;
+    Ms[cell * 2 * KI + KI + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// One persistent block per SM runs a contiguous range of work items (128
+// pairs of one class each) as a warp-specialised pipeline:
+//   producer (warp 12)    gathers the 128 source rows of an item with TMA,
+//                         one 64-coefficient swizzle atom (hi and lo tiles,
+//                         32 KB) per shared-memory stage;
+//   assemblers (8..11)    build the operator of each new class in one of two
+//                         tensor-memory slots (lane = output coefficient, hi
+//                         and lo bf16 parts), from the class harmonics;
+//   MMA (warp 13)         one thread issues, per atom and K step of 16, the
+//                         three products T_hi A_hi + T_lo A_hi + T_hi A_lo
+//                         into one of `nacc` 128-column accumulators;
+//   epilogue (warps 0..7) reads an accumulator (lane = output coefficient,
+//                         column = pair) and adds it into the targets' local
+//                         expansions: per pair, one warp-wide reduction of
+//                         32 consecutive coefficients.
+// Tensor memory: operator slot o in columns [o KI, (o+1) KI) (hi then lo,
+// two bf16 per column), accumulators from column 2 KI on.  mbarriers: full /
+// empty per stage, opfull / opempty per operator slot, accf / acce per
+// accumulator, fin for the last MMAs.  Every wait is bounded; a wait that
+// runs out raises a block-wide abort flag, every role leaves its loop, the
+// producer waits (bounded) for its copies in flight, and the kernel reports
+// FMM_ERR_TIMEOUT through *status.
+constexpr int TC_M = 128;                              // MMA M: output coefficients (K <= 128)
+constexpr int TC_ATOM = 64;                            // coefficients per 128-byte swizzle atom
+constexpr int TC_TILE_BYTES = TC_ROWS * TC_ATOM * 2;   // 128 rows x 128 B
+constexpr int TC_STAGE_BYTES = 2 * TC_TILE_BYTES;      // hi and lo tiles of one atom
+constexpr int TC_EPI_WARPS = 8, TC_ASM_WARPS = 4;
+constexpr int TC_PROD_WARP = TC_EPI_WARPS + TC_ASM_WARPS;
+constexpr int TC_MMA_WARP = TC_PROD_WARP + 1;
+constexpr int TC_THREADS = 32 * (TC_MMA_WARP + 1);
+constexpr int TC_MAX_STAGES = 8, TC_MAX_ACC = 3, TC_TMEM_COLS = 512;
+constexpr int TC_SRC_AHEAD = 6, TC_SRC_RING = 8;   // producer: items of source indices in flight, ring slots
+
+struct TcArgs {
+    int p, KR, KI, nat, stages, nacc, ldL, nh;
+    const int32_t* block_first;  // [gridDim.x + 1] item range of each block
+    const int4* items;        // (class, first pair, rows, -)
+    const int32_t* src;       // sources of the pairs in class order
+    const int32_t* tgt;       // targets
+    const uint64_t* keys;     // class keys
+    const cplx<float>* harm;  // class harmonics
+    float* L;
+    int* status;
+    long long budget_ns;
+};
 
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, long long budget_ns, volatile int* abort_flag) {
     if (tc::mbar_try_wait(bar, parity)) return true;
@@ -615,390 +757,372 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, long lon
     }
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+// all threads of a named barrier (id, nthreads) leave together: true iff every
+// one passed ok
+__device__ __forceinline__ bool bar_all(int id, int nthreads, bool ok) {
+    int all_ok;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\tselp.b32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(all_ok)
+        : "r"((int)ok), "r"(id), "r"(nthreads)
+        : "memory");
+    return all_ok != 0;
 }
 
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+// two FP32 values -> packed bf16 hi parts and packed bf16 lo parts
+__device__ __forceinline__ void split_pack(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
+    const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
+    hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+    lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
 }
 
-// producer thread pt (0..127): its share of the 128 x Kp source rows (hi,
-// lo); src[r] is the source cell of row r, -1 for an empty row.  One warp
-// instruction covers 8 rows x 4 consecutive 16-byte chunks: 64 contiguous
-// bytes (two whole sectors) per source row, and four whole 128-byte core
-// matrices in shared memory (no bank conflicts).
-__device__ __forceinline__ void tc_gather(int pt, int Kp, int cpr, const int* src,
-                                          const __nv_bfloat16* __restrict__ Ms, unsigned char* A_hi,
-                                          unsigned char* A_lo) {
-    const int lane = pt & 31, r_in = lane & 7, j_in = lane >> 3;
-    const int ntile = (TC_ROWS / 8) * ((cpr + 3) / 4);
-    for (int t = pt >> 5; t < ntile; t += TC_PROD_WARPS) {
-        const int r = 8 * (t % (TC_ROWS / 8)) + r_in, j = 4 * (t / (TC_ROWS / 8)) + j_in;
-        if (j >= cpr) continue;
-        const int sc = src[r];
-        const bool valid = sc >= 0;
-        const __nv_bfloat16* g = Ms + (size_t)(valid ? sc : 0) * 2 * Kp + 8 * j;
-        const uint32_t off = tc::core_offset(r, 8 * j, Kp);
-        tc::cp_async16_ca(A_hi + off, g, valid ? 16u : 0u);
-        tc::cp_async16_ca(A_lo + off, g + Kp, valid ? 16u : 0u);
-    }
+// Entry of a class operator in the real basis: output (k, l, pa) (pa = 0 real
+// part, 1 imaginary), input (n, m, pb).  From the complex M2L
+//   L_k^l += (-1)^k sum_{n, |m| <= n} rho^n M_n^m conj(I_{n+k}^{m+l}),
+// with M_n^{-m} = (-1)^m conj(M_n^m), the input pair (n, +-m) gives
+//   I_{n+k}^{m+l} and I_{n+k}^{|l-m|} (the latter through X^{-m} = (-1)^m conj X^m),
+// and the m = 0 term appears once (weight 1/2 on the symmetric form below).
+// No branch: the kernel evaluates 32 entries of a row side by side.
+//   colmeta  n | m << 4 | pb << 8 | tri(n, 0) << 9 | (input exists) << 15
+//   Tk = tri(k, 0), ksgn = (-1)^k (0 for a padding row), H = the class harmonics
+//   I_j^m as (re, im) at tri(j, 0) + m, rho^n = 2^(dl n).
+__device__ __forceinline__ float class_operator_entry(uint32_t colmeta, int k, int l, int pa, int Tk, float ksgn,
+                                                      int dl, const float2* __restrict__ H) {
+    const int n = colmeta & 15, m = (colmeta >> 4) & 15, pb = (colmeta >> 8) & 1, trin = (colmeta >> 9) & 63;
+    const int base = trin + Tk + n * k;   // tri(n + k, 0)
+    const bool ge = l >= m;
+    const float2 xa = H[base + m + l];
+    const float2 xb = H[base + (ge ? l - m : m - l)];
+    const float rp = ksgn * __int_as_float((127 + dl * n) << 23);   // (-1)^k 2^(dl n), exact
+    const float sg = (((ge ? m : l) & 1) ? -1.f : 1.f);
+    const float Ar = xa.x, Ai = -xa.y;
+    const float Br = sg * xb.x, Bi = (ge ? -sg : sg) * xb.y;
+    const float v = pa == 0 ? (pb == 0 ? Ar + Br : Bi - Ai) : (pb == 0 ? Ai + Bi : Ar - Br);
+    const float w = ((colmeta >> 15) & 1) ? (m == 0 ? 0.5f : 1.f) : 0.f;
+    return rp * w * v;
 }
 
-__device__ __forceinline__ void tc_load_operator(int pt, int Kp, int cls, const __nv_bfloat16* __restrict__ ops,
-                                                 unsigned char* B) {
-    const unsigned char* g = reinterpret_cast<const unsigned char*>(ops + (size_t)cls * 2 * Kp * Kp);
-    const int nchunk = Kp * Kp * 2 * 2 / 16;  // hi then lo, contiguous in both places
-    for (int q = pt; q < nchunk; q += TC_PROD_THREADS) tc::cp_async16(B + 16 * q, g + 16 * q, 16);
-}
-
-// Column blocks of 16 a drain warp reads per item: half of Kp / 16, at most
-// 5 (Kp = 144).
-constexpr int TC_MAX_CB = 5;
-
-// Reads the warp's share of one accumulator: rows 32 quarter + 16 h + lane/4
-// (v[h][c][0..1], v[h][c][4..5]) and that row + 8 (v[h][c][2..3],
-// v[h][c][6..7]), column blocks cb0 + c for c < ncb, all loads issued before
-// one wait.
-__device__ __forceinline__ void tc_load_acc(uint32_t tacc, int quarter, int cb0, int ncb,
-                                            uint32_t (&v)[2][TC_MAX_CB][8]) {
-#pragma unroll
-    for (int h = 0; h < 2; h++)
-#pragma unroll
-        for (int c = 0; c < TC_MAX_CB; c++)
-            if (c < ncb) tc::tmem_ld16x256_nowait(tacc + ((uint32_t)(32 * quarter + 16 * h) << 16) + 16 * (cb0 + c), v[h][c]);
-    tc::tmem_wait_ld();
-}
-
-// Adds one accumulator (TMEM columns from tacc on) into the targets' rows of
-// L; tgt[h][0..1] are the targets of rows 32 quarter + 16 h + lane/4 (+ 8),
-// -1 for an empty row.  The 16x256b TMEM load gives four consecutive threads
-// eight consecutive columns of one row, so each warp-wide float2 reduction
-// covers eight whole 32-byte sectors.
-__device__ __forceinline__ void tc_drain(uint32_t tacc, int quarter, int cb0, int cb1, int ncols, int ldL,
-                                         const int (&tgt)[2][2], float* __restrict__ L) {
-    const int lane = threadIdx.x & 31;
-    uint32_t v[2][TC_MAX_CB][8];
-    tc_load_acc(tacc, quarter, cb0, cb1 - cb0, v);
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const int ta = tgt[h][0], tb = tgt[h][1];
-        float* La = L + (size_t)(ta < 0 ? 0 : ta) * ldL;
-        float* Lb = L + (size_t)(tb < 0 ? 0 : tb) * ldL;
-#pragma unroll
-        for (int c = 0; c < TC_MAX_CB; c++) {
-            if (c >= cb1 - cb0) break;
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-                const int col = 16 * (cb0 + c) + 8 * k + 2 * (lane & 3);
-                if (col < ncols) {
-                    if (ta >= 0)
-                        atomicAdd(reinterpret_cast<float2*>(La + col),
-                                  make_float2(__uint_as_float(v[h][c][4 * k]), __uint_as_float(v[h][c][4 * k + 1])));
-                    if (tb >= 0)
-                        atomicAdd(reinterpret_cast<float2*>(Lb + col), make_float2(__uint_as_float(v[h][c][4 * k + 2]),
-                                                                                   __uint_as_float(v[h][c][4 * k + 3])));
-                }
-            }
-        }
-    }
-}
-
-// Bulk-reduction form of the drain: the warp's 32 rows x [c0, c1) columns go
-// through a shared-memory tile (row stride `stride` floats), then lane r adds
-// row r into its target's row of L with one TMA bulk reduction of
-// 4 (c1 - c0) bytes.  tgt_row is the target of row 32 quarter + lane.
-__device__ __forceinline__ void tc_drain_bulk(uint32_t tacc, int quarter, int cb0, int cb1, int c0, int c1,
-                                              int stride, int ldL, int tgt_row, float* stg,
-                                              float* __restrict__ L) {
-    const int lane = threadIdx.x & 31;
-    uint32_t v[2][TC_MAX_CB][8];
-    tc_load_acc(tacc, quarter, cb0, cb1 - cb0, v);
-    tc::bulk_wait_read();  // the previous item's reductions have read the tile
-    __syncwarp();
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const int ra = 16 * h + (lane >> 2);
-#pragma unroll
-        for (int c = 0; c < TC_MAX_CB; c++) {
-            if (c >= cb1 - cb0) break;
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-                const int col = 16 * c + 8 * k + 2 * (lane & 3);
-                *reinterpret_cast<uint2*>(stg + ra * stride + col) = make_uint2(v[h][c][4 * k], v[h][c][4 * k + 1]);
-                *reinterpret_cast<uint2*>(stg + (ra + 8) * stride + col) =
-                    make_uint2(v[h][c][4 * k + 2], v[h][c][4 * k + 3]);
-            }
-        }
-    }
-    tc::fence_proxy_async();
-    __syncwarp();
-    if (tgt_row >= 0 && c1 > c0) {
-        tc::bulk_reduce_add_f32(L + (size_t)tgt_row * ldL + c0, stg + lane * stride, (uint32_t)(4 * (c1 - c0)));
-        tc::bulk_commit();
-    }
-}
-
-struct TcShape {
-    int stages, nslots, nacc, stg_stride;  // stg_stride 0: float2 reductions, no staging tiles
-    size_t smem;
-};
-
-// Stages and operator slots that fit `cap` bytes of shared memory, and TMEM
-// accumulators that fit the 512 columns of one SM (one block per SM).  With
-// `bulk`, each epilogue warp also gets a 32-row staging tile for the bulk
-// reductions, if two stages and one operator slot still fit.  The tile's row
-// stride is 8 mod 16 floats, so that the 8-byte stores of a half-warp (four
-// rows of eight words) fall on distinct banks, unless that padding costs a
-// pipeline stage (then 4 mod 16).
-static TcShape tc_shape_stride(int Kp, size_t cap, int stride) {
-    const size_t stage = (size_t)2 * TC_ROWS * Kp * 2 + TC_ROWS * sizeof(int), slot = (size_t)2 * Kp * Kp * 2;
-    TcShape sh{};
-    size_t stg = 0;
-    if (stride > 0) {
-        sh.stg_stride = stride;
-        stg = (size_t)TC_EPI_WARPS * 32 * sh.stg_stride * 4;
-        if (stg + 2 * stage + slot > cap) { sh.stg_stride = 0; stg = 0; }
-    }
-    sh.nslots = 2 * slot + 2 * stage + stg <= cap ? 2 : 1;
-    sh.stages = (int)std::min<size_t>(TC_MAX_STAGES, (cap - stg - sh.nslots * slot) / stage);
-    sh.nacc = std::min(TC_MAX_ACC, TC_TMEM_COLS / Kp);
-    sh.smem = sh.stages * stage + sh.nslots * slot + stg;
-    return sh;
-}
-static TcShape tc_shape(int Kp, size_t cap, bool bulk) {
-    if (!bulk) return tc_shape_stride(Kp, cap, 0);
-    const int w = 16 * ((Kp / 16 + 1) / 2);   // half a row (the columns of one epilogue warp)
-    const TcShape a = tc_shape_stride(Kp, cap, w + 8), b = tc_shape_stride(Kp, cap, w + 4);
-    return (a.stages >= b.stages && a.nslots >= b.nslots && a.stg_stride > 0) ? a : b;
-}
-
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_m2l_tc(int Kp, int stages, int nslots, int nacc, int stg_stride, int ncols, int ldL, int n_items, int per_cta,
-             const int4* __restrict__ items, const int32_t* __restrict__ pc_src, const int32_t* __restrict__ pc_tgt,
-             const __nv_bfloat16* __restrict__ ops, const __nv_bfloat16* __restrict__ Ms, float* __restrict__ L,
-             int* status, long long budget_ns) {
-    extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ uint64_t full[TC_MAX_STAGES], empty[TC_MAX_STAGES], accf[TC_MAX_ACC], acce[TC_MAX_ACC], opfree[2];
+__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
+    extern __shared__ unsigned char smraw[];
+    // stages first (1024-byte aligned: the swizzle atoms), then the harmonics
+    unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    cplx<float>* hbuf = reinterpret_cast<cplx<float>*>(sm + (size_t)a.stages * TC_STAGE_BYTES);
+    __shared__ uint64_t full[TC_MAX_STAGES], empty[TC_MAX_STAGES], opfull[2], opempty[2], accf[TC_MAX_ACC],
+        acce[TC_MAX_ACC], fin;
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
-    const size_t abytes = (size_t)TC_ROWS * Kp * 2, bbytes = (size_t)Kp * Kp * 2;
-    // stage s: A hi at sm + 2 s abytes, A lo right after; operator slot o: hi at
-    // sm + 2 stages abytes + 2 o bbytes, lo right after; then the row sources
-    // of each stage (TC_ROWS ints per stage)
-    auto A_of = [&](int s) { return sm + 2 * s * abytes; };
-    auto B_of = [&](int o) { return sm + 2 * stages * abytes + 2 * o * bbytes; };
-    int* src_idx = reinterpret_cast<int*>(sm + 2 * stages * abytes + 2 * nslots * bbytes);
-    float* stg_all = reinterpret_cast<float*>(src_idx + stages * TC_ROWS);  // staging tiles (bulk drain)
+    __shared__ int dec[TC_M];        // real index -> n | m << 8 | im << 16 (-1 beyond K)
+    __shared__ uint32_t colmeta[TC_M];  // the same for the operator's columns (class_operator_entry)
+    __shared__ int src_ring[TC_SRC_RING * TC_ROWS];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        for (int s = 0; s < stages; s++) { tc::mbar_init(&full[s], TC_PROD_THREADS); tc::mbar_init(&empty[s], 1); }
-        for (int a = 0; a < nacc; a++) { tc::mbar_init(&accf[a], 1); tc::mbar_init(&acce[a], TC_EPI_WARPS); }
-        tc::mbar_init(&opfree[0], 1);
-        tc::mbar_init(&opfree[1], 1);
+        for (int s = 0; s < a.stages; s++) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+        for (int o = 0; o < 2; o++) { tc::mbar_init(&opfull[o], TC_ASM_WARPS); tc::mbar_init(&opempty[o], 1); }
+        for (int c = 0; c < a.nacc; c++) { tc::mbar_init(&accf[c], 1); tc::mbar_init(&acce[c], TC_EPI_WARPS); }
+        tc::mbar_init(&fin, 1);
         abort_flag = 0;
+    }
+    if (tid < TC_M) {
+        const int d = tid < a.KR ? real_index_decode(tid) : 0;
+        const int n = d & 0xff, m = (d >> 8) & 0xff, pb = (d >> 16) & 1;
+        dec[tid] = tid < a.KR ? d : -1;
+        colmeta[tid] = (uint32_t)(n | (m << 4) | (pb << 8) | (tri(n, 0) << 9) | ((tid < a.KR ? 1 : 0) << 15));
     }
     if (warp == TC_MMA_WARP) { tc::tmem_alloc(&tslot, TC_TMEM_COLS); tc::tmem_relinquish(); }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = tslot;
-    const int i0 = blockIdx.x * per_cta, i1 = min(n_items, i0 + per_cta), nit = max(0, i1 - i0);
+    const uint32_t acc_col0 = 2u * (uint32_t)a.KI;   // accumulators after the two operator slots
+    const int i0 = a.block_first[blockIdx.x], nit = max(0, a.block_first[blockIdx.x + 1] - i0);
     volatile int* abort_p = &abort_flag;
 
-    if (warp >= TC_EPI_WARPS && warp < TC_MMA_WARP) {
-        // ---------------- producers
-        // Item j+1 and the source of row pt of item j+1 are loaded while item j
-        // is gathered; the 128 sources of an item go through shared memory so
-        // that no cp.async waits on a global load.  Each producer thread's
-        // copies arrive on full[s] by themselves when they land
-        // (cp.async.mbarrier.arrive.noinc), so the gather of item j+1 never
-        // waits for item j.
-        const int pt = tid - 32 * TC_EPI_WARPS, cpr = Kp / 8;
-        int cur_cls = -1, cur_slot = 0, loads[2] = {0, 0};
-        int4 item_n = nit > 0 ? items[i0] : make_int4(0, 0, 0, 0);
-        int src_n = (nit > 0 && pt < item_n.z) ? pc_src[item_n.y + pt] : -1;
-        for (int j = 0; j < nit; j++) {
-            const int s = j % stages;
-            const int4 item = item_n;
-            const int src_j = src_n;
-            if (j + 1 < nit) item_n = items[i0 + j + 1];
-            bool ok = true;
-            if (item.x != cur_cls) {
-                const int o = (nslots == 2 && cur_cls >= 0) ? cur_slot ^ 1 : 0;
-                const int n = o == 0 ? loads[0] : loads[1];
-                // the slot is released once the MMAs of the last run that used it are done
-                if (n > 0) ok = tc_wait(&opfree[o], (uint32_t)((n - 1) & 1), budget_ns, abort_p);
-                if (ok) tc_load_operator(pt, Kp, item.x, ops, B_of(o));
-                if (o == 0) loads[0]++; else loads[1]++;
-                cur_cls = item.x;
-                cur_slot = o;
+    if (warp == TC_PROD_WARP) {
+        // ---------------- producer: TMA row gathers, lane l takes rows 4l .. 4l+3.
+        // The source indices of item j + TC_SRC_AHEAD are copied into a ring
+        // in shared memory (cp.async) while item j is issued.
+        int ctr = 0;
+        bool ok = true;
+        auto prefetch_rows = [&](int j) {
+            if (j < nit) {
+                const int4 it = a.items[i0 + j];
+                int* ring = src_ring + (j % TC_SRC_RING) * TC_ROWS;
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int r = 4 * lane + u;
+                    if (r < it.z)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc::smem_u32(ring + r)),
+                                     "l"(a.src + it.y + r)
+                                     : "memory");
+                    else
+                        ring[r] = -1;   // an empty row reads as zeros
+                }
             }
-            if (ok && j >= stages) ok = tc_wait(&empty[s], (uint32_t)(((j / stages) - 1) & 1), budget_ns, abort_p);
-            src_idx[s * TC_ROWS + pt] = src_j;
-            // all producers leave together (a named barrier with an AND reduction)
-            int all_ok;
-            asm volatile(
-                "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
-                "bar.red.and.pred q, 1, %2, p;\n\tselp.b32 %0, 1, 0, q;\n\t}\n"
-                : "=r"(all_ok)
-                : "r"((int)ok), "n"(TC_PROD_THREADS)
-                : "memory");
-            if (!all_ok) break;
-            if (j + 1 < nit) src_n = pt < item_n.z ? pc_src[item_n.y + pt] : -1;
-            tc_gather(pt, Kp, cpr, src_idx + s * TC_ROWS, Ms, A_of(s), A_of(s) + abytes);
-            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::smem_u32(&full[s]))
-                         : "memory");
+            tc::cp_async_commit();   // one group per item (empty beyond the last)
+        };
+        for (int j = 0; j < TC_SRC_AHEAD; j++) prefetch_rows(j);
+        for (int j = 0; j < nit && ok; j++) {
+            asm volatile("cp.async.wait_group %0;" ::"n"(TC_SRC_AHEAD - 1) : "memory");
+            const int* ring = src_ring + (j % TC_SRC_RING) * TC_ROWS;
+            const int y[4] = {ring[4 * lane], ring[4 * lane + 1], ring[4 * lane + 2], ring[4 * lane + 3]};
+            prefetch_rows(j + TC_SRC_AHEAD);
+            for (int at = 0; at < a.nat; at++, ctr++) {
+                const int s = ctr % a.stages, use = ctr / a.stages;
+                if (use > 0) ok = tc_wait(&empty[s], (uint32_t)((use - 1) & 1), a.budget_ns, abort_p);
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                if (lane == 0) tc::mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
+                __syncwarp();
+                const uint32_t dst = tc::smem_u32(sm + (size_t)s * TC_STAGE_BYTES) + 512u * lane;
+                const uint32_t bar = tc::smem_u32(&full[s]);
+                tc::tma_gather4(dst, &tmap, at * TC_ATOM, y[0], y[1], y[2], y[3], bar);
+                tc::tma_gather4(dst + TC_TILE_BYTES, &tmap, a.KI + at * TC_ATOM, y[0], y[1], y[2], y[3], bar);
+            }
         }
-        cp_async_wait_group<0>();
+        // the copies of every stage still in flight land before the block exits
+        tc::cp_async_wait_all();
+        volatile int never = 0;
+        for (int c = max(0, ctr - a.stages); c < ctr; c++)
+            tc_wait(&full[c % a.stages], (uint32_t)((c / a.stages) & 1), a.budget_ns, &never);
     } else if (warp == TC_MMA_WARP) {
         // ---------------- MMA issue (one thread)
         if (lane == 0) {
-            const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, Kp);
-            const uint32_t sbo = (Kp / 8) * 128;
-            int cur_cls = -1, cur_slot = 0, last_a = -1;
-            uint32_t last_parity = 0;
-            int cls_n = nit > 0 ? items[i0].x : -1;
+            const uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_ROWS);
+            int ctr = 0, cur_cls = -1, slot = 1, uses[2] = {0, 0};
+            int cls_next = nit > 0 ? a.items[i0].x : -1;
             for (int j = 0; j < nit; j++) {
-                const int s = j % stages, a = j % nacc;
-                const int4 item = make_int4(cls_n, 0, 0, 0);
-                cls_n = j + 1 < nit ? items[i0 + j + 1].x : -1;   // used after this item's MMAs
-                if (item.x != cur_cls) {
-                    cur_slot = (nslots == 2 && cur_cls >= 0) ? cur_slot ^ 1 : 0;
-                    cur_cls = item.x;
+                const int cls = cls_next;
+                cls_next = j + 1 < nit ? a.items[i0 + j + 1].x : -1;
+                if (cls != cur_cls) {
+                    slot ^= 1;
+                    cur_cls = cls;
+                    if (!tc_wait(&opfull[slot], (uint32_t)(uses[slot] & 1), a.budget_ns, abort_p)) break;
+                    uses[slot]++;
                 }
-                if (!tc_wait(&full[s], (uint32_t)((j / stages) & 1), budget_ns, abort_p)) break;
-                if (j >= nacc && !tc_wait(&acce[a], (uint32_t)(((j / nacc) - 1) & 1), budget_ns, abort_p)) break;
-                // the stage was written by the producers' cp.async (generic proxy)
-                // and is read by the tensor core (async proxy)
-                tc::fence_proxy_async();
+                const int acc = j % a.nacc;
+                if (j >= a.nacc && !tc_wait(&acce[acc], (uint32_t)(((j / a.nacc) - 1) & 1), a.budget_ns, abort_p)) break;
                 tc::fence_after_sync();
-                const uint32_t ah = tc::smem_u32(A_of(s)), al = ah + (uint32_t)abytes;
-                const uint32_t bh = tc::smem_u32(B_of(cur_slot)), bl = bh + (uint32_t)bbytes;
-                const uint32_t dacc = tbase + (uint32_t)(a * Kp);
-                for (int ks = 0; ks < Kp / 16; ks++) {
-                    const uint32_t o = ks * 256;
-                    const uint64_t dah = tc::make_desc(ah + o, 128, sbo), dal = tc::make_desc(al + o, 128, sbo);
-                    const uint64_t dbh = tc::make_desc(bh + o, 128, sbo), dbl = tc::make_desc(bl + o, 128, sbo);
-                    tc::mma_bf16(dacc, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-                    tc::mma_bf16(dacc, dah, dbl, idesc, 1u);
-                    tc::mma_bf16(dacc, dal, dbh, idesc, 1u);
+                const uint32_t dt = tbase + acc_col0 + (uint32_t)(acc * TC_ROWS);
+                const uint32_t th = tbase + (uint32_t)(slot * a.KI), tl = th + (uint32_t)(a.KI / 2);
+                bool ok = true;
+                for (int at = 0; at < a.nat; at++, ctr++) {
+                    const int s = ctr % a.stages;
+                    if (!tc_wait(&full[s], (uint32_t)((ctr / a.stages) & 1), a.budget_ns, abort_p)) { ok = false; break; }
+                    tc::fence_after_sync();
+                    const uint32_t bh = tc::smem_u32(sm + (size_t)s * TC_STAGE_BYTES), bl = bh + TC_TILE_BYTES;
+#pragma unroll
+                    for (int ks = 0; ks < TC_ATOM / 16; ks++) {
+                        const uint32_t ca = (uint32_t)(8 * (4 * at + ks));
+                        const uint64_t dbh = tc::make_desc_sw128(bh + 32 * ks), dbl = tc::make_desc_sw128(bl + 32 * ks);
+                        tc::mma_bf16_ta(dt, th + ca, dbh, idesc, (at | ks) ? 1u : 0u);
+                        tc::mma_bf16_ta(dt, tl + ca, dbh, idesc, 1u);
+                        tc::mma_bf16_ta(dt, th + ca, dbl, idesc, 1u);
+                    }
+                    tc::commit(&empty[s]);
                 }
-                tc::commit(&empty[s]);
-                tc::commit(&accf[a]);
-                last_a = a;
-                last_parity = (uint32_t)((j / nacc) & 1);
-                if (j + 1 < nit && cls_n != item.x) tc::commit(&opfree[cur_slot]);
+                if (!ok) break;
+                tc::commit(&accf[acc]);
+                if (cls_next != cur_cls) tc::commit(&opempty[slot]);
             }
-            // every MMA issued here has completed before TMEM is released
-            if (last_a >= 0) {
-                volatile int never = 0;
-                tc_wait(&accf[last_a], last_parity, budget_ns, &never);
-            }
+            // every MMA issued here has completed before tensor memory is released
+            tc::commit(&fin);
+            volatile int never = 0;
+            tc_wait(&fin, 0u, a.budget_ns, &never);
         }
         __syncwarp();
-    } else {
-        // ---------------- epilogue
-        // the targets of item j+1 are loaded while item j is drained
-        const int quarter = warp & 3, part = warp >> 2, nblk = Kp / 16;
-        const int cb0 = nblk * part / 2, cb1 = nblk * (part + 1) / 2;
-        auto load_targets = [&](const int4 it, int (&tg)[2][2]) {
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int ra = 32 * quarter + 16 * h + (lane >> 2);
-                tg[h][0] = ra < it.z ? pc_tgt[it.y + ra] : -1;
-                tg[h][1] = ra + 8 < it.z ? pc_tgt[it.y + ra + 8] : -1;
-            }
+    } else if (warp >= TC_EPI_WARPS) {
+        // ---------------- assemblers: thread = output coefficient (tensor-memory lane)
+        const int q = warp - TC_EPI_WARPS, at_id = tid - 32 * TC_EPI_WARPS;
+        const int co = 32 * q + lane;
+        const int dco = dec[co];
+        const int k = dco >= 0 ? (dco & 0xff) : 0, l = dco >= 0 ? ((dco >> 8) & 0xff) : 0, pa = (dco >> 16) & 1;
+        const int Tk = tri(k, 0);
+        const float ksgn = dco < 0 ? 0.f : ((k & 1) ? -1.f : 1.f);   // a padding row stays zero
+        const float2* H = reinterpret_cast<const float2*>(hbuf);
+        const uint32_t lane_base = tbase + ((uint32_t)(32 * q) << 16);
+        // the harmonics and key of the next class run are loaded into registers
+        // while the current run is assembled
+        int run = -1, cur_cls = -1, jn = 0;
+        cplx<float> hn[2];
+        uint64_t keyn = 0;
+        auto next_run = [&](int& jj) {   // first item of the next run at or after jj: its class, or -1
+            while (jj < nit && a.items[i0 + jj].x == cur_cls) jj++;
+            return jj < nit ? a.items[i0 + jj].x : -1;
         };
-        if (stg_stride > 0) {
-            // bulk reductions: lane r owns row 32 quarter + r of the item
-            const int c0 = 16 * cb0, c1 = min(16 * cb1, (ncols + 3) & ~3);
-            float* stg = stg_all + (size_t)warp * 32 * stg_stride;
-            const int row = 32 * quarter + lane;
-            int4 item_n = nit > 1 ? items[i0 + 1] : make_int4(0, 0, 0, 0);
-            int tg = -1, tg_n = -1;
-            if (nit > 0) { const int4 it = items[i0]; tg = row < it.z ? pc_tgt[it.y + row] : -1; }
-            for (int j = 0; j < nit; j++) {
-                const int a = j % nacc;
-                if (j + 1 < nit) tg_n = row < item_n.z ? pc_tgt[item_n.y + row] : -1;
-                if (j + 2 < nit) item_n = items[i0 + j + 2];
-                const bool got = tc_wait(&accf[a], (uint32_t)((j / nacc) & 1), budget_ns, abort_p);
-                if (!__all_sync(0xffffffffu, got)) break;
-                tc::fence_after_sync();
-                tc_drain_bulk(tbase + (uint32_t)(a * Kp), quarter, cb0, cb1, c0, c1, stg_stride, ldL, tg, stg, L);
-                tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[a]);
-                tg = tg_n;
-            }
-            tc::bulk_wait_all();
-        } else {
-            int tgt[2][2], tgt_n[2][2];
-            int4 item_n = nit > 1 ? items[i0 + 1] : make_int4(0, 0, 0, 0);
-            if (nit > 0) load_targets(items[i0], tgt);
-            for (int j = 0; j < nit; j++) {
-                const int a = j % nacc;
-                if (j + 1 < nit) load_targets(item_n, tgt_n);
-                if (j + 2 < nit) item_n = items[i0 + j + 2];
-                const bool got = tc_wait(&accf[a], (uint32_t)((j / nacc) & 1), budget_ns, abort_p);
-                if (!__all_sync(0xffffffffu, got)) break;
-                tc::fence_after_sync();
-                tc_drain(tbase + (uint32_t)(a * Kp), quarter, cb0, cb1, ncols, ldL, tgt, L);
-                tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[a]);
+        auto load_class = [&](int c) {
+            if (c < 0) return;
 #pragma unroll
-                for (int h = 0; h < 2; h++) { tgt[h][0] = tgt_n[h][0]; tgt[h][1] = tgt_n[h][1]; }
+            for (int u = 0; u < 2; u++) {
+                const int e = at_id + 32 * TC_ASM_WARPS * u;
+                if (e < a.nh) hn[u] = a.harm[(size_t)c * a.nh + e];
             }
+            keyn = a.keys[c];
+        };
+        int cls = next_run(jn);
+        load_class(cls);
+        while (cls >= 0) {
+            cur_cls = cls;
+            run++;
+            const int slot = run & 1, use = run >> 1;
+            bool ok = true;
+            if (use > 0) ok = tc_wait(&opempty[slot], (uint32_t)((use - 1) & 1), a.budget_ns, abort_p);
+            // every assembler is past its last read of hbuf, and all leave together
+            if (!bar_all(1, 32 * TC_ASM_WARPS, ok)) break;
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const int e = at_id + 32 * TC_ASM_WARPS * u;
+                if (e < a.nh) hbuf[e] = hn[u];
+            }
+            int dl;
+            {
+                double dx, dy, dz;
+                class_offset(keyn, dl, dx, dy, dz);
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_ASM_WARPS) : "memory");
+            cls = next_run(jn);
+            load_class(cls);
+            const uint32_t ts = lane_base + (uint32_t)(slot * a.KI);
+            for (int ch = 0; ch < a.KI / 32; ch++) {
+                uint32_t hw[16], lw[16];
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    const float v0 = class_operator_entry(colmeta[32 * ch + 2 * i], k, l, pa, Tk, ksgn, dl, H);
+                    const float v1 = class_operator_entry(colmeta[32 * ch + 2 * i + 1], k, l, pa, Tk, ksgn, dl, H);
+                    split_pack(v0, v1, hw[i], lw[i]);
+                }
+                tc::tmem_st16(ts + (uint32_t)(16 * ch), hw);
+                tc::tmem_st16(ts + (uint32_t)(a.KI / 2 + 16 * ch), lw);
+            }
+            tc::tmem_wait_st();
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&opfull[slot]);
+        }
+    } else {
+        // ---------------- epilogue: lane = output coefficient of quarter q,
+        // columns (pairs) [64 part, 64 part + 64) of each accumulator
+        const int q = warp & 3, part = warp >> 2;
+        const int co = 32 * q + lane;
+        const bool valid = co < a.KR;
+        const int foff = valid ? real_index_offset(co) : 0;
+        const uint32_t lane_base = tbase + ((uint32_t)(32 * q) << 16) + acc_col0 + (uint32_t)(64 * part);
+        auto load_targets = [&](int j, int& t0, int& t1) {
+            const int4 it = a.items[i0 + j];
+            const int r0 = 64 * part + lane, r1 = r0 + 32;
+            t0 = r0 < it.z ? a.tgt[it.y + r0] : -1;
+            t1 = r1 < it.z ? a.tgt[it.y + r1] : -1;
+        };
+        int tg0 = -1, tg1 = -1, ng0 = -1, ng1 = -1;
+        if (nit > 0) load_targets(0, tg0, tg1);
+        for (int j = 0; j < nit; j++) {
+            const int acc = j % a.nacc;
+            if (j + 1 < nit) load_targets(j + 1, ng0, ng1);
+            const bool got = tc_wait(&accf[acc], (uint32_t)((j / a.nacc) & 1), a.budget_ns, abort_p);
+            if (!__all_sync(0xffffffffu, got)) break;
+            tc::fence_after_sync();
+            uint32_t v[4][16];
+            const uint32_t ta = lane_base + (uint32_t)(acc * TC_ROWS);
+#pragma unroll
+            for (int c = 0; c < 4; c++) tc::tmem_ld16_nowait(ta + 16 * c, v[c]);
+            tc::tmem_wait_ld();
+            // the accumulator is in registers: hand it back to the MMA thread
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[acc]);
+#pragma unroll
+            for (int c = 0; c < 4; c++)
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    const int col = 16 * c + i;
+                    const int t = __shfl_sync(0xffffffffu, col < 32 ? tg0 : tg1, col & 31);
+                    if (t >= 0 && valid) atomicAdd(a.L + (size_t)t * a.ldL + foff, __uint_as_float(v[c][i]));
+                }
+            tg0 = ng0;
+            tg1 = ng1;
         }
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (tid == 0 && abort_flag) atomicExch(status, 1);
+    if (tid == 0 && abort_flag) atomicExch(a.status, 1);
     if (warp == TC_MMA_WARP) tc::tmem_dealloc(tbase, TC_TMEM_COLS);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the library
+// does not link the driver API)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// TMA map of the split multipole table: ncell rows of 2 KI bf16 (hi | lo),
+// read in boxes of one row x 64 coefficients with the 128-byte swizzle
+static int encode_split_map(fmm_tree* t) {
+    const int KI = tc_kin(t->prm.p);
+    auto enc = tensor_map_encoder();
+    if (!enc) { fmm_set_error("tensor-core M2L: cuTensorMapEncodeTiled is unavailable"); return FMM_ERR_CUDA; }
+    const cuuint64_t gdim[2] = {(cuuint64_t)(2 * KI), (cuuint64_t)t->ncell};
+    const cuuint64_t gstride[1] = {(cuuint64_t)(4 * KI)};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_ATOM, 1u}, estride[2] = {1u, 1u};
+    const CUresult r = enc(&t->tc_tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, t->d.tc_msplit, gdim, gstride, box,
+                           estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { fmm_set_error("tensor-core M2L: cuTensorMapEncodeTiled failed (%d)", (int)r); return FMM_ERR_CUDA; }
+    t->tc_tmap_ok = true;
+    return FMM_OK;
 }
 
 int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st) {
     TreeDev& d = t->d;
-    const int p = t->prm.p, Kp = tc_kpad(p), K2 = 2 * ntri(p), KS = kstride(p);
+    const int p = t->prm.p, KR = tc_kreal(p), KI = tc_kin(p), KS = kstride(p), nh = ntri(2 * p);
     if (t->tc_nitems == 0) return FMM_OK;
-    const int64_t ne = (int64_t)t->ncell * Kp;
-    __nv_bfloat16* msplit = (__nv_bfloat16*)d.tc_msplit;
-    const __nv_bfloat16* ops = (const __nv_bfloat16*)d.tc_ops;
-    k_split_multipoles<<<nblk(ne, 256), 256, 0, st>>>(t->ncell, K2, KS, Kp, M, msplit);
+    int rc;
+    if (!t->tc_tmap_ok && (rc = encode_split_map(t))) return rc;
+    const int64_t ne = (int64_t)t->ncell * KI;
+    k_split_real<<<nblk(ne, 256), 256, 0, st>>>(t->ncell, KR, KI, 2 * KS, M, (__nv_bfloat16*)d.tc_msplit);
     count_launch(t);
     int dev = 0, optin = 0;
     FMM_CUDA_TRY(cudaGetDevice(&dev));
     FMM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     cudaFuncAttributes fa{};
     FMM_CUDA_TRY(cudaFuncGetAttributes(&fa, k_m2l_tc));
-    const size_t cap = (size_t)optin - fa.sharedSizeBytes - 128;  // slack for the 128-byte alignment
-    const TcShape sh = tc_shape(Kp, cap, TC_BULK_DRAIN);
-    if (sh.stages < 2 || sh.nacc < 2) {
-        fmm_set_error("tensor-core M2L: Kp = %d does not fit shared memory", Kp);
+    const size_t hbytes = (size_t)nh * sizeof(cplx<float>);
+    const size_t cap = (size_t)optin - fa.sharedSizeBytes - 1024 - hbytes;   // 1024: alignment of the stages
+    const int stages = (int)std::min<size_t>(TC_MAX_STAGES, cap / TC_STAGE_BYTES);
+    const int nacc = std::min(TC_MAX_ACC, (TC_TMEM_COLS - 2 * KI) / TC_ROWS);
+    if (stages < 2 || nacc < 1) {
+        fmm_set_error("tensor-core M2L: p = %d does not fit shared or tensor memory", p);
         return FMM_ERR_ARG;
     }
-    // at least half of the SM's shared memory, so that one block (and its 512
-    // TMEM columns) runs per SM
-    const size_t smem = std::max(sh.smem, (size_t)optin / 2 + 1024);
+    const size_t smem = (size_t)stages * TC_STAGE_BYTES + hbytes + 1024;
     FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int grid = (int)std::min<int64_t>(t->tc_nitems, (int64_t)t->num_sms);
-    int per_cta = (int)((t->tc_nitems + grid - 1) / grid);
-    grid = (int)((t->tc_nitems + per_cta - 1) / per_cta);
+    const int grid = t->tc_nblocks;
     if (t->ev_ops) {
-        // the class operators are built on the side stream; under stream capture
+        // the class harmonics are built on a side stream; under stream capture
         // the wait enters the graph as an external event wait node
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         FMM_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
         FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_ops,
                                          cs == cudaStreamCaptureStatusNone ? cudaEventWaitDefault : cudaEventWaitExternal));
     }
+    TcArgs a;
+    a.p = p; a.KR = KR; a.KI = KI; a.nat = KI / TC_ATOM; a.stages = stages; a.nacc = nacc; a.ldL = 2 * KS;
+    a.nh = nh; a.block_first = d.tc_block_first;
+    a.items = d.tc_items; a.src = d.tc_src; a.tgt = d.tc_tgt; a.keys = d.tc_keys;
+    a.harm = (const cplx<float>*)d.tc_harm; a.L = L; a.status = d.status; a.budget_ns = t->prm.timeout_ns;
     stage_begin(t, FMM_STAGE_M2L_TC, st);
-    k_m2l_tc<<<grid, TC_THREADS, smem, st>>>(Kp, sh.stages, sh.nslots, sh.nacc, sh.stg_stride, K2, 2 * KS, (int)t->tc_nitems,
-                                              per_cta, d.tc_items, d.tc_src, d.tc_tgt, ops, msplit, L, d.status,
-                                              t->prm.timeout_ns);
+    k_m2l_tc<<<grid, TC_THREADS, smem, st>>>(t->tc_tmap, a);
     count_launch(t);
     stage_end(t, FMM_STAGE_M2L_TC, st);
     FMM_CUDA_TRY(cudaGetLastError());

@@ -28,6 +28,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};
+int g_noalloc_sms[kMaxDevices] = {};   // multiprocessors of each device, read with the address
 
 constexpr int NA_THREADS = 128;
 constexpr int NA_TILE = 512;
@@ -89,8 +90,9 @@ __global__ void k_na_finish(int64_t n, const double4_32a* __restrict__ xq, const
 }
 
 // Device address of the scratch array for the current device, looked up once
-// per device (the symbol's host-side name is not a device address).
-int scratch_for_current_device(void** out) {
+// per device (the symbol's host-side name is not a device address), and the
+// device's multiprocessor count, read at the same time.
+int scratch_for_current_device(void** out, int* sms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { fmm_set_error("fmm_direct_noalloc: cudaGetDevice: %s", cudaGetErrorString(e)); return FMM_ERR_CUDA; }
@@ -103,21 +105,29 @@ int scratch_for_current_device(void** out) {
             fmm_set_error("fmm_direct_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
             return FMM_ERR_CUDA;
         }
+        int nsm = 0;
+        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess || nsm < 1) {
+            fmm_set_error("fmm_direct_noalloc: cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+            return FMM_ERR_CUDA;
+        }
         g_noalloc_ptr[dev] = p;
+        g_noalloc_sms[dev] = nsm;
     }
     *out = g_noalloc_ptr[dev];
+    *sms = g_noalloc_sms[dev];
     return FMM_OK;
 }
 
 template <typename T>
 int direct_noalloc_typed(int64_t n, const T* pos, const T* q, T* phi, T* force, int field, cudaStream_t st,
-                         void* scratch) {
+                         void* scratch, int sms) {
     double4_32a* xq = (double4_32a*)scratch;
     double* acc = (double*)((char*)scratch + (size_t)kNoAllocMaxN * sizeof(double4_32a));
     unsigned nb = (unsigned)((n + NA_THREADS - 1) / NA_THREADS);
     k_na_stage<T><<<nb, NA_THREADS, 0, st>>>(n, pos, q, xq, acc);
-    // spread the sources over enough slices to give every SM work
-    int64_t splits = std::max<int64_t>(1, std::min<int64_t>(64, (4 * 152 + nb - 1) / nb));
+    // spread the sources over enough slices to give every SM four blocks
+    int64_t splits = std::max<int64_t>(1, std::min<int64_t>(64, (4 * (int64_t)sms + nb - 1) / nb));
     int64_t slice = (n + splits - 1) / splits;
     splits = (n + slice - 1) / slice;
     k_na_p2p<<<dim3(nb, (unsigned)splits), NA_THREADS, 0, st>>>(n, slice, xq, acc);
@@ -141,15 +151,16 @@ extern "C" int fmm_direct_noalloc(int64_t n, const void* pos, const void* q, voi
     if (n > 0 && (!pos || !q)) { fmm_set_error("fmm_direct_noalloc: pos and q must not be NULL"); return FMM_ERR_ARG; }
     if (n == 0) return FMM_OK;
     void* scratch = nullptr;
-    int rc = scratch_for_current_device(&scratch);
+    int sms = 0;
+    int rc = scratch_for_current_device(&scratch, &sms);
     if (rc) return rc;
     int field = (flags & FMM_OUT_FIELD) ? 1 : 0;
     cudaStream_t st = (cudaStream_t)stream;
     if (dtype == FMM_F64)
         return direct_noalloc_typed<double>(n, (const double*)pos, (const double*)q, (double*)phi, (double*)force,
-                                            field, st, scratch);
+                                            field, st, scratch, sms);
     return direct_noalloc_typed<float>(n, (const float*)pos, (const float*)q, (float*)phi, (float*)force, field, st,
-                                       scratch);
+                                       scratch, sms);
 }
 
 extern "C" int64_t fmm_direct_noalloc_max_n(void) { return kNoAllocMaxN; }

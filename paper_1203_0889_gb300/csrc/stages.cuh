@@ -207,16 +207,15 @@ __device__ void shift_cell_block(int p, int c, int kind, const int32_t* __restri
 
 // ---------------------------------------------------------------- M2L
 // One source slot (a half-warp) accumulates, into acc[r], the outputs
-// j = hl + 16 r of target t over the sources e = s0 + slot, s0 + slot + nslot, ...
+// j = hl + 16 r of target t over the list entries e = s0 + slot, s0 + slot + nslot, ... < s1
 // Ms / Is: the slot's shared scratch (ntri(p) and ntri(2p) entries).
 // The caller combines the slots and applies the (-1)^k sign.
 template <typename T, int RMAX, bool COH>
-__device__ void m2l_slot(int p, int t, int slot, int nslot, int hl, const int64_t* __restrict__ start,
-                         const int32_t* __restrict__ src, const double4_32a* __restrict__ centre,
-                         const cplx<T>* __restrict__ M, cplx<T>* Ms, cplx<T>* Is, const int* kk, const int* ll,
-                         cplx<T>* acc) {
+__device__ void m2l_range(int p, int t, int64_t s0, int64_t s1, int slot, int nslot, int hl,
+                          const int32_t* __restrict__ src, const double4_32a* __restrict__ centre,
+                          const cplx<T>* __restrict__ M, cplx<T>* Ms, cplx<T>* Is, const int* kk, const int* ll,
+                          cplx<T>* acc) {
     const int K = ntri(p), KS = kstride(p);
-    const int64_t s0 = start[t], s1 = start[t + 1];
     const double4_32a ct = centre[t];
     const double invht = 1.0 / ct.w;
     // every slot of the warp runs the same number of rounds (warp-synchronous scratch)
@@ -271,6 +270,15 @@ __device__ void m2l_slot(int p, int t, int slot, int nslot, int hl, const int64_
         }
         __syncwarp();
     }
+}
+
+// the whole list of target t: sources start[t] .. start[t + 1]
+template <typename T, int RMAX, bool COH>
+__device__ __forceinline__ void m2l_slot(int p, int t, int slot, int nslot, int hl, const int64_t* __restrict__ start,
+                                         const int32_t* __restrict__ src, const double4_32a* __restrict__ centre,
+                                         const cplx<T>* __restrict__ M, cplx<T>* Ms, cplx<T>* Is, const int* kk,
+                                         const int* ll, cplx<T>* acc) {
+    m2l_range<T, RMAX, COH>(p, t, start[t], start[t + 1], slot, nslot, hl, src, centre, M, Ms, Is, kk, ll, acc);
 }
 
 template <int RMAX>

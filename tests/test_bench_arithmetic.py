@@ -35,7 +35,7 @@ def test_kernel_rooflines_arithmetic():
     ex = _export(ref)
     pairs = bench.p2p_pairs(ex)
     K = (bench.P + 1) ** 2
-    kp = ((bench.P + 1) * (bench.P + 2) + 15) // 16 * 16
+    ki = (K + 63) // 64 * 64
     info = types.SimpleNamespace(tc_pairs=len(ref.m2l), tc_items=(len(ref.m2l) + 127) // 128)
     stage_ms = {"p2p": 2.0, "m2l_tc": 4.0, "m2l": 4.5}
     roofs = {r["kernel"]: r for r in bench.kernel_rooflines(stage_ms, ex, 3, 152, info)}
@@ -46,7 +46,7 @@ def test_kernel_rooflines_arithmetic():
     tc = roofs["k_m2l_tc"]
     assert np.isclose(tc["achieved"], len(ref.m2l) * 2.0 * K * K / 4e-3 / 1e12)
     assert np.isclose(tc["frac"], tc["achieved"] / tc["peak"])
-    assert np.isclose(tc["issued_frac"] * tc["peak"], info.tc_items * 128 * 2.0 * kp * kp * 3 / 4e-3 / 1e12)
+    assert np.isclose(tc["issued_frac"] * tc["peak"], info.tc_items * 3 * 2.0 * 128 * 128 * ki / 4e-3 / 1e12)
     # FP64 and FP32 task-queue forms: one entry, M2L and P2P flops over the queue time
     q = bench.kernel_rooflines({"queue": 10.0}, ex, 0, 152)
     assert len(q) == 1 and q[0]["kernel"] == "k_queue"

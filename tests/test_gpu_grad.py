@@ -88,3 +88,22 @@ def test_backward_needs_field_tree():
     with pytest.raises(fmm.FMMError) as e:
         t.backward(q, q, torch.zeros((1000, 3), dtype=torch.float64, device=dev))
     assert e.value.code == fmm.FMM_ERR_STATE
+
+
+def test_function_follows_its_positions():
+    """FMMFunction evaluates at the positions it is given: a tensor other than the
+    tree's own (here the particles moved by a small shift) is loaded into the
+    fixed tree first; a tensor of the wrong shape is refused."""
+    fmm, torch, wl, pos, q, w, tree = _setup(4096, 8, 0)
+    moved = pos + 1e-4 * float(tree.info().side)
+    phi = fmm.FMMFunction.apply(moved.clone().requires_grad_(True), q, tree)
+    ref = fmm.build_tree(pos, p=8, leaf_size=64, theta=0.5, precision=0, flags=fmm.OUT_FIELD)
+    ref.set_positions(moved)
+    phi_ref, _ = ref.evaluate(q)
+    assert torch.equal(phi.detach(), phi_ref)
+    # back at the tree's own positions: the same values as a plain evaluation
+    phi0 = fmm.FMMFunction.apply(pos.clone().requires_grad_(True), q, tree)
+    ref.set_positions(pos)
+    assert torch.equal(phi0.detach(), ref.evaluate(q)[0])
+    with pytest.raises(ValueError):
+        fmm.FMMFunction.apply(pos[:100], q, tree)

@@ -14,6 +14,9 @@ from tests.gpu_common import gpu_eval, gpu_tree, oracle_phi_force, torch_dev
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
+# a few times the error measured on these workloads: FP32 P2P with FP64
+# expansions about 3e-7, all-FP32 about 1e-6, tensor-core M2L 2e-6 to 5e-6
+TIGHT = {1: 5e-6, 2: 1e-5, 3: 2e-5}
 
 
 @pytest.mark.parametrize("name,n,p,leaf,theta", [
@@ -47,9 +50,14 @@ def test_reduced_precision_within_bar(prec, name, n, p, leaf, theta):
     t = gpu_tree(wl.pos, p=p, leaf_size=leaf, theta=theta, precision=prec)
     for dt in ("f64", "f32"):
         torch, _ = torch_dev()
-        phi, f = gpu_eval(t, wl.q, dtype=torch.float64 if dt == "f64" else torch.float32)
-        assert O.rel_l2(phi, ref_phi) <= 1e-4
-        assert O.rel_l2(f, ref_f) <= 1e-4
+        q = wl.q if dt == "f64" else wl.q.astype(np.float32).astype(np.float64)
+        if dt == "f32":
+            ref_phi, ref_f, _ = oracle_phi_force(wl.pos, q, p, leaf, theta)
+        phi, f = gpu_eval(t, q, dtype=torch.float64 if dt == "f64" else torch.float32)
+        e_phi, e_f = O.rel_l2(phi, ref_phi), O.rel_l2(f, ref_f)
+        assert e_phi <= 1e-4 and e_f <= 1e-4
+        # the measured error, a few times below the stated bar
+        assert e_phi <= TIGHT[prec] and e_f <= TIGHT[prec], (e_phi, e_f)
 
 
 @pytest.mark.parametrize("name,n,p,theta", [("plummer", 60000, 8, 0.4), ("uniform", 40000, 4, 0.5),
