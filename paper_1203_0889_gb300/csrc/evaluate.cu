@@ -416,6 +416,9 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st) {
         char* ms = nullptr;
         if ((rc = dev_alloc(&ms, (size_t)t->ncell * 2 * tc_kin(t->prm.p) * 2, t, st))) return rc;
         d.tc_msplit = ms;
+        char* lr = nullptr;
+        if ((rc = dev_alloc(&lr, (size_t)t->ncell * 128 * sizeof(float), t, st))) return rc;
+        d.tc_lr = lr;
     }
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;

@@ -155,7 +155,8 @@ struct TreeDev {
     int4* p2p_rec = nullptr;      // [np2p] (first, count, particle offset within the target's sources, source)
     // tensor-core M2L (FMM_PREC_MIXED_TC): pairs grouped by translation class
     int4* tc_items = nullptr;     // [tc_nitems] (class, first pair, rows, -)
-    int32_t* tc_block_first = nullptr;  // [tc_nblocks + 1] item range of each tensor-core block
+    int32_t* tc_block_first = nullptr;  // [tc_nblocks + 1] range of each tensor-core block in tc_item_list
+    int32_t* tc_item_list = nullptr;    // [tc_nitems] work items, grouped by tensor-core block
     void* tc_harm = nullptr;      // [nclass][ntri(2p)] cplx<float>: irregular harmonics of each class offset
     uint64_t* tc_keys = nullptr;  // [nclass] class keys, in class order
     int32_t* tc_tgt = nullptr;    // [nm2l] targets in class order (class-less pairs last)
@@ -163,6 +164,7 @@ struct TreeDev {
     int64_t* rem_start = nullptr; // CSR of the class-less pairs by target
     int2* rem_chunks = nullptr;   // (target, first entry) chunks of at most M2L_CHUNK class-less pairs
     void* tc_msplit = nullptr;    // [ncell][hi | lo][KI] bf16 multipoles in the real basis (tc_kin)
+    void* tc_lr = nullptr;        // [ncell][128] FP32 tensor-core M2L results in the real basis
     Geometry* geom = nullptr;     // [nsys] root cube of each system
     int64_t* sys_off = nullptr;   // [nsys+1] particle offsets of the systems
     float* cu2f = nullptr;        // [ncell] side/2^22 of the cell's system (FP32 P2P offsets)

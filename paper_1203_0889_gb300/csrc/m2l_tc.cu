@@ -84,42 +84,112 @@ __global__ void k_class_keys(int64_t np, const int2* __restrict__ pairs, const i
     idx[e] = (int32_t)e;
 }
 
-// per class: number of 128-row work items
-__global__ void k_class_tiles(int nclass, const int32_t* counts, int32_t* tiles) {
+// per segment: number of 128-row work items
+__global__ void k_class_tiles(int nseg, const int32_t* counts, int32_t* tiles) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < nclass) tiles[c] = (counts[c] + TC_ROWS - 1) / TC_ROWS;
+    if (c < nseg) tiles[c] = (counts[c] + TC_ROWS - 1) / TC_ROWS;
 }
 
-__global__ void k_emit_items(int nclass, const int32_t* counts, const int32_t* class_first,
-                             const int32_t* tile_first, int4* items) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nclass) return;
-    int n = counts[c], f = class_first[c], w = tile_first[c];
-    for (int r = 0; r < n; r += TC_ROWS) items[w++] = make_int4(c, f + r, min(TC_ROWS, n - r), 0);
+// Spatial blocks of the tensor-core work: the octant at level TC_BLOCK_LEVEL
+// of the target cell.  Work items are ordered by (spatial block, class), and
+// every block of the kernel takes its share of each spatial block in turn, so
+// that at any time the SMs gather sources and reduce into targets of one
+// region of the tree.  Measured on 4M clustered particles at level 1 (8
+// blocks): DRAM traffic of the kernel fell from 24 to 0.9 GB but its time did
+// not (the gathers and reductions are bound per SM, not by DRAM), and the
+// extra sort cost 2.3 ms of build, so one block (level 0, no re-sort) is used.
+constexpr int TC_BLOCK_LEVEL = 0, TC_NSPATIAL = 1 << (3 * TC_BLOCK_LEVEL);
+__device__ __forceinline__ int spatial_block(int level, uint64_t ckey) {
+    return level >= TC_BLOCK_LEVEL ? (int)(ckey >> (3 * (level - TC_BLOCK_LEVEL)))
+                                   : (int)(ckey << (3 * (TC_BLOCK_LEVEL - level)));
 }
 
-// Partition of the work items over the blocks of the tensor-core kernel by
-// cost: an item costs one unit, plus TC_RUN_COST when it starts a class run
-// (the block assembles that class's operator).  Item ranges stay contiguous.
-constexpr int TC_RUN_COST = 4;
+// sort key of position i of `order` (the kept classes' pairs in class order):
+// spatial block of the target << cbits | class
+__global__ void k_segment_keys(int64_t ntc, int nclass, int cbits, const int32_t* __restrict__ cfirst,
+                               const int32_t* __restrict__ order, const int2* __restrict__ pairs,
+                               const int32_t* __restrict__ level, const uint64_t* __restrict__ ckey, int32_t* key) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ntc) return;
+    int lo = 0, hi = nclass;   // last class with cfirst <= i
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (cfirst[mid] <= i) lo = mid; else hi = mid;
+    }
+    const int t = pairs[order[i]].x;
+    key[i] = (spatial_block(level[t], ckey[t]) << cbits) | lo;
+}
+
+// work items of 128 pairs per segment (run of equal block and class):
+// (class, first pair, rows, spatial block)
+__global__ void k_emit_items(int nseg, int cbits, const int32_t* __restrict__ segkey, const int32_t* __restrict__ segc,
+                             const int32_t* __restrict__ segf, const int32_t* __restrict__ tile_first, int4* items) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nseg) return;
+    const int n = segc[g], f = segf[g], cls = segkey[g] & ((1 << cbits) - 1), blk = segkey[g] >> cbits;
+    int w = tile_first[g];
+    for (int r = 0; r < n; r += TC_ROWS) items[w++] = make_int4(cls, f + r, min(TC_ROWS, n - r), blk);
+}
+
+// Cost of each work item for splitting the work over the kernel's blocks: one
+// unit, plus TC_RUN_COST when the item starts a class run (its block assembles
+// the operator of that class).
+constexpr int TC_RUN_COST = 2;
 __global__ void k_item_cost(int64_t nitems, const int4* __restrict__ items, int32_t* cost) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nitems) return;
     cost[i] = 1 + ((i == 0 || items[i].x != items[i - 1].x) ? TC_RUN_COST : 0);
 }
-// first[b] = first item of block b: the first item whose inclusive cost prefix
-// exceeds b / nb of the total; first[nb] = nitems
-__global__ void k_block_ranges(int64_t nitems, const int32_t* __restrict__ prefix, int nb, int32_t* first) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b > nb) return;
-    if (b == 0 || b == nb) { first[b] = b == 0 ? 0 : (int32_t)nitems; return; }
-    const int64_t target = (int64_t)prefix[nitems - 1] * b / nb;
-    int64_t lo = 0, hi = nitems;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (prefix[mid] > target) hi = mid; else lo = mid + 1;
+
+// One block of threads: kernel block k gets, from every spatial block b (items
+// [bs_b, bs_{b+1})), the contiguous share whose inclusive cost prefix falls in
+// (k / nb, (k + 1) / nb] of that spatial block's cost; list[first[k] ..
+// first[k + 1]) holds those items, spatial block after spatial block.
+__global__ void k_block_lists(int64_t nitems, const int4* __restrict__ items, const int32_t* __restrict__ pre, int nb,
+                              int32_t* list, int32_t* first) {
+    __shared__ int32_t bs[TC_NSPATIAL + 1];
+    __shared__ int32_t off[257];
+    const int k = threadIdx.x;
+    if (k <= TC_NSPATIAL) {   // first item of spatial block k
+        int64_t lo = 0, hi = nitems;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (items[mid].w < k) lo = mid + 1; else hi = mid;
+        }
+        bs[k] = (int32_t)lo;
     }
-    first[b] = (int32_t)lo;
+    __syncthreads();
+    auto bound = [&](int b, int kk) -> int32_t {   // first item of block kk's share of spatial block b
+        const int32_t i0 = bs[b], i1 = bs[b + 1];
+        if (kk <= 0 || i1 <= i0) return i0;
+        if (kk >= nb) return i1;
+        const int64_t base = i0 > 0 ? pre[i0 - 1] : 0, tot = (int64_t)pre[i1 - 1] - base;
+        const int64_t target = base + tot * kk / nb;
+        int32_t lo = i0, hi = i1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (pre[mid] > target) hi = mid; else lo = mid + 1;
+        }
+        return lo;
+    };
+    int32_t len = 0;
+    if (k < nb)
+        for (int b = 0; b < TC_NSPATIAL; b++) len += bound(b, k + 1) - bound(b, k);
+    if (k < nb) off[k + 1] = len;
+    __syncthreads();
+    if (k == 0) {
+        off[0] = 0;
+        for (int j = 1; j <= nb; j++) off[j] += off[j - 1];
+    }
+    __syncthreads();
+    if (k <= nb) first[k] = off[k];
+    if (k < nb) {
+        int32_t pos = off[k];
+        for (int b = 0; b < TC_NSPATIAL; b++) {
+            const int32_t e0 = bound(b, k), e1 = bound(b, k + 1);
+            for (int32_t i = e0; i < e1; i++) list[pos++] = i;
+        }
+    }
 }
 
 __global__ void k_gather_pairs(int64_t np, const int32_t* __restrict__ order, const int2* __restrict__ pairs,
@@ -275,53 +345,94 @@ __global__ void k_class_harmonics(int p, int nclass, const uint64_t* __restrict_
 // Work items and class harmonics of nclass classes with sizes counts[] and
 // keys ukeys[] (both in class order); cfirst[c] receives the first pair of
 // class c.
-static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const int32_t* counts, int32_t* cfirst,
-                        int64_t* items_out, cudaStream_t st) {
+static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const int32_t* counts, int32_t* order,
+                        int64_t ntc, const int2* pairs, int64_t* items_out, cudaStream_t st) {
     TreeDev& d = t->d;
     int rc;
     const int p = t->prm.p;
     *items_out = 0;
     if (nclass == 0) return FMM_OK;
-    int32_t *tiles = nullptr, *tfirst = nullptr;
-    if ((rc = dev_alloc(&tiles, (size_t)nclass + 1, nullptr, st))) return rc;
-    if ((rc = dev_alloc(&tfirst, (size_t)nclass + 1, nullptr, st))) return rc;
-    size_t tb = 0;
+    int cbits = 1;
+    while ((1 << cbits) < nclass) cbits++;
+    const int kbits = cbits + 3 * TC_BLOCK_LEVEL;
+    // segments: runs of equal (spatial block, class); with one spatial block the
+    // pairs are in class order already and the segments are the classes
+    int32_t *cfirst = nullptr, *k0 = nullptr, *k1 = nullptr, *o1 = nullptr, *segc = nullptr, *segf = nullptr;
+    int32_t *tiles = nullptr, *tfirst = nullptr, *nseg_d = nullptr;
+    size_t tb = 0, tb2 = 0;
     char* tmp = nullptr;
-    cub::DeviceScan::ExclusiveSum(nullptr, tb, counts, cfirst, nclass, st);
-    if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
-    FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, counts, cfirst, nclass, st));
-    k_class_tiles<<<nblk(nclass, 256), 256, 0, st>>>(nclass, counts, tiles);
-    FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, tiles, tfirst, nclass, st));
+    int32_t nseg = 0;
+    if (TC_NSPATIAL == 1) {
+        nseg = nclass;
+        if ((rc = dev_alloc(&k0, (size_t)nclass, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&segc, (size_t)nclass, nullptr, st))) return rc;
+        k_iota32<<<nblk(nclass, 256), 256, 0, st>>>(nclass, k0);
+        FMM_CUDA_TRY(cudaMemcpyAsync(segc, counts, sizeof(int32_t) * nclass, cudaMemcpyDeviceToDevice, st));
+        cub::DeviceScan::ExclusiveSum(nullptr, tb, segc, segc, nclass, st);
+        if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
+        count_launch(t);
+    } else {
+        // the kept classes' pairs in (spatial block of the target, class) order,
+        // stable, so each class keeps its target order within a block
+        if ((rc = dev_alloc(&cfirst, (size_t)nclass, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&k0, (size_t)ntc, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&k1, (size_t)ntc, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&o1, (size_t)ntc, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&segc, (size_t)ntc, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&nseg_d, 1, nullptr, st))) return rc;
+        cub::DeviceScan::ExclusiveSum(nullptr, tb, counts, cfirst, nclass, st);
+        cub::DeviceRadixSort::SortPairs(nullptr, tb2, k0, k1, order, o1, ntc, 0, kbits, st);
+        tb = std::max(tb, tb2);
+        cub::DeviceRunLengthEncode::Encode(nullptr, tb2, k1, k0, segc, nseg_d, ntc, st);
+        tb = std::max(tb, tb2);
+        if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
+        FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, counts, cfirst, nclass, st));
+        k_segment_keys<<<nblk(ntc, 256), 256, 0, st>>>(ntc, nclass, cbits, cfirst, order, pairs, d.level, d.ckey, k0);
+        FMM_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tb, k0, k1, order, o1, ntc, 0, kbits, st));
+        FMM_CUDA_TRY(cudaMemcpyAsync(order, o1, sizeof(int32_t) * ntc, cudaMemcpyDeviceToDevice, st));
+        FMM_CUDA_TRY(cub::DeviceRunLengthEncode::Encode(tmp, tb, k1, k0, segc, nseg_d, ntc, st));
+        count_launch(t, 4);
+        FMM_CUDA_TRY(cudaMemcpyAsync(&nseg, nseg_d, 4, cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    if ((rc = dev_alloc(&segf, (size_t)nseg, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&tiles, (size_t)nseg, nullptr, st))) return rc;
+    if ((rc = dev_alloc(&tfirst, (size_t)nseg, nullptr, st))) return rc;
+    FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, segc, segf, nseg, st));
+    k_class_tiles<<<nblk(nseg, 256), 256, 0, st>>>(nseg, segc, tiles);
+    FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, tiles, tfirst, nseg, st));
     count_launch(t, 3);
-    cudaFreeAsync(tmp, st);
     int32_t lt = 0, lf = 0;
-    FMM_CUDA_TRY(cudaMemcpyAsync(&lt, tiles + nclass - 1, 4, cudaMemcpyDeviceToHost, st));
-    FMM_CUDA_TRY(cudaMemcpyAsync(&lf, tfirst + nclass - 1, 4, cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(&lt, tiles + nseg - 1, 4, cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(&lf, tfirst + nseg - 1, 4, cudaMemcpyDeviceToHost, st));
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
     const int64_t h_items = (int64_t)lt + lf;
     if ((rc = dev_alloc(&d.tc_items, (size_t)h_items, t, st))) return rc;
-    k_emit_items<<<nblk(nclass, 256), 256, 0, st>>>(nclass, counts, cfirst, tfirst, d.tc_items);
+    k_emit_items<<<nblk(nseg, 256), 256, 0, st>>>(nseg, cbits, k0, segc, segf, tfirst, d.tc_items);
     count_launch(t);
-    // block ranges of the tensor-core kernel (one block per SM), balanced by cost
+    // each kernel block's share of every spatial block, balanced by cost
     {
-        const int nb = (int)std::min<int64_t>(h_items, (int64_t)t->num_sms);
+        const int nb = (int)std::min<int64_t>(std::min<int64_t>(h_items, (int64_t)t->num_sms), 255);
         int32_t *cost = nullptr, *pre = nullptr;
         if ((rc = dev_alloc(&cost, (size_t)h_items, nullptr, st))) return rc;
         if ((rc = dev_alloc(&pre, (size_t)h_items, nullptr, st))) return rc;
         if ((rc = dev_alloc(&d.tc_block_first, (size_t)nb + 1, t, st))) return rc;
+        if ((rc = dev_alloc(&d.tc_item_list, (size_t)h_items, t, st))) return rc;
         k_item_cost<<<nblk(h_items, 256), 256, 0, st>>>(h_items, d.tc_items, cost);
         size_t sb = 0;
         char* stmp = nullptr;
         cub::DeviceScan::InclusiveSum(nullptr, sb, cost, pre, h_items, st);
         if ((rc = dev_alloc(&stmp, sb, nullptr, st))) return rc;
         FMM_CUDA_TRY(cub::DeviceScan::InclusiveSum(stmp, sb, cost, pre, h_items, st));
-        k_block_ranges<<<nblk(nb + 1, 256), 256, 0, st>>>(h_items, pre, nb, d.tc_block_first);
+        k_block_lists<<<1, 256, 0, st>>>(h_items, d.tc_items, pre, nb, d.tc_item_list, d.tc_block_first);
         count_launch(t, 3);
         cudaFreeAsync(stmp, st);
         cudaFreeAsync(cost, st);
         cudaFreeAsync(pre, st);
         t->tc_nblocks = nb;
     }
+    cudaFreeAsync(tmp, st); cudaFreeAsync(cfirst, st); cudaFreeAsync(k0, st); cudaFreeAsync(k1, st);
+    cudaFreeAsync(o1, st); cudaFreeAsync(segc, st); cudaFreeAsync(segf, st); cudaFreeAsync(nseg_d, st);
     // harmonics: on the side stream, so that they overlap the rest of the
     // build and the upward pass; the tensor-core M2L waits for ev_ops
     const int nh = ntri(2 * p);
@@ -561,7 +672,7 @@ static int classes_by_hash(fmm_tree* t, const int2* pairs, bool* done, cudaStrea
     if ((rc = drop_small_classes(t, np, idx1, nclass, skeys, counts, ntc, st))) return rc;
     const int64_t nrem = np - ntc;
     int64_t h_items = 0;
-    if ((rc = emit_classes(t, nclass, skeys, counts, cfirst, &h_items, st))) return rc;
+    if ((rc = emit_classes(t, nclass, skeys, counts, idx1, ntc, pairs, &h_items, st))) return rc;
     if ((rc = dev_alloc(&d.tc_tgt, (size_t)np, t, st))) return rc;
     if ((rc = dev_alloc(&d.tc_src, (size_t)np, t, st))) return rc;
     k_gather_pairs<<<nblk(np, 256), 256, 0, st>>>(np, idx1, pairs, d.tc_tgt, d.tc_src);
@@ -642,7 +753,7 @@ int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st) {
     int32_t* cfirst = nullptr;
     if ((rc = dev_alloc(&cfirst, (size_t)nclass + 1, nullptr, st))) return rc;
     int64_t h_items = 0;
-    if ((rc = emit_classes(t, nclass, ukeys, counts, cfirst, &h_items, st))) return rc;
+    if ((rc = emit_classes(t, nclass, ukeys, counts, i1, ntc, pairs, &h_items, st))) return rc;
     // pairs in class order, then the rest (sorted by target below)
     if ((rc = dev_alloc(&d.tc_tgt, (size_t)np, t, st))) return rc;
     if ((rc = dev_alloc(&d.tc_src, (size_t)np, t, st))) return rc;
@@ -696,48 +807,60 @@ __global__ void k_split_real(int ncell, int KR, int KI, int ldM, const float* __
     Ms[cell * 2 * KI + KI + c] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// One persistent block per SM runs a contiguous range of work items (128
-// pairs of one class each) as a warp-specialised pipeline:
-//   producer (warp 12)    gathers the 128 source rows of an item with TMA,
-//                         one 64-coefficient swizzle atom (hi and lo tiles,
-//                         32 KB) per shared-memory stage;
-//   assemblers (8..11)    build the operator of each new class in one of two
-//                         tensor-memory slots (lane = output coefficient, hi
-//                         and lo bf16 parts), from the class harmonics;
-//   MMA (warp 13)         one thread issues, per atom and K step of 16, the
-//                         three products T_hi A_hi + T_lo A_hi + T_hi A_lo
-//                         into one of `nacc` 128-column accumulators;
-//   epilogue (warps 0..7) reads an accumulator (lane = output coefficient,
-//                         column = pair) and adds it into the targets' local
-//                         expansions: per pair, one warp-wide reduction of
-//                         32 consecutive coefficients.
+// One persistent block per SM runs its list of work items (128 pairs of one
+// class each) as a warp-specialised pipeline:
+//   producer (warp 16)      TMA row gather (tile::gather4) of the hi tile of the
+//                           first 64-coefficient atom of each item; the source
+//                           indices come through a cp.async ring;
+//   gatherers (warps 8..15) cp.async 16-byte copies of the other tiles (the
+//                           lo tile of that atom, both tiles of the others)
+//                           into the same 128-byte swizzled layout: the TMA
+//                           row gather alone delivers about 8 B/cycle per SM,
+//                           cp.async from 8 warps about 18;
+//   assemblers (warps 8..11, between their gathers) build the operator of each
+//                           new class in one of two tensor-memory slots (lane
+//                           = output coefficient, hi and lo bf16 parts) from
+//                           the class harmonics;
+//   MMA (warp 17)           one thread issues, per atom and K step of 16, the
+//                           three products T_hi A_hi + T_lo A_hi + T_hi A_lo
+//                           into one of `nacc` 128-column accumulators;
+//   epilogue (warps 0..7)   reads an accumulator (lane = output coefficient,
+//                           column = pair), transposes 4 x 4 blocks within
+//                           lane quads, and adds 4 consecutive coefficients of
+//                           a pair into the real-basis accumulator Lr with one
+//                           16-byte vector reduction.
 // Tensor memory: operator slot o in columns [o KI, (o+1) KI) (hi then lo,
 // two bf16 per column), accumulators from column 2 KI on.  mbarriers: full /
-// empty per stage, opfull / opempty per operator slot, accf / acce per
-// accumulator, fin for the last MMAs.  Every wait is bounded; a wait that
-// runs out raises a block-wide abort flag, every role leaves its loop, the
-// producer waits (bounded) for its copies in flight, and the kernel reports
-// FMM_ERR_TIMEOUT through *status.
+// empty per stage (full: the producer's arrival with the TMA bytes, plus one
+// arrival per gathering thread when its copies land), opfull / opempty per
+// operator slot, accf / acce per accumulator, fin for the last MMAs.  Every
+// wait is bounded; a wait that runs out raises a block-wide abort flag, every
+// role leaves its loop, the copies in flight land before the block exits, and
+// the kernel reports FMM_ERR_TIMEOUT through *status.
 constexpr int TC_M = 128;                              // MMA M: output coefficients (K <= 128)
 constexpr int TC_ATOM = 64;                            // coefficients per 128-byte swizzle atom
 constexpr int TC_TILE_BYTES = TC_ROWS * TC_ATOM * 2;   // 128 rows x 128 B
 constexpr int TC_STAGE_BYTES = 2 * TC_TILE_BYTES;      // hi and lo tiles of one atom
-constexpr int TC_EPI_WARPS = 8, TC_ASM_WARPS = 4;
-constexpr int TC_PROD_WARP = TC_EPI_WARPS + TC_ASM_WARPS;
+constexpr int TC_EPI_WARPS = 8, TC_ASM_WARPS = 4, TC_GATH_WARPS = 4;
+constexpr int TC_GATHER_THREADS = 32 * (TC_ASM_WARPS + TC_GATH_WARPS);   // the assemblers gather too
+constexpr int TC_PROD_WARP = TC_EPI_WARPS + TC_ASM_WARPS + TC_GATH_WARPS;
 constexpr int TC_MMA_WARP = TC_PROD_WARP + 1;
 constexpr int TC_THREADS = 32 * (TC_MMA_WARP + 1);
 constexpr int TC_MAX_STAGES = 8, TC_MAX_ACC = 3, TC_TMEM_COLS = 512;
 constexpr int TC_SRC_AHEAD = 6, TC_SRC_RING = 8;   // producer: items of source indices in flight, ring slots
+constexpr int TC_LR = 128;                         // floats per row of the real-basis accumulator
 
 struct TcArgs {
-    int p, KR, KI, nat, stages, nacc, ldL, nh;
-    const int32_t* block_first;  // [gridDim.x + 1] item range of each block
+    int p, KR, KI, nat, stages, nacc, nh;
+    const int32_t* block_first;  // [gridDim.x + 1] range of each block in list
+    const int32_t* list;         // work items of the blocks
     const int4* items;        // (class, first pair, rows, -)
     const int32_t* src;       // sources of the pairs in class order
     const int32_t* tgt;       // targets
     const uint64_t* keys;     // class keys
     const cplx<float>* harm;  // class harmonics
-    float* L;
+    const __nv_bfloat16* Ms;  // split multipoles, rows of [hi KI | lo KI]
+    float* Lr;                // real-basis accumulator, rows of TC_LR floats
     int* status;
     long long budget_ns;
 };
@@ -777,6 +900,31 @@ __device__ __forceinline__ void split_pack(float a, float b, uint32_t& hi, uint3
     const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
     hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
     lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+}
+
+// x0..x3 of lane 4g + r hold (row 4g + r, column k), k = 0..3; afterwards
+// lane 4g + r holds (row 4g + k, column r): a 4 x 4 transpose within each lane
+// quad, three shuffles.
+__device__ __forceinline__ float sel4(float a0, float a1, float a2, float a3, int i) {
+    const float lo = (i & 1) ? a1 : a0, hi = (i & 1) ? a3 : a2;
+    return (i & 2) ? hi : lo;
+}
+__device__ __forceinline__ void quad_transpose(float& x0, float& x1, float& x2, float& x3, int r) {
+    float o0 = x0, o1 = x1, o2 = x2, o3 = x3;
+#pragma unroll
+    for (int xm = 1; xm < 4; xm++) {
+        const int k = r ^ xm;
+        const float v = __shfl_xor_sync(0xffffffffu, sel4(x0, x1, x2, x3, k), xm);
+        o0 = k == 0 ? v : o0;
+        o1 = k == 1 ? v : o1;
+        o2 = k == 2 ? v : o2;
+        o3 = k == 3 ? v : o3;
+    }
+    x0 = o0; x1 = o1; x2 = o2; x3 = o3;
+}
+// p[0..3] += (a, b, c, d): one 16-byte vector reduction (p 16-byte aligned)
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
 // Entry of a class operator in the real basis: output (k, l, pa) (pa = 0 real
@@ -819,7 +967,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
     __shared__ int src_ring[TC_SRC_RING * TC_ROWS];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        for (int s = 0; s < a.stages; s++) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+        for (int s = 0; s < a.stages; s++) {
+            tc::mbar_init(&full[s], 1 + TC_GATHER_THREADS);
+            tc::mbar_init(&empty[s], 1);
+        }
         for (int o = 0; o < 2; o++) { tc::mbar_init(&opfull[o], TC_ASM_WARPS); tc::mbar_init(&opempty[o], 1); }
         for (int c = 0; c < a.nacc; c++) { tc::mbar_init(&accf[c], 1); tc::mbar_init(&acce[c], TC_EPI_WARPS); }
         tc::mbar_init(&fin, 1);
@@ -840,15 +991,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
     const int i0 = a.block_first[blockIdx.x], nit = max(0, a.block_first[blockIdx.x + 1] - i0);
     volatile int* abort_p = &abort_flag;
 
+    // the j-th work item of this block's list
+    auto item = [&](int j) { return a.items[a.list[i0 + j]]; };
+
     if (warp == TC_PROD_WARP) {
-        // ---------------- producer: TMA row gathers, lane l takes rows 4l .. 4l+3.
-        // The source indices of item j + TC_SRC_AHEAD are copied into a ring
-        // in shared memory (cp.async) while item j is issued.
+        // ---------------- producer: TMA row gather of the hi tile of each item's
+        // first atom, lane l taking rows 4l .. 4l+3; plain arrivals for the
+        // other stages.  The source indices of item j + TC_SRC_AHEAD are copied
+        // into a ring in shared memory (cp.async) while item j is issued.
         int ctr = 0;
         bool ok = true;
         auto prefetch_rows = [&](int j) {
             if (j < nit) {
-                const int4 it = a.items[i0 + j];
+                const int4 it = item(j);
                 int* ring = src_ring + (j % TC_SRC_RING) * TC_ROWS;
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
@@ -873,12 +1028,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
                 const int s = ctr % a.stages, use = ctr / a.stages;
                 if (use > 0) ok = tc_wait(&empty[s], (uint32_t)((use - 1) & 1), a.budget_ns, abort_p);
                 if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
-                if (lane == 0) tc::mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
-                __syncwarp();
-                const uint32_t dst = tc::smem_u32(sm + (size_t)s * TC_STAGE_BYTES) + 512u * lane;
-                const uint32_t bar = tc::smem_u32(&full[s]);
-                tc::tma_gather4(dst, &tmap, at * TC_ATOM, y[0], y[1], y[2], y[3], bar);
-                tc::tma_gather4(dst + TC_TILE_BYTES, &tmap, a.KI + at * TC_ATOM, y[0], y[1], y[2], y[3], bar);
+                if (at == 0) {
+                    if (lane == 0) tc::mbar_arrive_expect_tx(&full[s], TC_TILE_BYTES);
+                    __syncwarp();
+                    tc::tma_gather4(tc::smem_u32(sm + (size_t)s * TC_STAGE_BYTES) + 512u * lane, &tmap, 0, y[0], y[1],
+                                    y[2], y[3], tc::smem_u32(&full[s]));
+                } else if (lane == 0) {
+                    tc::mbar_arrive(&full[s]);
+                }
             }
         }
         // the copies of every stage still in flight land before the block exits
@@ -891,10 +1048,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_ROWS);
             int ctr = 0, cur_cls = -1, slot = 1, uses[2] = {0, 0};
-            int cls_next = nit > 0 ? a.items[i0].x : -1;
+            int cls_next = nit > 0 ? a.items[a.list[i0]].x : -1;
             for (int j = 0; j < nit; j++) {
                 const int cls = cls_next;
-                cls_next = j + 1 < nit ? a.items[i0 + j + 1].x : -1;
+                cls_next = j + 1 < nit ? a.items[a.list[i0 + j + 1]].x : -1;
                 if (cls != cur_cls) {
                     slot ^= 1;
                     cur_cls = cls;
@@ -933,8 +1090,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
         }
         __syncwarp();
     } else if (warp >= TC_EPI_WARPS) {
-        // ---------------- assemblers: thread = output coefficient (tensor-memory lane)
-        const int q = warp - TC_EPI_WARPS, at_id = tid - 32 * TC_EPI_WARPS;
+        // ---------------- gatherers (warps 8..15): thread gi copies row
+        // 16 (gi / 32) + (lane / 2), 16-byte chunks 4 (lane & 1) .. +3 of every
+        // cp.async tile (one whole 32-byte sector per thread pair and row).
+        // Warps 8..11 are also the assemblers: thread = output coefficient
+        // (tensor-memory lane) of the operator of each new class.
+        const int gi = tid - 32 * TC_EPI_WARPS;
+        const int grow = 16 * (gi >> 5) + (lane >> 1), gc0 = 4 * (lane & 1);
+        const uint32_t goff = (uint32_t)((grow >> 3) * 1024 + (grow & 7) * 128);
+        const bool assembler = warp < TC_EPI_WARPS + TC_ASM_WARPS;
+        const int q = (warp - TC_EPI_WARPS) & 3;
         const int co = 32 * q + lane;
         const int dco = dec[co];
         const int k = dco >= 0 ? (dco & 0xff) : 0, l = dco >= 0 ? ((dco >> 8) & 0xff) : 0, pa = (dco >> 16) & 1;
@@ -942,74 +1107,92 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
         const float ksgn = dco < 0 ? 0.f : ((k & 1) ? -1.f : 1.f);   // a padding row stays zero
         const float2* H = reinterpret_cast<const float2*>(hbuf);
         const uint32_t lane_base = tbase + ((uint32_t)(32 * q) << 16);
-        // the harmonics and key of the next class run are loaded into registers
-        // while the current run is assembled
-        int run = -1, cur_cls = -1, jn = 0;
-        cplx<float> hn[2];
-        uint64_t keyn = 0;
-        auto next_run = [&](int& jj) {   // first item of the next run at or after jj: its class, or -1
-            while (jj < nit && a.items[i0 + jj].x == cur_cls) jj++;
-            return jj < nit ? a.items[i0 + jj].x : -1;
-        };
-        auto load_class = [&](int c) {
-            if (c < 0) return;
+        int run = -1, cur_cls = -1;
+        bool ok = true;
+        int srcn = -1;
+        if (nit > 0) { const int4 it = item(0); srcn = grow < it.z ? a.src[it.y + grow] : -1; }
+        int ctr = 0;
+        for (int j = 0; j < nit; j++) {
+            const int4 it = item(j);
+            const int src_j = srcn;
+            if (j + 1 < nit) { const int4 in = item(j + 1); srcn = grow < in.z ? a.src[in.y + grow] : -1; }
+            if (assembler && it.x != cur_cls) {
+                // a new class run: its operator into slot run & 1 once the MMAs of
+                // the run two back (the slot's last user) are done.  All 128
+                // assemblers take part in every run, failed or not, and leave
+                // together when one of them failed.
+                cur_cls = it.x;
+                run++;
+                const int slot = run & 1, use = run >> 1;
+                bool wok = ok;
+                if (wok && use > 0) wok = tc_wait(&opempty[slot], (uint32_t)((use - 1) & 1), a.budget_ns, abort_p);
+                if (!bar_all(1, 32 * TC_ASM_WARPS, wok)) {
+                    ok = false;
+                } else {
+                    for (int e = lane + 32 * q; e < a.nh; e += 32 * TC_ASM_WARPS) hbuf[e] = a.harm[(size_t)cur_cls * a.nh + e];
+                    int dl;
+                    {
+                        double dx, dy, dz;
+                        class_offset(a.keys[cur_cls], dl, dx, dy, dz);
+                    }
+                    asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_ASM_WARPS) : "memory");
+                    const uint32_t ts = lane_base + (uint32_t)(slot * a.KI);
+                    for (int ch = 0; ch < a.KI / 32; ch++) {
+                        uint32_t hw[16], lw[16];
 #pragma unroll
-            for (int u = 0; u < 2; u++) {
-                const int e = at_id + 32 * TC_ASM_WARPS * u;
-                if (e < a.nh) hn[u] = a.harm[(size_t)c * a.nh + e];
-            }
-            keyn = a.keys[c];
-        };
-        int cls = next_run(jn);
-        load_class(cls);
-        while (cls >= 0) {
-            cur_cls = cls;
-            run++;
-            const int slot = run & 1, use = run >> 1;
-            bool ok = true;
-            if (use > 0) ok = tc_wait(&opempty[slot], (uint32_t)((use - 1) & 1), a.budget_ns, abort_p);
-            // every assembler is past its last read of hbuf, and all leave together
-            if (!bar_all(1, 32 * TC_ASM_WARPS, ok)) break;
-#pragma unroll
-            for (int u = 0; u < 2; u++) {
-                const int e = at_id + 32 * TC_ASM_WARPS * u;
-                if (e < a.nh) hbuf[e] = hn[u];
-            }
-            int dl;
-            {
-                double dx, dy, dz;
-                class_offset(keyn, dl, dx, dy, dz);
-            }
-            asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_ASM_WARPS) : "memory");
-            cls = next_run(jn);
-            load_class(cls);
-            const uint32_t ts = lane_base + (uint32_t)(slot * a.KI);
-            for (int ch = 0; ch < a.KI / 32; ch++) {
-                uint32_t hw[16], lw[16];
-#pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const float v0 = class_operator_entry(colmeta[32 * ch + 2 * i], k, l, pa, Tk, ksgn, dl, H);
-                    const float v1 = class_operator_entry(colmeta[32 * ch + 2 * i + 1], k, l, pa, Tk, ksgn, dl, H);
-                    split_pack(v0, v1, hw[i], lw[i]);
+                        for (int i = 0; i < 16; i++) {
+                            const float v0 = class_operator_entry(colmeta[32 * ch + 2 * i], k, l, pa, Tk, ksgn, dl, H);
+                            const float v1 = class_operator_entry(colmeta[32 * ch + 2 * i + 1], k, l, pa, Tk, ksgn, dl, H);
+                            split_pack(v0, v1, hw[i], lw[i]);
+                        }
+                        tc::tmem_st16(ts + (uint32_t)(16 * ch), hw);
+                        tc::tmem_st16(ts + (uint32_t)(a.KI / 2 + 16 * ch), lw);
+                    }
+                    tc::tmem_wait_st();
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&opfull[slot]);
+                    // every assembler is past its last read of hbuf before the next run writes it
+                    asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_ASM_WARPS) : "memory");
                 }
-                tc::tmem_st16(ts + (uint32_t)(16 * ch), hw);
-                tc::tmem_st16(ts + (uint32_t)(a.KI / 2 + 16 * ch), lw);
             }
-            tc::tmem_wait_st();
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&opfull[slot]);
+            if (!ok) {
+                if (assembler) continue;   // stay in step with the other assemblers' runs
+                break;
+            }
+            for (int at = 0; at < a.nat; at++, ctr++) {
+                const int s = ctr % a.stages, use = ctr / a.stages;
+                if (use > 0 && !tc_wait(&empty[s], (uint32_t)((use - 1) & 1), a.budget_ns, abort_p)) { ok = false; break; }
+                const bool valid = src_j >= 0;
+                const __nv_bfloat16* g = a.Ms + (size_t)(valid ? src_j : 0) * 2 * a.KI + TC_ATOM * at;
+                unsigned char* base = sm + (size_t)s * TC_STAGE_BYTES + goff;
+#pragma unroll
+                for (int t2 = 0; t2 < 2; t2++) {
+                    if (at == 0 && t2 == 0) continue;   // the producer's TMA tile
+                    unsigned char* tile = base + t2 * TC_TILE_BYTES;
+                    const __nv_bfloat16* gt = g + t2 * a.KI;
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        const int ch = gc0 + c;
+                        tc::cp_async16(tile + ((ch ^ (grow & 7)) << 4), gt + 8 * ch, valid ? 16u : 0u);
+                    }
+                }
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::smem_u32(&full[s]))
+                             : "memory");
+            }
         }
+        tc::cp_async_wait_all();
     } else {
         // ---------------- epilogue: lane = output coefficient of quarter q,
-        // columns (pairs) [64 part, 64 part + 64) of each accumulator
-        const int q = warp & 3, part = warp >> 2;
-        const int co = 32 * q + lane;
-        const bool valid = co < a.KR;
-        const int foff = valid ? real_index_offset(co) : 0;
+        // columns (pairs) [64 part, 64 part + 64) of each accumulator.  Lane
+        // quads swap 4 x 4 blocks, so lane 4g + r ends with coefficients
+        // 32 q + 4g .. + 3 of one pair, added with one vector reduction.
+        const int q = warp & 3, part = warp >> 2, r4 = lane & 3;
+        const int cq = 32 * q + (lane & ~3);
+        const bool quad_valid = cq < a.KR;
         const uint32_t lane_base = tbase + ((uint32_t)(32 * q) << 16) + acc_col0 + (uint32_t)(64 * part);
         auto load_targets = [&](int j, int& t0, int& t1) {
-            const int4 it = a.items[i0 + j];
+            const int4 it = item(j);
             const int r0 = 64 * part + lane, r1 = r0 + 32;
             t0 = r0 < it.z ? a.tgt[it.y + r0] : -1;
             t1 = r1 < it.z ? a.tgt[it.y + r1] : -1;
@@ -1034,10 +1217,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
 #pragma unroll
             for (int c = 0; c < 4; c++)
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const int col = 16 * c + i;
-                    const int t = __shfl_sync(0xffffffffu, col < 32 ? tg0 : tg1, col & 31);
-                    if (t >= 0 && valid) atomicAdd(a.L + (size_t)t * a.ldL + foff, __uint_as_float(v[c][i]));
+                for (int b4 = 0; b4 < 4; b4++) {
+                    float x0 = __uint_as_float(v[c][4 * b4]), x1 = __uint_as_float(v[c][4 * b4 + 1]);
+                    float x2 = __uint_as_float(v[c][4 * b4 + 2]), x3 = __uint_as_float(v[c][4 * b4 + 3]);
+                    quad_transpose(x0, x1, x2, x3, r4);
+                    const int col = 16 * c + 4 * b4 + r4;   // the pair this lane now holds
+                    const int t = __shfl_sync(0xffffffffu, c < 2 ? tg0 : tg1, col & 31);
+                    if (t >= 0 && quad_valid) red_add_v4(a.Lr + (size_t)t * TC_LR + cq, x0, x1, x2, x3);
                 }
             tg0 = ng0;
             tg1 = ng1;
@@ -1048,6 +1234,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
     tc::fence_after_sync();
     if (tid == 0 && abort_flag) atomicExch(a.status, 1);
     if (warp == TC_MMA_WARP) tc::tmem_dealloc(tbase, TC_TMEM_COLS);
+}
+
+// L (complex rows of ldL floats) += Lr (real-basis rows of TC_LR floats), the
+// first KR coefficients of each cell
+__global__ void k_fold_real(int ncell, int KR, int ldL, const float* __restrict__ Lr, float* __restrict__ L) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)ncell * KR) return;
+    const int64_t cell = e / KR;
+    const int c = (int)(e % KR);
+    L[cell * ldL + real_index_offset(c)] += Lr[cell * TC_LR + c];
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (the library
@@ -1116,15 +1312,20 @@ int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st) {
         FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_ops,
                                          cs == cudaStreamCaptureStatusNone ? cudaEventWaitDefault : cudaEventWaitExternal));
     }
+    float* Lr = (float*)d.tc_lr;
+    FMM_CUDA_TRY(cudaMemsetAsync(Lr, 0, sizeof(float) * TC_LR * (size_t)t->ncell, st));
     TcArgs a;
-    a.p = p; a.KR = KR; a.KI = KI; a.nat = KI / TC_ATOM; a.stages = stages; a.nacc = nacc; a.ldL = 2 * KS;
-    a.nh = nh; a.block_first = d.tc_block_first;
+    a.p = p; a.KR = KR; a.KI = KI; a.nat = KI / TC_ATOM; a.stages = stages; a.nacc = nacc;
+    a.Ms = (const __nv_bfloat16*)d.tc_msplit; a.Lr = Lr;
+    a.nh = nh; a.block_first = d.tc_block_first; a.list = d.tc_item_list;
     a.items = d.tc_items; a.src = d.tc_src; a.tgt = d.tc_tgt; a.keys = d.tc_keys;
-    a.harm = (const cplx<float>*)d.tc_harm; a.L = L; a.status = d.status; a.budget_ns = t->prm.timeout_ns;
+    a.harm = (const cplx<float>*)d.tc_harm; a.status = d.status; a.budget_ns = t->prm.timeout_ns;
     stage_begin(t, FMM_STAGE_M2L_TC, st);
     k_m2l_tc<<<grid, TC_THREADS, smem, st>>>(t->tc_tmap, a);
     count_launch(t);
     stage_end(t, FMM_STAGE_M2L_TC, st);
+    k_fold_real<<<nblk((int64_t)t->ncell * KR, 256), 256, 0, st>>>(t->ncell, KR, 2 * KS, Lr, L);
+    count_launch(t);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }

@@ -1435,14 +1435,15 @@ void free_tree_device(fmm_tree* t) {
     dev_free(d.geom, st); dev_free(d.status, st);
     if (d.grad_tmp) cudaFreeAsync(d.grad_tmp, st);
     d.grad_tmp = nullptr;
-    dev_free(d.m2l_tgt, st); dev_free(d.p2p_rec, st); dev_free(d.tc_items, st); dev_free(d.tc_block_first, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
+    dev_free(d.m2l_tgt, st); dev_free(d.p2p_rec, st); dev_free(d.tc_items, st); dev_free(d.tc_block_first, st); dev_free(d.tc_item_list, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
     dev_free(d.rem_start, st); dev_free(d.rem_chunks, st);
     dev_free(d.tr_start, st); dev_free(d.tr_tgt, st); dev_free(d.q_cnt_init, st); dev_free(d.q_cnt, st);
     dev_free(d.q_init, st); dev_free(d.q_work, st); dev_free(d.q_ctr, st);
     dev_free(d.tc_keys, st);
     if (d.tc_harm) cudaFreeAsync(d.tc_harm, st);
     if (d.tc_msplit) cudaFreeAsync(d.tc_msplit, st);
-    d.tc_harm = nullptr; d.tc_msplit = nullptr;
+    if (d.tc_lr) cudaFreeAsync(d.tc_lr, st);
+    d.tc_harm = nullptr; d.tc_msplit = nullptr; d.tc_lr = nullptr;
     t->tc_tmap_ok = false;
     dev_free(d.M, st); dev_free(d.L, st); dev_free(d.xq, st); dev_free(d.near, st);
     if (d.shift_ops) cudaFreeAsync(d.shift_ops, st);
