@@ -82,6 +82,8 @@ def parse():
                     help="0 fp64, 1 fp32 P2P + fp64 expansions, 2 fp32, 3 mixed: bf16x3 tensor-core M2L + fp32")
     ap.add_argument("--no-variants", action="store_true", help="skip the other precisions' context timings")
     ap.add_argument("--staged", action="store_true", help="one kernel per stage instead of the task queue")
+    ap.add_argument("--task-graph", action="store_true",
+                    help="mixed form: run the evaluation as one persistent task-graph launch (FMM_TASK_GRAPH)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=1 << 21,
@@ -307,6 +309,46 @@ def fp64_roofline_ratio(value: float, n: int, ex, v64):
             "fp64_frac_of_roofline": ideal_s * 1e3 / v64["ms_per_step"]}
 
 
+def execution_name(args) -> str:
+    if args.staged:
+        return "staged kernels"
+    if args.precision == 3:
+        return "persistent task graph (one launch)" if args.task_graph else "staged kernels"
+    return "persistent task queue"
+
+
+def schedule_variant(fmm, torch, pos, q, phi64, f64, flush, stream, flags: int, steps: int = 3):
+    """The same system and precision under the other schedule of the mixed form
+    (the persistent task graph, or the staged kernels): build + evaluation
+    particles/s, the evaluation alone, and the error against the FP64 GPU path."""
+    n = pos.shape[0]
+    phi = torch.empty_like(phi64)
+    force = torch.empty_like(f64)
+    ts, te = [], []
+    for k in range(steps + 2):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        t = fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=3, flags=flags)
+        e1.record(stream)
+        t.evaluate(q, phi=phi, force=force)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        status = t.status()
+        t.close()
+        if status != fmm.FMM_OK:
+            return {"error": f"status {status}"}
+        if k >= 2:
+            ts.append(e0.elapsed_time(e2))
+            te.append(e1.elapsed_time(e2))
+    ms = statistics.median(ts)
+    return {"execution": "persistent task graph (one launch)" if flags & fmm.TASK_GRAPH else "staged kernels",
+            "value": n / (ms * 1e-3), "ms_per_step": ms, "evaluate_ms": statistics.median(te), "steps": steps,
+            "dtype": PREC_DTYPE[3],
+            "rel_l2_vs_fp64_gpu": {"phi": float(((phi - phi64).norm() / phi64.norm()).item()),
+                                   "force": float(((force - f64).norm() / f64.norm()).item())}}
+
+
 def plummer_variant(fmm, torch, dev, flush, stream, steps: int = 3):
     """The mixed form on the Plummer configuration (1M particles, p = 8, leaf 64,
     theta = 0.4): particles/s of build + evaluation and its error against the
@@ -360,7 +402,7 @@ def run_ours(args):
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     force = torch.empty((n, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    flags = fmm.TIMING | (fmm.STAGED if args.staged else 0)
+    flags = fmm.TIMING | (fmm.STAGED if args.staged else 0) | (fmm.TASK_GRAPH if args.task_graph else 0)
 
     def step():
         t = fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=args.precision, flags=flags)
@@ -435,7 +477,7 @@ def run_ours(args):
     # the same kernels with nothing running beside them (FMM_NO_OVERLAP: P2P and
     # the far field one after the other), outside the timed region: the step
     # overlaps P2P with the far field, which stretches both kernels' event times
-    if args.precision == 3 or args.staged:
+    if (args.precision == 3 and not args.task_graph) or args.staged:
         iso_acc = {}
         for k in range(4):
             flush.zero_()
@@ -492,6 +534,9 @@ def run_ours(args):
             del pv, fv
         if WORKLOAD != "plummer":
             variants["plummer_mixed_tc"] = plummer_variant(fmm, torch, dev, flush, stream)
+        if args.precision == 3:
+            variants["task_graph" if not args.task_graph else "staged"] = schedule_variant(
+                fmm, torch, pos, q, phi64, f64, flush, stream, 0 if args.task_graph else fmm.TASK_GRAPH)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -504,7 +549,8 @@ def run_ours(args):
         def e2e_step():
             dpos = hpos.to(dev, non_blocking=True)
             dq = hq.to(dev, non_blocking=True)
-            t = fmm.build_tree(dpos, p=P, leaf_size=LEAF, theta=THETA, precision=args.precision)
+            t = fmm.build_tree(dpos, p=P, leaf_size=LEAF, theta=THETA, precision=args.precision,
+                               flags=flags & ~fmm.TIMING)
             ph, fo = t.evaluate(dq)
             hphi.copy_(ph, non_blocking=True)
             hforce.copy_(fo, non_blocking=True)
@@ -539,7 +585,7 @@ def run_ours(args):
             "config": {"workload": workload_line(n),
                        "step": "fmm_build_tree + fmm_evaluate (potentials and forces)",
                        "precision": PREC_NAMES[args.precision], "l2": "flushed between steps (512 MB write)",
-                       "execution": "staged kernels" if (args.staged or args.precision == 3) else "persistent task queue",
+                       "execution": execution_name(args),
                        "parallelism": f"replicas x{world}", "ncell": info.ncell, "nleaf": info.nleaf,
                        "nm2l": info.nm2l, "np2p": info.np2p, "tc_pairs": info.tc_pairs,
                        "tc_classes": info.tc_classes,

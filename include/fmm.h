@@ -64,6 +64,12 @@ extern "C" {
                                   cell indices; the paths otherwise taken only when a buffer or
                                   table overflows: round-by-round traversal, tensor-core classes
                                   grouped by sorting their keys); same tree and lists */
+#define FMM_TASK_GRAPH  32  /* FMM_PREC_MIXED_TC: run the whole evaluation as one persistent launch
+                               over a task graph (P2M, M2M, CUDA-core M2L, L2L, L2P and P2P tasks
+                               released by device-side dependency counters, the tensor-core M2L
+                               inside the same launch); without it the mixed form runs stage by
+                               stage.  Ignored with FMM_STAGED or FMM_NO_OVERLAP and for the other
+                               precisions (they run the persistent task queue by default). */
 
 /* stage indices for fmm_stage_times / fmm_stage_name */
 #define FMM_STAGE_KEYS      0   /* root cube, Morton keys, key sort */
@@ -95,7 +101,8 @@ typedef struct {
                             through M2L iff (s_i + s_j) < theta * |2 (c_i - c_j)|,
                             s = cell side, c = cell centre (Sections 2.1 and 4) */
     int32_t precision;   /* FMM_PREC_* */
-    int32_t flags;       /* FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP | FMM_BUILD_FALLBACKS */
+    int32_t flags;       /* FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP | FMM_BUILD_FALLBACKS
+                            | FMM_TASK_GRAPH */
     int64_t timeout_ns;  /* budget of each bounded device-side wait; 0 = 2 s */
 } fmm_params;
 
@@ -239,10 +246,11 @@ int fmm_status(fmm_tree* tree);
  * Failure injection for the task-queue evaluation (tests of the bounded waits).
  * Adds `delta` to the initial dependency counter `counter` of cell `cell`:
  * counter 0 = children still to finish M (M2M), 1 = M2L sources not final,
- * 2 = L2L prerequisites, 3 = L2P prerequisites.  A counter raised by one
- * leaves its task never ready: the evaluation then ends after the tree's
- * timeout with FMM_ERR_TIMEOUT reported by fmm_status, without a hang.
- * FMM_ERR_STATE if the tree does not use the task queue.  Synchronises.
+ * 2 = L2L prerequisites, 3 = L2P prerequisites (the mixed form's task graph,
+ * FMM_TASK_GRAPH, keeps counters 0 and 3 only: FMM_ERR_ARG for 1 and 2).  A
+ * counter raised by one leaves its task never ready: the evaluation then ends
+ * after the tree's timeout with FMM_ERR_TIMEOUT reported by fmm_status,
+ * without a hang.  FMM_ERR_STATE if the tree uses neither.  Synchronises.
  */
 int fmm_inject_dependency(fmm_tree* tree, int32_t counter, int32_t cell, int32_t delta);
 

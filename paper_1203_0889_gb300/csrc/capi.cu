@@ -32,7 +32,7 @@ int check_params(const fmm_params* prm) {
         fmm_set_error("unknown precision %d", prm->precision);
         return FMM_ERR_ARG;
     }
-    if (prm->flags & ~(FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP | FMM_BUILD_FALLBACKS)) { fmm_set_error("unknown flags 0x%x", prm->flags); return FMM_ERR_ARG; }
+    if (prm->flags & ~(FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP | FMM_BUILD_FALLBACKS | FMM_TASK_GRAPH)) { fmm_set_error("unknown flags 0x%x", prm->flags); return FMM_ERR_ARG; }
     if (prm->timeout_ns < 0) { fmm_set_error("timeout_ns < 0"); return FMM_ERR_ARG; }
     return FMM_OK;
 }
@@ -322,10 +322,17 @@ int fmm_tree_export(const fmm_tree* t, uint64_t* keys, int64_t* perm, int32_t* l
 
 int fmm_inject_dependency(fmm_tree* t, int32_t counter, int32_t cell, int32_t delta) {
     if (!t) { fmm_set_error("tree is NULL"); return FMM_ERR_ARG; }
-    if (!t->d.q_cnt_init) { fmm_set_error("tree does not use the task queue"); return FMM_ERR_STATE; }
+    if (!t->d.q_cnt_init && !t->d.dag_cnt_init) { fmm_set_error("tree does not use the task queue"); return FMM_ERR_STATE; }
     if (counter < 0 || counter > 3 || cell < 0 || cell >= t->ncell) { fmm_set_error("bad counter or cell"); return FMM_ERR_ARG; }
+    int32_t* p = nullptr;
+    if (t->d.q_cnt_init) {
+        p = t->d.q_cnt_init + (size_t)counter * t->ncell + cell;
+    } else {
+        // the mixed form's task graph keeps counters 0 (children not final) and 3 (L2P)
+        if (counter != 0 && counter != 3) { fmm_set_error("this tree's task graph has counters 0 and 3 only"); return FMM_ERR_ARG; }
+        p = t->d.dag_cnt_init + (size_t)(counter == 0 ? 0 : 1) * t->ncell + cell;
+    }
     int32_t v = 0;
-    int32_t* p = t->d.q_cnt_init + (size_t)counter * t->ncell + cell;
     cudaError_t e = cudaMemcpy(&v, p, 4, cudaMemcpyDeviceToHost);
     v += delta;
     if (e == cudaSuccess) e = cudaMemcpy(p, &v, 4, cudaMemcpyHostToDevice);

@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(32 * NW) k_shift_block(int p, int lb, int le, 
     const int c = lb + blockIdx.x;
     if (c >= le) return;
     if (kind == 0 && child_count[c] == 0) return;
-    shift_cell_block<T, RQ, NW>(p, c, kind, child_first, child_count, parent, ckey, ops, E, xin, red);
+    shift_cell_block<T, RQ, NW, false>(p, c, kind, child_first, child_count, parent, ckey, ops, E, xin, red,
+                                       (int)(threadIdx.x >> 5), (int)threadIdx.x, BlockSync{});
 }
 
 // one warp per leaf
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(P2P_THREADS, sizeof(T) == 4 ? 9 : 1) k_p2p(int
     __shared__ typename Vec4<T>::type buf[P2P_BUF];
     __shared__ T part[P2P_THREADS][4];
     if (blockIdx.x >= nleaf) return;
-    p2p_leaf<T>(leaves[blockIdx.x], first, count, start, rec, xq, icentre, cu2f, near, buf, part);
+    p2p_leaf<T>(leaves[blockIdx.x], first, count, start, rec, xq, icentre, cu2f, near, buf, part, threadIdx.x);
 }
 
 // L2P + near field + output in input order, one thread per sorted particle
@@ -412,7 +413,7 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st) {
             k_shift_operators<float><<<16, 256, smem, st>>>(t->prm.p, (float*)ops);
         count_launch(t);
     }
-    if (t->prm.precision == FMM_PREC_MIXED_TC && t->tc_nitems > 0) {
+    if (t->prm.precision == FMM_PREC_MIXED_TC && tc_supported(t->prm.p) && (t->tc_nitems > 0 || tc_uses_dag(t))) {
         char* ms = nullptr;
         if ((rc = dev_alloc(&ms, (size_t)t->ncell * 2 * tc_kin(t->prm.p) * 2, t, st))) return rc;
         d.tc_msplit = ms;
@@ -536,6 +537,9 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
         k_prepare32<Q><<<nblk(n, 256), 256, 0, st>>>(d.spos, d.perm, q, n, d.pleaf, d.centre, xq64, xq32);
     count_launch(t);
     stage_end(t, FMM_STAGE_PREPARE, st);
+    if constexpr (sizeof(T) == 4) {
+        if (tc_uses_dag(t)) return evaluate_dag<O>(t, xq64, xq32, phi, force, st);
+    }
     if (queue_supported(t)) {
         // one persistent launch runs the whole task graph
         if constexpr (std::is_same<T, double>::value) {

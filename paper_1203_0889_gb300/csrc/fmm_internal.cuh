@@ -32,6 +32,19 @@ __host__ __device__ inline int ntri(int p) { return (p + 1) * (p + 2) / 2; }
 // or 64-byte (FP64) boundaries, so FP32 rows can take 16-byte vector atomics
 __host__ __device__ inline int kstride(int p) { return (ntri(p) + 3) & ~3; }
 
+// Real basis of an expansion truncated at degree p (tensor-core M2L): index c
+// runs over, for n = 0..p, (n, 0) re, then (n, m) re, (n, m) im for m = 1..n,
+// so there are (p+1)^2 of them (the imaginary parts of the m = 0 terms vanish
+// for real charges and are left out).  Decoded as n | m << 8 | im << 16.
+__host__ __device__ inline int real_index_decode(int c) {
+    int n = 0;
+    while ((n + 1) * (n + 1) <= c) n++;
+    const int r = c - n * n;
+    if (r == 0) return n;
+    const int m = (r + 1) >> 1;
+    return n | (m << 8) | ((r & 1) ? 0 : (1 << 16));
+}
+
 template <typename T>
 struct cplx {
     T re, im;
@@ -184,6 +197,14 @@ struct TreeDev {
     int32_t* q_work = nullptr;
     char* q_ctr = nullptr;        // queue heads / tails / done
     void* grad_tmp = nullptr;     // [n*3] field of the adjoint pass (fmm_backward)
+    // task-graph evaluation of the mixed form (dag.cu)
+    int32_t* dag_cnt_init = nullptr;  // [2][ncell] initial counters: children not final, L2P prerequisites
+    int32_t* dag_cnt = nullptr;       // working copy
+    int32_t* dag_q_init = nullptr;    // initial high-priority queue (the P2M tasks, then empty slots)
+    int32_t* dag_q = nullptr;
+    int32_t* dag_lvl = nullptr;       // [2][FMM_MAX_LEVEL + 1]: cells per level, final cells per level
+    char* dag_ctr = nullptr;          // queue counters
+    int32_t* dag_zero_first = nullptr;  // an empty item list per block (trees without tensor-core items)
 };
 
 }  // namespace fmm
@@ -222,6 +243,7 @@ struct fmm_tree {
     int num_sms = 148;
     int64_t tc_nclass = 0, tc_nitems = 0, tc_npairs = 0, tc_nrem = 0;
     int tc_nblocks = 0;
+    int64_t dag_n_hi = 0, dag_n_tasks = 0, dag_nrem_tasks = 0, dag_m2l_total = 0;
     int64_t rem_nchunk = 0;
     // TMA map of d.tc_msplit (row gathers of the tensor-core M2L), encoded once
     // the table is allocated
@@ -269,6 +291,18 @@ int build_queue(fmm_tree* t, cudaStream_t st);
 template <typename T, typename TP, typename O>
 int evaluate_queue(fmm_tree* t, const double4_32a* xq64, const void* xqp, O* phi, O* force, cudaStream_t st);
 bool tc_supported(int p);
+// the mixed form runs as one task-graph launch unless a stage-by-stage flag is set
+inline bool tc_uses_dag(const fmm_tree* t) {
+    return t->prm.precision == FMM_PREC_MIXED_TC && tc_supported(t->prm.p) && (t->prm.flags & FMM_TASK_GRAPH) &&
+           !(t->prm.flags & (FMM_STAGED | FMM_NO_OVERLAP));
+}
+int build_dag(fmm_tree* t, cudaStream_t st);
+int tc_epilogue_warps();   // epilogue warps per tensor-core block: each counts an item once
+struct DagArgs;
+template <typename O>
+int launch_m2l_dag(fmm_tree* t, const DagArgs& g, cudaStream_t st);
+template <typename O>
+int evaluate_dag(fmm_tree* t, const double4_32a* xq64, const float4* xq32, O* phi, O* force, cudaStream_t st);
 void free_tree_device(fmm_tree* t);
 template <typename T>
 int dev_alloc(T** p, size_t count, fmm_tree* t, cudaStream_t st);

@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "dag.cuh"
 #include "fmm_internal.cuh"
 #include "tc_sm100.cuh"
 
@@ -106,7 +107,9 @@ __device__ __forceinline__ int spatial_block(int level, uint64_t ckey) {
 
 // sort key of position i of `order` (the kept classes' pairs in class order):
 // spatial block of the target << cbits | class
-__global__ void k_segment_keys(int64_t ntc, int nclass, int cbits, const int32_t* __restrict__ cfirst,
+// (by_level: FMM_MAX_LEVEL - level of the source instead, so that the task
+// graph meets the deepest source levels first)
+__global__ void k_segment_keys(int64_t ntc, int nclass, int cbits, int by_level, const int32_t* __restrict__ cfirst,
                                const int32_t* __restrict__ order, const int2* __restrict__ pairs,
                                const int32_t* __restrict__ level, const uint64_t* __restrict__ ckey, int32_t* key) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -116,8 +119,9 @@ __global__ void k_segment_keys(int64_t ntc, int nclass, int cbits, const int32_t
         const int mid = (lo + hi) >> 1;
         if (cfirst[mid] <= i) lo = mid; else hi = mid;
     }
-    const int t = pairs[order[i]].x;
-    key[i] = (spatial_block(level[t], ckey[t]) << cbits) | lo;
+    const int2 pr = pairs[order[i]];
+    const int grp = by_level ? FMM_MAX_LEVEL - level[pr.y] : spatial_block(level[pr.x], ckey[pr.x]);
+    key[i] = (grp << cbits) | lo;
 }
 
 // work items of 128 pairs per segment (run of equal block and class):
@@ -146,11 +150,11 @@ __global__ void k_item_cost(int64_t nitems, const int4* __restrict__ items, int3
 // (k / nb, (k + 1) / nb] of that spatial block's cost; list[first[k] ..
 // first[k + 1]) holds those items, spatial block after spatial block.
 __global__ void k_block_lists(int64_t nitems, const int4* __restrict__ items, const int32_t* __restrict__ pre, int nb,
-                              int32_t* list, int32_t* first) {
-    __shared__ int32_t bs[TC_NSPATIAL + 1];
+                              int ngroup, int32_t* list, int32_t* first) {
+    __shared__ int32_t bs[33];
     __shared__ int32_t off[257];
     const int k = threadIdx.x;
-    if (k <= TC_NSPATIAL) {   // first item of spatial block k
+    if (k <= ngroup) {   // first item of group k
         int64_t lo = 0, hi = nitems;
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
@@ -174,7 +178,7 @@ __global__ void k_block_lists(int64_t nitems, const int4* __restrict__ items, co
     };
     int32_t len = 0;
     if (k < nb)
-        for (int b = 0; b < TC_NSPATIAL; b++) len += bound(b, k + 1) - bound(b, k);
+        for (int b = 0; b < ngroup; b++) len += bound(b, k + 1) - bound(b, k);
     if (k < nb) off[k + 1] = len;
     __syncthreads();
     if (k == 0) {
@@ -185,7 +189,7 @@ __global__ void k_block_lists(int64_t nitems, const int4* __restrict__ items, co
     if (k <= nb) first[k] = off[k];
     if (k < nb) {
         int32_t pos = off[k];
-        for (int b = 0; b < TC_NSPATIAL; b++) {
+        for (int b = 0; b < ngroup; b++) {
             const int32_t e0 = bound(b, k), e1 = bound(b, k + 1);
             for (int32_t i = e0; i < e1; i++) list[pos++] = i;
         }
@@ -352,9 +356,13 @@ static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const in
     const int p = t->prm.p;
     *items_out = 0;
     if (nclass == 0) return FMM_OK;
+    // the task graph takes items deepest source level first; every SM gets a
+    // share of each level
+    const bool by_level = tc_uses_dag(t);
+    const int ngroup = by_level ? FMM_MAX_LEVEL + 1 : TC_NSPATIAL;
     int cbits = 1;
     while ((1 << cbits) < nclass) cbits++;
-    const int kbits = cbits + 3 * TC_BLOCK_LEVEL;
+    const int kbits = cbits + (by_level ? 5 : 3 * TC_BLOCK_LEVEL);
     // segments: runs of equal (spatial block, class); with one spatial block the
     // pairs are in class order already and the segments are the classes
     int32_t *cfirst = nullptr, *k0 = nullptr, *k1 = nullptr, *o1 = nullptr, *segc = nullptr, *segf = nullptr;
@@ -362,7 +370,7 @@ static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const in
     size_t tb = 0, tb2 = 0;
     char* tmp = nullptr;
     int32_t nseg = 0;
-    if (TC_NSPATIAL == 1) {
+    if (ngroup == 1) {
         nseg = nclass;
         if ((rc = dev_alloc(&k0, (size_t)nclass, nullptr, st))) return rc;
         if ((rc = dev_alloc(&segc, (size_t)nclass, nullptr, st))) return rc;
@@ -387,7 +395,8 @@ static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const in
         tb = std::max(tb, tb2);
         if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
         FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, counts, cfirst, nclass, st));
-        k_segment_keys<<<nblk(ntc, 256), 256, 0, st>>>(ntc, nclass, cbits, cfirst, order, pairs, d.level, d.ckey, k0);
+        k_segment_keys<<<nblk(ntc, 256), 256, 0, st>>>(ntc, nclass, cbits, by_level ? 1 : 0, cfirst, order, pairs,
+                                                       d.level, d.ckey, k0);
         FMM_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tb, k0, k1, order, o1, ntc, 0, kbits, st));
         FMM_CUDA_TRY(cudaMemcpyAsync(order, o1, sizeof(int32_t) * ntc, cudaMemcpyDeviceToDevice, st));
         FMM_CUDA_TRY(cub::DeviceRunLengthEncode::Encode(tmp, tb, k1, k0, segc, nseg_d, ntc, st));
@@ -412,7 +421,8 @@ static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const in
     count_launch(t);
     // each kernel block's share of every spatial block, balanced by cost
     {
-        const int nb = (int)std::min<int64_t>(std::min<int64_t>(h_items, (int64_t)t->num_sms), 255);
+        const int nb = by_level ? std::min(t->num_sms, 255)
+                                : (int)std::min<int64_t>(std::min<int64_t>(h_items, (int64_t)t->num_sms), 255);
         int32_t *cost = nullptr, *pre = nullptr;
         if ((rc = dev_alloc(&cost, (size_t)h_items, nullptr, st))) return rc;
         if ((rc = dev_alloc(&pre, (size_t)h_items, nullptr, st))) return rc;
@@ -424,7 +434,7 @@ static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const in
         cub::DeviceScan::InclusiveSum(nullptr, sb, cost, pre, h_items, st);
         if ((rc = dev_alloc(&stmp, sb, nullptr, st))) return rc;
         FMM_CUDA_TRY(cub::DeviceScan::InclusiveSum(stmp, sb, cost, pre, h_items, st));
-        k_block_lists<<<1, 256, 0, st>>>(h_items, d.tc_items, pre, nb, d.tc_item_list, d.tc_block_first);
+        k_block_lists<<<1, 256, 0, st>>>(h_items, d.tc_items, pre, nb, ngroup, d.tc_item_list, d.tc_block_first);
         count_launch(t, 3);
         cudaFreeAsync(stmp, st);
         cudaFreeAsync(cost, st);
@@ -775,18 +785,6 @@ int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st) {
 // evaluate: real-basis split of the multipoles, transposed class product
 // ---------------------------------------------------------------------------
 
-// Real basis of an expansion truncated at degree p: index c runs over, for
-// n = 0..p, (n, 0) re, then (n, m) re, (n, m) im for m = 1..n, so there are
-// (p+1)^2 of them (the imaginary parts of the m = 0 terms vanish for real
-// charges and are left out).  Decoded as n | m << 8 | im << 16.
-__host__ __device__ inline int real_index_decode(int c) {
-    int n = 0;
-    while ((n + 1) * (n + 1) <= c) n++;
-    const int r = c - n * n;
-    if (r == 0) return n;
-    const int m = (r + 1) >> 1;
-    return n | (m << 8) | ((r & 1) ? 0 : (1 << 16));
-}
 // float offset of real coefficient c in a complex (m >= 0, triangular) row
 __host__ __device__ inline int real_index_offset(int c) {
     const int d = real_index_decode(c);
@@ -856,6 +854,7 @@ constexpr int TC_LR = 128;                         // floats per row of the real
 
 struct TcArgs {
     int p, KR, KI, nat, stages, nacc, nh;
+    int wscratch;                // bytes of scratch per worker group (task-graph form)
     const int32_t* block_first;  // [gridDim.x + 1] range of each block in list
     const int32_t* list;         // work items of the blocks
     const int4* items;        // (class, first pair, rows, -)
@@ -957,7 +956,25 @@ __device__ __forceinline__ float class_operator_entry(uint32_t colmeta, int k, i
     return rp * w * v;
 }
 
-__global__ void __maxnreg__(TC_MAX_REGS) k_m2l_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
+// bounded wait until every cell of level lev is final (task-graph form)
+__device__ __forceinline__ bool dag_level_ready(const DagArgs& g, int lev, long long budget_ns, volatile int* abort_flag) {
+    if (dag_vload(&g.lvl_done[lev]) >= g.lvl_count[lev]) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        __nanosleep(256);
+        if (dag_vload(&g.lvl_done[lev]) >= g.lvl_count[lev]) return true;
+        if (*abort_flag || dag_vload(g.status) != 0) { *abort_flag = 1; return false; }
+        if (clock64() - t0 > 2 * budget_ns) { *abort_flag = 1; return false; }
+    }
+}
+
+// DAG = false: the tensor-core M2L alone (stage-by-stage evaluation).
+// DAG = true: the whole evaluation; DAG_GROUPS worker groups per block run the
+// task graph of dag.cuh, items wait for their source level, and the epilogue
+// counts its items towards the M2L gate.
+template <bool DAG, typename O, int R>
+__global__ void __maxnreg__(TC_MAX_REGS) k_m2l_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs a,
+                                                   const DagArgs g) {
     extern __shared__ unsigned char smraw[];
     // stages first (1024-byte aligned: the swizzle atoms), then the harmonics
     unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -969,6 +986,7 @@ __global__ void __maxnreg__(TC_MAX_REGS) k_m2l_tc(const __grid_constant__ CUtens
     __shared__ int dec[TC_M];        // real index -> n | m << 8 | im << 16 (-1 beyond K)
     __shared__ uint32_t colmeta[TC_M];  // the same for the operator's columns (class_operator_entry)
     __shared__ int src_ring[TC_SRC_RING * TC_ROWS];
+    __shared__ int wslot[DAG_GROUPS + 4];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < a.stages; s++) {
@@ -997,6 +1015,19 @@ __global__ void __maxnreg__(TC_MAX_REGS) k_m2l_tc(const __grid_constant__ CUtens
 
     // the j-th work item of this block's list
     auto item = [&](int j) { return a.items[a.list[i0 + j]]; };
+    const bool stage_scratch = (size_t)a.stages * TC_STAGE_BYTES >= (size_t)4 * a.wscratch;
+
+    if (DAG && warp <= TC_MMA_WARP) {
+        // until every multipole is final (every item then ready at once), the
+        // epilogue and gatherer warps run as four more worker groups, with the
+        // stages as their scratch; then every tensor-core role starts together
+        if (warp < TC_PROD_WARP && stage_scratch) {
+            const int grp = DAG_GROUPS + warp / 4;
+            dag_worker<O, R>(g, grp, tid & (DAG_GROUP_THREADS - 1), sm + (size_t)(grp - DAG_GROUPS) * a.wscratch,
+                             &wslot[grp], true);
+        }
+        asm volatile("bar.sync %0, %1;" ::"n"(DAG_BAR0 + DAG_GROUPS + 4), "n"(TC_THREADS) : "memory");
+    }
 
     if (warp == TC_PROD_WARP) {
         // ---------------- producer: TMA row gather of the hi tile of each item's
@@ -1024,6 +1055,8 @@ __global__ void __maxnreg__(TC_MAX_REGS) k_m2l_tc(const __grid_constant__ CUtens
         };
         for (int j = 0; j < TC_SRC_AHEAD; j++) prefetch_rows(j);
         for (int j = 0; j < nit && ok; j++) {
+            if (DAG) ok = __all_sync(0xffffffffu, dag_level_ready(g, FMM_MAX_LEVEL - item(j).w, a.budget_ns, abort_p));
+            if (!ok) break;
             asm volatile("cp.async.wait_group %0;" ::"n"(TC_SRC_AHEAD - 1) : "memory");
             const int* ring = src_ring + (j % TC_SRC_RING) * TC_ROWS;
             const int y[4] = {ring[4 * lane], ring[4 * lane + 1], ring[4 * lane + 2], ring[4 * lane + 3]};
@@ -1093,6 +1126,12 @@ __global__ void __maxnreg__(TC_MAX_REGS) k_m2l_tc(const __grid_constant__ CUtens
             tc_wait(&fin, 0u, a.budget_ns, &never);
         }
         __syncwarp();
+    } else if (DAG && warp > TC_MMA_WARP) {
+        // ---------------- worker groups of the task graph
+        const int group = (warp - TC_MMA_WARP - 1) / 4;
+        unsigned char* wbase = reinterpret_cast<unsigned char*>(hbuf) + ((size_t)a.nh * sizeof(cplx<float>) + 127) / 128 * 128;
+        dag_worker<O, R>(g, group, tid - 32 * (TC_MMA_WARP + 1) - DAG_GROUP_THREADS * group,
+                         wbase + (size_t)group * a.wscratch, &wslot[group]);
     } else if (warp >= TC_EPI_WARPS) {
         // ---------------- gatherers (warps 8..15): thread gi copies row
         // 16 (gi / 32) + (lane / 2), 16-byte chunks 4 (lane & 1) .. +3 of every
@@ -1160,6 +1199,7 @@ __global__ void __maxnreg__(TC_MAX_REGS) k_m2l_tc(const __grid_constant__ CUtens
                     asm volatile("bar.sync 1, %0;" ::"n"(32 * TC_ASM_WARPS) : "memory");
                 }
             }
+            if (DAG && ok) ok = dag_level_ready(g, FMM_MAX_LEVEL - it.w, a.budget_ns, abort_p);
             if (!ok) {
                 if (assembler) continue;   // stay in step with the other assemblers' runs
                 break;
@@ -1229,8 +1269,24 @@ __global__ void __maxnreg__(TC_MAX_REGS) k_m2l_tc(const __grid_constant__ CUtens
                     const int t = __shfl_sync(0xffffffffu, c < 2 ? tg0 : tg1, col & 31);
                     if (t >= 0 && quad_valid) red_add_v4(a.Lr + (size_t)t * TC_LR + cq, x0, x1, x2, x3);
                 }
+            if (DAG) {   // this warp's share of the item has landed
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) dag_m2l_done(g, 1u);
+            }
             tg0 = ng0;
             tg1 = ng1;
+        }
+    }
+    if (DAG && warp <= TC_MMA_WARP) {
+        // every tensor-core role of the block is done (its copies landed, its MMAs
+        // completed, its results added): the epilogue and gatherer warps become
+        // four more worker groups, with the stages as their scratch
+        asm volatile("bar.sync %0, %1;" ::"n"(DAG_BAR0 + DAG_GROUPS + 4), "n"(TC_THREADS) : "memory");
+        if (warp < TC_PROD_WARP && stage_scratch) {
+            const int grp = DAG_GROUPS + warp / 4;
+            dag_worker<O, R>(g, grp, tid & (DAG_GROUP_THREADS - 1), sm + (size_t)(grp - DAG_GROUPS) * a.wscratch,
+                             &wslot[grp]);
         }
     }
     tc::fence_before_sync();
@@ -1283,31 +1339,30 @@ static int encode_split_map(fmm_tree* t) {
     return FMM_OK;
 }
 
-int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st) {
+// Shape and arguments of the tensor-core kernel; wscratch: bytes per worker
+// group (0 for the stage-by-stage form)
+template <bool DAG, typename O, int R>
+static int tc_setup(fmm_tree* t, size_t wscratch, TcArgs& a, size_t& smem, cudaStream_t st) {
     TreeDev& d = t->d;
-    const int p = t->prm.p, KR = tc_kreal(p), KI = tc_kin(p), KS = kstride(p), nh = ntri(2 * p);
-    if (t->tc_nitems == 0) return FMM_OK;
+    const int p = t->prm.p, KR = tc_kreal(p), KI = tc_kin(p), nh = ntri(2 * p);
     int rc;
     if (!t->tc_tmap_ok && (rc = encode_split_map(t))) return rc;
-    const int64_t ne = (int64_t)t->ncell * KI;
-    k_split_real<<<nblk(ne, 256), 256, 0, st>>>(t->ncell, KR, KI, 2 * KS, M, (__nv_bfloat16*)d.tc_msplit);
-    count_launch(t);
     int dev = 0, optin = 0;
     FMM_CUDA_TRY(cudaGetDevice(&dev));
     FMM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     cudaFuncAttributes fa{};
-    FMM_CUDA_TRY(cudaFuncGetAttributes(&fa, k_m2l_tc));
-    const size_t hbytes = (size_t)nh * sizeof(cplx<float>);
-    const size_t cap = (size_t)optin - fa.sharedSizeBytes - 1024 - hbytes;   // 1024: alignment of the stages
+    FMM_CUDA_TRY(cudaFuncGetAttributes(&fa, k_m2l_tc<DAG, O, R>));
+    const size_t hbytes = ((size_t)nh * sizeof(cplx<float>) + 127) / 128 * 128;
+    const size_t other = 1024 + hbytes + (DAG ? DAG_GROUPS * wscratch : 0);   // 1024: alignment of the stages
+    const size_t cap = (size_t)optin - fa.sharedSizeBytes - other;
     const int stages = (int)std::min<size_t>(TC_MAX_STAGES, cap / TC_STAGE_BYTES);
     const int nacc = std::min(TC_MAX_ACC, (TC_TMEM_COLS - 2 * KI) / TC_ROWS);
     if (stages < 2 || nacc < 1) {
         fmm_set_error("tensor-core M2L: p = %d does not fit shared or tensor memory", p);
         return FMM_ERR_ARG;
     }
-    const size_t smem = (size_t)stages * TC_STAGE_BYTES + hbytes + 1024;
-    FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = t->tc_nblocks;
+    smem = (size_t)stages * TC_STAGE_BYTES + other;
+    FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<DAG, O, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (t->ev_ops) {
         // the class harmonics are built on a side stream; under stream capture
         // the wait enters the graph as an external event wait node
@@ -1316,22 +1371,77 @@ int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st) {
         FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_ops,
                                          cs == cudaStreamCaptureStatusNone ? cudaEventWaitDefault : cudaEventWaitExternal));
     }
-    float* Lr = (float*)d.tc_lr;
-    FMM_CUDA_TRY(cudaMemsetAsync(Lr, 0, sizeof(float) * TC_LR * (size_t)t->ncell, st));
-    TcArgs a;
+    FMM_CUDA_TRY(cudaMemsetAsync(d.tc_lr, 0, sizeof(float) * TC_LR * (size_t)t->ncell, st));
+    a = TcArgs{};
     a.p = p; a.KR = KR; a.KI = KI; a.nat = KI / TC_ATOM; a.stages = stages; a.nacc = nacc;
-    a.Ms = (const __nv_bfloat16*)d.tc_msplit; a.Lr = Lr;
+    a.wscratch = (int)wscratch;
+    a.Ms = (const __nv_bfloat16*)d.tc_msplit; a.Lr = (float*)d.tc_lr;
     a.nh = nh; a.block_first = d.tc_block_first; a.list = d.tc_item_list;
     a.items = d.tc_items; a.src = d.tc_src; a.tgt = d.tc_tgt; a.keys = d.tc_keys;
     a.harm = (const cplx<float>*)d.tc_harm; a.status = d.status; a.budget_ns = t->prm.timeout_ns;
+    return FMM_OK;
+}
+
+int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st) {
+    TreeDev& d = t->d;
+    const int p = t->prm.p, KR = tc_kreal(p), KI = tc_kin(p), KS = kstride(p);
+    if (t->tc_nitems == 0) return FMM_OK;
+    int rc;
+    const int64_t ne = (int64_t)t->ncell * KI;
+    k_split_real<<<nblk(ne, 256), 256, 0, st>>>(t->ncell, KR, KI, 2 * KS, M, (__nv_bfloat16*)d.tc_msplit);
+    count_launch(t);
+    TcArgs a;
+    size_t smem = 0;
+    if ((rc = tc_setup<false, float, 3>(t, 0, a, smem, st))) return rc;
     stage_begin(t, FMM_STAGE_M2L_TC, st);
-    k_m2l_tc<<<grid, TC_THREADS, smem, st>>>(t->tc_tmap, a);
+    k_m2l_tc<false, float, 3><<<t->tc_nblocks, TC_THREADS, smem, st>>>(t->tc_tmap, a, DagArgs{});
     count_launch(t);
     stage_end(t, FMM_STAGE_M2L_TC, st);
-    k_fold_real<<<nblk((int64_t)t->ncell * KR, 256), 256, 0, st>>>(t->ncell, KR, 2 * KS, Lr, L);
+    k_fold_real<<<nblk((int64_t)t->ncell * KR, 256), 256, 0, st>>>(t->ncell, KR, 2 * KS, (const float*)d.tc_lr, L);
     count_launch(t);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
+
+int tc_epilogue_warps() { return TC_EPI_WARPS; }
+
+// The whole evaluation of the mixed form as one launch (task graph, dag.cuh):
+// the tensor-core roles of every block take its item list, its worker groups
+// the task queue.  One block per SM, all resident.
+template <typename O>
+int launch_m2l_dag(fmm_tree* t, const DagArgs& g, cudaStream_t st) {
+    const size_t ws = dag_group_scratch(t->prm.p);
+    TcArgs a;
+    size_t smem = 0;
+    int rc;
+    // one block per SM, launched cooperatively: every block is resident (the
+    // downward pass waits for the tensor-core items of all blocks)
+    const int grid = std::min(t->num_sms, 255);
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(TC_THREADS + DAG_GROUPS * DAG_GROUP_THREADS);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (g.R <= 3) {
+        if ((rc = tc_setup<true, O, 3>(t, ws, a, smem, st))) return rc;
+        if (t->tc_nitems == 0) { a.block_first = t->d.dag_zero_first; a.list = t->d.dag_zero_first; }
+        cfg.dynamicSmemBytes = smem;
+        FMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_m2l_tc<true, O, 3>, t->tc_tmap, a, g));
+    } else {
+        if ((rc = tc_setup<true, O, 6>(t, ws, a, smem, st))) return rc;
+        if (t->tc_nitems == 0) { a.block_first = t->d.dag_zero_first; a.list = t->d.dag_zero_first; }
+        cfg.dynamicSmemBytes = smem;
+        FMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_m2l_tc<true, O, 6>, t->tc_tmap, a, g));
+    }
+    count_launch(t);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+template int launch_m2l_dag<float>(fmm_tree*, const DagArgs&, cudaStream_t);
+template int launch_m2l_dag<double>(fmm_tree*, const DagArgs&, cudaStream_t);
 
 }  // namespace fmm

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(QUEUE_THREADS) k_queue(QueueArgs a) {
             VP* buf = reinterpret_cast<VP*>(sm);
             TP(*part)[4] = reinterpret_cast<TP(*)[4]>(sm + P2P_BUF * sizeof(VP));
             p2p_leaf<TP>(a.leaves[idx], a.first, a.count, a.p2p_start, a.p2p_rec, (const VP*)a.xqp, a.icentre, a.cu2f,
-                         a.near, buf, part);
+                         a.near, buf, part, tid);
         }
         // publish this task's writes, then release its successors
         __threadfence();

@@ -142,36 +142,54 @@ __device__ void shift_cell(int p, int c, int kind, int lane, const int32_t* __re
     }
 }
 
-// Block version for the stage-by-stage kernels: NW warps share one destination
-// cell and split its inputs (M2M: warp w takes child w; L2L: warp w takes a
-// slice of the parent's coefficients), so the chain of dependent operator-row
-// loads per warp is NW times shorter; partial sums meet in shared memory.
+constexpr int P2P_THREADS = 128;   // threads of a P2P block or worker group
+
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct GroupSync {
+    int id;   // named barrier id, P2P_THREADS threads
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(P2P_THREADS) : "memory");
+    }
+};
+
+// Group version: NW warps share one destination cell and split its inputs
+// (M2M: warp w takes children w, w + NW, ...; L2L: warp w takes a slice of the
+// parent's coefficients), so the chain of dependent operator-row loads per
+// warp is NW times shorter; partial sums meet in shared memory.  warp / tix:
+// the caller's warp and thread index within the NW warps; sync: their barrier.
+// COH: read E through L2 (E is written by other blocks of the same launch).
 // red: NW * K2 entries; xin: NW * K2 entries.
-template <typename T, int RQ, int NW>
+template <typename T, int RQ, int NW, bool COH, typename Sync>
 __device__ void shift_cell_block(int p, int c, int kind, const int32_t* __restrict__ child_first,
                                  const int32_t* __restrict__ child_count, const int32_t* __restrict__ parent,
                                  const uint64_t* __restrict__ ckey, const T* __restrict__ ops, cplx<T>* E, T* xin,
-                                 T* red) {
+                                 T* red, int warp, int tix, Sync sync) {
     const int K2 = 2 * ntri(p), ld = 2 * kstride(p);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = tix & 31;
     T* Ef = reinterpret_cast<T*>(E);
     T* xw = xin + warp * K2;
     T acc[RQ];
 #pragma unroll
     for (int q = 0; q < RQ; q++) acc[q] = T(0);
-    int s = -1, i_lo = 0, i_hi = K2;
+    int s_first = 0, s_step = 1, s_end = 0, i_lo = 0, i_hi = K2;
     if (kind == 0) {
-        if (warp < child_count[c]) s = child_first[c] + warp;
+        s_first = child_first[c] + warp;
+        s_step = NW;
+        s_end = child_first[c] + child_count[c];
     } else {
-        s = parent[c];
+        s_first = parent[c];
+        s_end = s_first + 1;
         const int per = (K2 + NW - 1) / NW;
         i_lo = min(K2, warp * per);
         i_hi = min(K2, i_lo + per);
     }
-    if (s >= 0 && i_hi > i_lo) {
+    for (int s = s_first; s < s_end && i_hi > i_lo; s += s_step) {
         const int oct = (int)(ckey[kind == 0 ? s : c] & 7);
         const T* op = ops + (size_t)(kind * 8 + oct) * K2 * K2;
-        for (int j = lane; j < K2; j += 32) xw[j] = Ef[(size_t)s * ld + j];
+        __syncwarp();
+        for (int j = lane; j < K2; j += 32) xw[j] = ldx<COH>(Ef + (size_t)s * ld + j);
         __syncwarp();
         for (int i0 = i_lo; i0 < i_hi; i0 += 8) {
             T w[8][RQ];
@@ -197,9 +215,9 @@ __device__ void shift_cell_block(int p, int c, int kind, const int32_t* __restri
         const int j = lane + 32 * q;
         if (j < K2) red[warp * K2 + j] = acc[q];
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < K2; j += 32 * NW) {
-        T v = kind == 0 ? T(0) : Ef[(size_t)c * ld + j];
+    sync();
+    for (int j = tix; j < K2; j += 32 * NW) {
+        T v = kind == 0 ? T(0) : ldx<COH>(Ef + (size_t)c * ld + j);
         for (int w = 0; w < NW; w++) v += red[w * K2 + j];
         Ef[(size_t)c * ld + j] = v;
     }
@@ -321,7 +339,6 @@ __device__ __forceinline__ float rsqrt_t(float x) {
 __device__ __forceinline__ double pair_floor(double) { return 0.0; }
 __device__ __forceinline__ float pair_floor(float) { return 1.17549435e-38f; }
 
-constexpr int P2P_THREADS = 128;
 constexpr int P2P_BUF = 1024;
 
 template <typename T>
@@ -416,19 +433,22 @@ struct P2PBlocking { static constexpr int TPT = 2; };
 // pair interactions: thread t works on targets TPT u + i (u = t mod nu,
 // nu = ceil(nt / TPT)) over the staged sources j = (t / nu) (mod G),
 // G = P2P_THREADS / nu.
-template <typename T>
+// Barrier of the P2P_THREADS threads running p2p_leaf: the whole block, or a
+// named barrier of one 128-thread group inside a larger block.
+
+template <typename T, typename Sync = BlockSync>
 __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t* __restrict__ count,
                          const int64_t* __restrict__ start, const int4* __restrict__ rec,
                          const typename Vec4<T>::type* __restrict__ xq, const int4* __restrict__ icentre,
                          const float* __restrict__ cu2f, double* __restrict__ near, typename Vec4<T>::type* buf,
-                         T (*part)[4]) {
+                         T (*part)[4], int tix, Sync sync = Sync()) {
     typedef typename Vec4<T>::type V;
     constexpr int TPT = P2PBlocking<T>::TPT;
     static_assert(sizeof(T) == 8 || TPT == 2, "the paired FP32 loop holds two targets");
     // sources per staging round: FP32 stages each source as two float4 (negated,
     // duplicated for the paired arithmetic), so half as many fit the buffer
     constexpr int NB = sizeof(T) == 4 ? P2P_BUF / 2 : P2P_BUF;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = tix >> 5, lane = tix & 31;
     const int tf = first[c], nt = count[c];
     const int64_t s0 = start[c], s1 = start[c + 1];
     int total = 0;
@@ -439,7 +459,7 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
         const int ntc = min(TPT * P2P_THREADS, nt - tb);
         const int nu = (ntc + TPT - 1) / TPT;
         const int G = P2P_THREADS / nu;
-        const int u = threadIdx.x % nu, sub = threadIdx.x / nu;
+        const int u = tix % nu, sub = tix / nu;
         const bool active = sub < G;
         V me[TPT];
         T ph[TPT], gx[TPT], gy[TPT], gz[TPT];
@@ -483,7 +503,7 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
                     }
                 }
             }
-            __syncthreads();
+            sync();
             if (active) {
                 if constexpr (sizeof(T) == 4) {
                     const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(buf);
@@ -506,7 +526,7 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
                     }
                 }
             }
-            __syncthreads();
+            sync();
             while (e_lo < s1) {
                 const int4 r = rec[e_lo];
                 if (r.z + r.y > base + NB) break;
@@ -532,20 +552,20 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
         // partial sums of the TPT targets, reduced over the G source streams
 #pragma unroll
         for (int h = 0; h < TPT; h++) {
-            part[threadIdx.x][0] = ph[h]; part[threadIdx.x][1] = gx[h];
-            part[threadIdx.x][2] = gy[h]; part[threadIdx.x][3] = gz[h];
-            __syncthreads();
-            if (threadIdx.x < nu && TPT * threadIdx.x + h < ntc) {
+            part[tix][0] = ph[h]; part[tix][1] = gx[h];
+            part[tix][2] = gy[h]; part[tix][3] = gz[h];
+            sync();
+            if (tix < nu && TPT * tix + h < ntc) {
                 T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
                 for (int q = 0; q < G; q++) {
-                    const int k = q * nu + threadIdx.x;
+                    const int k = q * nu + tix;
                     a0 += part[k][0]; a1 += part[k][1]; a2 += part[k][2]; a3 += part[k][3];
                 }
-                const int64_t i = tf + tb + TPT * threadIdx.x + h;
+                const int64_t i = tf + tb + TPT * tix + h;
                 near[4 * i] = (double)a0; near[4 * i + 1] = (double)a1; near[4 * i + 2] = (double)a2;
                 near[4 * i + 3] = (double)a3;
             }
-            __syncthreads();
+            sync();
         }
     }
 }

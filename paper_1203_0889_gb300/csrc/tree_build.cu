@@ -1388,6 +1388,7 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     stage_end(t, FMM_STAGE_CLASSES, st);
     if (sl != st) FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join_hi, 0));
     if (queue_supported(t) && (rc = build_queue(t, st))) return rc;
+    if (tc_uses_dag(t) && (rc = build_dag(t, st))) return rc;
     stage_end(t, FMM_STAGE_LISTS, st);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
@@ -1437,6 +1438,8 @@ void free_tree_device(fmm_tree* t) {
     d.grad_tmp = nullptr;
     dev_free(d.m2l_tgt, st); dev_free(d.p2p_rec, st); dev_free(d.tc_items, st); dev_free(d.tc_block_first, st); dev_free(d.tc_item_list, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
     dev_free(d.rem_start, st); dev_free(d.rem_chunks, st);
+    dev_free(d.dag_cnt_init, st); dev_free(d.dag_cnt, st); dev_free(d.dag_q_init, st); dev_free(d.dag_q, st);
+    dev_free(d.dag_lvl, st); dev_free(d.dag_ctr, st); dev_free(d.dag_zero_first, st);
     dev_free(d.tr_start, st); dev_free(d.tr_tgt, st); dev_free(d.q_cnt_init, st); dev_free(d.q_cnt, st);
     dev_free(d.q_init, st); dev_free(d.q_work, st); dev_free(d.q_ctr, st);
     dev_free(d.tc_keys, st);
