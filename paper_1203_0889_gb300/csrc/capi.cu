@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -52,6 +53,44 @@ void setup_pool_once() {
 
 }  // namespace
 
+namespace fmm {
+// Pinned host words, PIN_WORDS per live tree, from one arena allocated on first
+// use: the build copies a few device-computed sizes into its tree's slot
+// asynchronously, so that the evaluation knows them without a host round trip.
+namespace {
+constexpr int PIN_SLOTS = 4096;
+std::mutex g_pin_mu;
+int32_t* g_pin = nullptr;
+bool g_pin_failed = false;
+std::vector<int> g_pin_free;
+}  // namespace
+
+int32_t* pinned_slot_acquire() {
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    if (!g_pin && !g_pin_failed) {
+        if (cudaMallocHost(&g_pin, sizeof(int32_t) * PIN_WORDS * PIN_SLOTS) != cudaSuccess) {
+            cudaGetLastError();
+            g_pin = nullptr;
+            g_pin_failed = true;
+        } else {
+            for (int i = PIN_SLOTS - 1; i >= 0; i--) g_pin_free.push_back(i);
+        }
+    }
+    if (!g_pin || g_pin_free.empty()) return nullptr;
+    const int i = g_pin_free.back();
+    g_pin_free.pop_back();
+    int32_t* w = g_pin + (size_t)i * PIN_WORDS;
+    for (int k = 0; k < PIN_WORDS; k++) w[k] = -1;   // not written by a build yet
+    return w;
+}
+
+void pinned_slot_release(int32_t* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    g_pin_free.push_back((int)((p - g_pin) / PIN_WORDS));
+}
+}  // namespace fmm
+
 extern "C" {
 
 const char* fmm_last_error(void) { return g_err; }
@@ -79,6 +118,7 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
     setup_pool_once();
     fmm_tree* t = new (std::nothrow) fmm_tree();
     if (!t) { fmm_set_error("host allocation failed"); return FMM_ERR_ALLOC; }
+    t->h_pin = fmm::pinned_slot_acquire();
     if (offsets) t->h_sys_off = *offsets;
     t->prm = *params;
     if (t->prm.timeout_ns == 0) t->prm.timeout_ns = 2000000000LL;
@@ -93,6 +133,7 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
             if (e != cudaSuccess) {
                 fmm_set_error("cudaEventCreate: %s", cudaGetErrorString(e));
                 for (int k = 0; k < i; k++) cudaEventDestroy(t->ev[k]);
+                fmm::pinned_slot_release(t->h_pin);
                 delete t;
                 return FMM_ERR_CUDA;
             }
@@ -152,6 +193,7 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
         if (t->ev_join) cudaEventDestroy(t->ev_join);
         if (t->ev_join_hi) cudaEventDestroy(t->ev_join_hi);
         if (t->ev_ops) cudaEventDestroy(t->ev_ops);
+        fmm::pinned_slot_release(t->h_pin);
         delete t;
         return rc;
     }
@@ -369,6 +411,7 @@ void fmm_tree_destroy(fmm_tree* t) {
     if (t->ev_fork) cudaEventDestroy(t->ev_fork);
     if (t->ev_join) cudaEventDestroy(t->ev_join);
     if (t->ev_ops) cudaEventDestroy(t->ev_ops);
+    fmm::pinned_slot_release(t->h_pin);
     delete t;
 }
 

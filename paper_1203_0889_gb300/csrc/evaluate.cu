@@ -331,10 +331,17 @@ __global__ void __launch_bounds__(128) k_m2l_chunks(int p, int64_t nchunk, const
     }
 }
 
-// one block per target leaf (FP32: registers capped for 9 resident blocks per
-// SM, measured 2 % faster than the uncapped 62 registers)
+// One work item per block: a leaf's whole list, or a run of the records of a
+// split leaf's list.  The k items of a split leaf write their sums to their
+// own partial slots; the block that finishes last (a counter per leaf, reset
+// by that block) adds the k slots in item order into near, so the result does
+// not depend on the order the blocks ran in.  FP32: registers capped for 9
+// resident blocks per SM, measured 2 % faster than the uncapped 62 registers.
 template <typename T>
-__global__ void __launch_bounds__(P2P_THREADS, sizeof(T) == 4 ? 9 : 1) k_p2p(int nleaf, const int32_t* __restrict__ leaves,
+__global__ void __launch_bounds__(P2P_THREADS, sizeof(T) == 4 ? 9 : 1) k_p2p(const int4* __restrict__ items,
+                                                     const int32_t* __restrict__ nitems,
+                                                     const int4* __restrict__ split, int32_t* __restrict__ arrived,
+                                                     double* __restrict__ partial,
                                                      const int32_t* __restrict__ first,
                                                      const int32_t* __restrict__ count,
                                                      const int64_t* __restrict__ start,
@@ -344,8 +351,39 @@ __global__ void __launch_bounds__(P2P_THREADS, sizeof(T) == 4 ? 9 : 1) k_p2p(int
                                                      double* __restrict__ near) {
     __shared__ typename Vec4<T>::type buf[P2P_BUF];
     __shared__ T part[P2P_THREADS][4];
-    if (blockIdx.x >= nleaf) return;
-    p2p_leaf<T>(leaves[blockIdx.x], first, count, start, rec, xq, icentre, cu2f, near, buf, part, threadIdx.x);
+    __shared__ int last;
+    if ((int)blockIdx.x >= *nitems) return;   // the grid may be an upper bound
+    const int4 it = items[blockIdx.x];
+    const int64_t s0 = start[it.x] + it.y;
+    if (!(it.w & 1)) {
+        p2p_range<T>(it.x, s0, s0 + it.z, (it.w & 2) != 0, nullptr, first, count, rec, xq, icentre, cu2f, near, buf,
+                     part, threadIdx.x);
+        return;
+    }
+    // split leaf: si = (items k, this item's rank j, partial slot base lo / hi)
+    const int4 si = split[blockIdx.x];
+    const int nt = count[it.x];
+    const int64_t pbase = (int64_t)(uint32_t)si.z | ((int64_t)si.w << 32);   // slot of (j = 0, target 0)
+    p2p_range<T>(it.x, s0, s0 + it.z, (it.w & 2) != 0, partial + 4 * (pbase + (int64_t)si.y * nt), first, count,
+                 rec, xq, icentre, cu2f, near, buf, part, threadIdx.x);
+    __threadfence();
+    __syncthreads();
+    int32_t* ctr = arrived + (blockIdx.x - si.y);   // the leaf's first item
+    if (threadIdx.x == 0) last = atomicAdd(ctr, 1) == si.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int tf = first[it.x];
+    for (int t = threadIdx.x; t < nt; t += P2P_THREADS) {
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int j = 0; j < si.x; j++) {
+            const double* q = partial + 4 * (pbase + (int64_t)j * nt + t);
+            a0 += __ldcg(q); a1 += __ldcg(q + 1); a2 += __ldcg(q + 2); a3 += __ldcg(q + 3);
+        }
+        double* o = near + 4 * ((int64_t)tf + t);
+        o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3;
+    }
+    if (threadIdx.x == 0) *ctr = 0;   // ready for the next evaluation
 }
 
 // L2P + near field + output in input order, one thread per sorted particle
@@ -400,6 +438,14 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st) {
     if ((rc = dev_alloc(&xq, xb, t, st))) return rc;
     if ((rc = dev_alloc(&d.near, (size_t)t->n * 4, t, st))) return rc;
     d.M = M; d.L = L; d.xq = xq;
+    // partial slots of the split P2P leaves: their number comes back from the
+    // build through the pinned words (the build's work has to finish before it
+    // returns anyway, so waiting for it here costs next to nothing)
+    if (d.p2p_items && t->h_pin) {
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+        const int64_t nslot = (int64_t)(uint32_t)t->h_pin[2] | ((int64_t)t->h_pin[3] << 32);
+        if (nslot > 0 && (rc = dev_alloc(&d.p2p_part, (size_t)nslot * 4, t, st))) return rc;
+    }
     {
         const int K2 = 2 * ntri(t->prm.p);
         size_t tsz = exp_fp64(t) ? sizeof(double) : sizeof(float);
@@ -557,12 +603,19 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
         FMM_CUDA_TRY(cudaStreamWaitEvent(sp, t->ev_fork, 0));
     }
     stage_begin(t, FMM_STAGE_P2P, sp);
-    if (p2p_fp64(t))
-        k_p2p<double><<<t->nleaf, P2P_THREADS, 0, sp>>>(t->nleaf, d.leaves, d.first, d.count, d.p2p_start,
-                                                          d.p2p_rec, xq64, d.icentre, d.cu2f, d.near);
+    // the item count from the build (pinned host words), else the bound with the
+    // surplus blocks returning at once; split leaves add into a zeroed near
+    const unsigned nitems = (unsigned)(t->h_pin && t->h_pin[0] >= 0 ? t->h_pin[0] : t->p2p_items_bound);
+    if (nitems == 0)
+        ;
+    else if (p2p_fp64(t))
+        k_p2p<double><<<nitems, P2P_THREADS, 0, sp>>>(d.p2p_items, d.p2p_nitems, d.p2p_split, d.p2p_arrived,
+                                                        d.p2p_part, d.first, d.count, d.p2p_start,
+                                                        d.p2p_rec, xq64, d.icentre, d.cu2f, d.near);
     else
-        k_p2p<float><<<t->nleaf, P2P_THREADS, 0, sp>>>(t->nleaf, d.leaves, d.first, d.count, d.p2p_start,
-                                                         d.p2p_rec, xq32, d.icentre, d.cu2f, d.near);
+        k_p2p<float><<<nitems, P2P_THREADS, 0, sp>>>(d.p2p_items, d.p2p_nitems, d.p2p_split, d.p2p_arrived,
+                                                       d.p2p_part, d.first, d.count, d.p2p_start,
+                                                       d.p2p_rec, xq32, d.icentre, d.cu2f, d.near);
     count_launch(t);
     stage_end(t, FMM_STAGE_P2P, sp);
     if (sp != st) FMM_CUDA_TRY(cudaEventRecord(t->ev_join, sp));

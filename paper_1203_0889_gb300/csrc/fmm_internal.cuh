@@ -166,6 +166,19 @@ struct TreeDev {
     int32_t* p2p_src = nullptr;
     int32_t* m2l_tgt = nullptr;   // [nm2l] target of each list entry (class build only)
     int4* p2p_rec = nullptr;      // [np2p] (first, count, particle offset within the target's sources, source)
+    // stage-by-stage P2P work items (target cell, first record - p2p_start[cell],
+    // records, flags: 1 = the leaf is split over several items, 2 = the item adds
+    // the leaf's own particles); leaves split into runs of P2P_ITEM_RECORDS
+    // records come first.  p2p_nitems: [items, split items, partial slots (low,
+    // high word)].
+    // Split items: p2p_split (items of the leaf, rank, first partial slot of the
+    // leaf as two words), p2p_arrived (per leaf, at its first item: blocks done,
+    // back to 0 after the combine), p2p_part (4 doubles per slot: item x target)
+    int4* p2p_items = nullptr;
+    int32_t* p2p_nitems = nullptr;
+    int4* p2p_split = nullptr;
+    int32_t* p2p_arrived = nullptr;
+    double* p2p_part = nullptr;
     // tensor-core M2L (FMM_PREC_MIXED_TC): pairs grouped by translation class
     int4* tc_items = nullptr;     // [tc_nitems] (class, first pair, rows, -)
     int32_t* tc_block_first = nullptr;  // [tc_nblocks + 1] range of each tensor-core block in tc_item_list
@@ -234,6 +247,12 @@ struct fmm_tree {
     int64_t n = 0;
     int ncell = 0, nlevel = 0, nleaf = 0;
     int64_t nm2l = 0, np2p = 0;
+    // P2P work items: host bound of their number (the grid when the exact count
+    // is not on the host), and pinned host words [items, split items] copied
+    // from p2p_nitems during the build (valid once the build has synchronised);
+    // without them no leaf is split
+    int64_t p2p_items_bound = 0;
+    int32_t* h_pin = nullptr;
     int level_start[FMM_MAX_LEVEL + 2] = {0};  // cells of level l: [level_start[l], level_start[l+1])
     double origin[3] = {0, 0, 0}, side = 1.0;
     int64_t device_bytes = 0;
@@ -278,6 +297,12 @@ inline void count_launch(fmm_tree* t, int k = 1) {
     if (t && t->launch_ctr) *t->launch_ctr += k;
 }
 int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st);
+// a slot of PIN_WORDS pinned host words for one tree (nullptr when none is free)
+constexpr int PIN_WORDS = 4;
+int32_t* pinned_slot_acquire();
+void pinned_slot_release(int32_t* p);
+// records per P2P work item of a split leaf
+constexpr int P2P_ITEM_RECORDS = 64;
 int evaluate_impl(fmm_tree* t, const void* q, void* phi, void* force, int dtype, cudaStream_t st);
 int alloc_eval_workspace(fmm_tree* t, cudaStream_t st);
 int set_positions_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st);

@@ -436,12 +436,17 @@ struct P2PBlocking { static constexpr int TPT = 2; };
 // Barrier of the P2P_THREADS threads running p2p_leaf: the whole block, or a
 // named barrier of one 128-thread group inside a larger block.
 
+// p2p_range: records s0 .. s1 - 1 of the leaf's list only (a contiguous run of
+// its source stream); own: add the leaf's own particles (FP32: they are staged
+// at zero charge and added by a guarded loop); partial: when not null, the
+// sums go to partial[4 t + 0..3] (t = target within the leaf) instead of near
+// (the leaf's list is split over several blocks, combined afterwards).
 template <typename T, typename Sync = BlockSync>
-__device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t* __restrict__ count,
-                         const int64_t* __restrict__ start, const int4* __restrict__ rec,
-                         const typename Vec4<T>::type* __restrict__ xq, const int4* __restrict__ icentre,
-                         const float* __restrict__ cu2f, double* __restrict__ near, typename Vec4<T>::type* buf,
-                         T (*part)[4], int tix, Sync sync = Sync()) {
+__device__ void p2p_range(int c, int64_t s0, int64_t s1, bool own, double* partial, const int32_t* __restrict__ first,
+                          const int32_t* __restrict__ count, const int4* __restrict__ rec,
+                          const typename Vec4<T>::type* __restrict__ xq, const int4* __restrict__ icentre,
+                          const float* __restrict__ cu2f, double* __restrict__ near, typename Vec4<T>::type* buf,
+                          T (*part)[4], int tix, Sync sync = Sync()) {
     typedef typename Vec4<T>::type V;
     constexpr int TPT = P2PBlocking<T>::TPT;
     static_assert(sizeof(T) == 8 || TPT == 2, "the paired FP32 loop holds two targets");
@@ -450,9 +455,8 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
     constexpr int NB = sizeof(T) == 4 ? P2P_BUF / 2 : P2P_BUF;
     const int warp = tix >> 5, lane = tix & 31;
     const int tf = first[c], nt = count[c];
-    const int64_t s0 = start[c], s1 = start[c + 1];
-    int total = 0;
-    if (s1 > s0) { const int4 r = rec[s1 - 1]; total = r.z + r.y; }
+    int sb = 0, se = 0;   // the records' run of the source stream
+    if (s1 > s0) { sb = rec[s0].z; const int4 r = rec[s1 - 1]; se = r.z + r.y; }
     const int4 ict = icentre[c];
     const float u2f = cu2f[c];   // side/2^22 of the target's system (sources share it)
     for (int tb = 0; tb < nt; tb += TPT * P2P_THREADS) {
@@ -477,8 +481,8 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
             Z = f2::pack(me[0].z, me[1].z);
         }
         int64_t e_lo = s0;
-        for (int base = 0; base < total; base += NB) {
-            const int lim = min(NB, total - base);
+        for (int base = sb; base < se; base += NB) {
+            const int lim = min(NB, se - base);
             for (int64_t e = e_lo + warp; e < s1; e += P2P_THREADS / 32) {
                 const int4 r = rec[e];
                 if (r.z >= base + NB) break;
@@ -535,7 +539,7 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
         }
         if constexpr (sizeof(T) == 4) {
             // the target leaf's own particles (same leaf frame, no shift), guarded
-            if (active) {
+            if (active && own) {
                 for (int j = sub; j < nt; j += G) {
                     const V s = xq[tf + j];
                     const ulonglong2 s01 = make_ulonglong2(f2::pack(-s.x, -s.x), f2::pack(-s.y, -s.y));
@@ -562,12 +566,29 @@ __device__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t
                     a0 += part[k][0]; a1 += part[k][1]; a2 += part[k][2]; a3 += part[k][3];
                 }
                 const int64_t i = tf + tb + TPT * tix + h;
-                near[4 * i] = (double)a0; near[4 * i + 1] = (double)a1; near[4 * i + 2] = (double)a2;
-                near[4 * i + 3] = (double)a3;
+                if (partial) {
+                    double* o = partial + 4 * (i - tf);
+                    o[0] = (double)a0; o[1] = (double)a1; o[2] = (double)a2; o[3] = (double)a3;
+                } else {
+                    near[4 * i] = (double)a0; near[4 * i + 1] = (double)a1; near[4 * i + 2] = (double)a2;
+                    near[4 * i + 3] = (double)a3;
+                }
             }
             sync();
         }
     }
+}
+
+// the whole list of target leaf c
+template <typename T, typename Sync = BlockSync>
+__device__ __forceinline__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t* __restrict__ count,
+                                         const int64_t* __restrict__ start, const int4* __restrict__ rec,
+                                         const typename Vec4<T>::type* __restrict__ xq,
+                                         const int4* __restrict__ icentre, const float* __restrict__ cu2f,
+                                         double* __restrict__ near, typename Vec4<T>::type* buf, T (*part)[4], int tix,
+                                         Sync sync = Sync()) {
+    p2p_range<T, Sync>(c, start[c], start[c + 1], true, nullptr, first, count, rec, xq, icentre, cu2f, near, buf, part,
+                       tix, sync);
 }
 
 // ---------------------------------------------------------------- L2P

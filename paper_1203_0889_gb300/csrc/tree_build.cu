@@ -846,6 +846,52 @@ __global__ void k_p2p_records(int64_t np, const int32_t* src, const int32_t* tgt
     rec[e] = make_int4(first[s], count[s], (int)(gcum[e] - gcum[start[tgt[e]]]), s);
 }
 
+// P2P work items of the stage-by-stage kernel.  A leaf whose list holds more
+// than P2P_ITEM_RECORDS source records (a coarse leaf beside much finer ones
+// can hold thousands) is split into runs of that many records, so that no
+// block carries a large share of the kernel; the split leaves' items come
+// first in the grid, then one item per other leaf.
+__global__ void k_p2p_item_counts(int nleaf, int split_ok, const int32_t* __restrict__ leaves,
+                                  const int64_t* __restrict__ start, const int32_t* __restrict__ count,
+                                  int32_t* nsplit, int32_t* nwhole, int64_t* nslot) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nleaf) return;
+    const int c = leaves[i];
+    const int64_t nrec = start[c + 1] - start[c];
+    const int k = split_ok && nrec > P2P_ITEM_RECORDS ? (int)((nrec + P2P_ITEM_RECORDS - 1) / P2P_ITEM_RECORDS) : 1;
+    nsplit[i] = k > 1 ? k : 0;
+    nwhole[i] = k > 1 ? 0 : 1;
+    nslot[i] = k > 1 ? (int64_t)k * count[c] : 0;   // partial slots: items x targets
+}
+__global__ void k_p2p_items(int nleaf, const int32_t* __restrict__ leaves, const int64_t* __restrict__ start,
+                            const int32_t* __restrict__ nsplit, const int32_t* __restrict__ osplit,
+                            const int32_t* __restrict__ owhole, const int64_t* __restrict__ nslot,
+                            const int64_t* __restrict__ oslot, int4* items, int4* split, int32_t* nitems) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nleaf) return;
+    const int c = leaves[i];
+    const int nrec = (int)(start[c + 1] - start[c]);
+    const int nsp = osplit[nleaf - 1] + nsplit[nleaf - 1];   // items of split leaves
+    const int k = nsplit[i];
+    if (k > 0) {
+        const int64_t b = oslot[i];
+        for (int j = 0; j < k; j++) {
+            items[osplit[i] + j] = make_int4(c, j * P2P_ITEM_RECORDS, min(P2P_ITEM_RECORDS, nrec - j * P2P_ITEM_RECORDS),
+                                             1 | (j == 0 ? 2 : 0));
+            split[osplit[i] + j] = make_int4(k, j, (int)(uint32_t)b, (int)(b >> 32));
+        }
+    } else {
+        items[nsp + owhole[i]] = make_int4(c, 0, nrec, 2);
+    }
+    if (i == nleaf - 1) {
+        nitems[0] = nsp + owhole[i] + (k > 0 ? 0 : 1);
+        nitems[1] = nsp;
+        const int64_t ns = oslot[i] + nslot[i];   // partial slots, as two words
+        nitems[2] = (int32_t)(uint32_t)ns;
+        nitems[3] = (int32_t)(ns >> 32);
+    }
+}
+
 __global__ void k_leaf_flags(int ncell, const int32_t* child_count, char* flag, int32_t* iota) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < ncell) { flag[c] = child_count[c] == 0; iota[c] = c; }
@@ -969,6 +1015,38 @@ static int finish_p2p_list(fmm_tree* t, int2* pairs, int64_t np, cudaStream_t st
     dev_free(cnt, st);
     dev_free(gcum, st);
     dev_free(tgt, st);
+    // work items of the stage-by-stage P2P kernel; their count reaches the
+    // tree's pinned words when the build synchronises
+    if (t->nleaf > 0) {
+        const int nl = t->nleaf;
+        t->p2p_items_bound = nl + (np + P2P_ITEM_RECORDS - 1) / P2P_ITEM_RECORDS;
+        int32_t* w = nullptr;
+        int64_t* w64 = nullptr;
+        const size_t nb = (size_t)t->p2p_items_bound;
+        if ((rc = dev_alloc(&d.p2p_items, nb, t, st))) return rc;
+        if ((rc = dev_alloc(&d.p2p_split, nb, t, st))) return rc;
+        if ((rc = dev_alloc(&d.p2p_arrived, nb, t, st))) return rc;
+        if ((rc = dev_alloc(&d.p2p_nitems, 4, t, st))) return rc;
+        if ((rc = dev_alloc(&w, (size_t)4 * nl, nullptr, st))) return rc;
+        if ((rc = dev_alloc(&w64, (size_t)2 * nl, nullptr, st))) return rc;
+        FMM_CUDA_TRY(cudaMemsetAsync(d.p2p_arrived, 0, sizeof(int32_t) * nb, st));
+        k_p2p_item_counts<<<nblk(nl, 256), 256, 0, st>>>(nl, t->h_pin ? 1 : 0, d.leaves, d.p2p_start, d.count, w,
+                                                          w + nl, w64);
+        size_t sb = 0, sb64 = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, sb, w, w + 2 * nl, nl, st);
+        cub::DeviceScan::ExclusiveSum(nullptr, sb64, w64, w64 + nl, nl, st);
+        if ((rc = dev_alloc(&tmp, std::max(sb, sb64), nullptr, st))) return rc;
+        FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, w, w + 2 * nl, nl, st));
+        FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, w + nl, w + 3 * nl, nl, st));
+        FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb64, w64, w64 + nl, nl, st));
+        k_p2p_items<<<nblk(nl, 256), 256, 0, st>>>(nl, d.leaves, d.p2p_start, w, w + 2 * nl, w + 3 * nl, w64, w64 + nl,
+                                                    d.p2p_items, d.p2p_split, d.p2p_nitems);
+        count_launch(t, 5);
+        if (t->h_pin) FMM_CUDA_TRY(cudaMemcpyAsync(t->h_pin, d.p2p_nitems, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        dev_free(tmp, st);
+        dev_free(w, st);
+        dev_free(w64, st);
+    }
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
@@ -1436,7 +1514,8 @@ void free_tree_device(fmm_tree* t) {
     dev_free(d.geom, st); dev_free(d.status, st);
     if (d.grad_tmp) cudaFreeAsync(d.grad_tmp, st);
     d.grad_tmp = nullptr;
-    dev_free(d.m2l_tgt, st); dev_free(d.p2p_rec, st); dev_free(d.tc_items, st); dev_free(d.tc_block_first, st); dev_free(d.tc_item_list, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
+    dev_free(d.m2l_tgt, st); dev_free(d.p2p_rec, st); dev_free(d.p2p_items, st); dev_free(d.p2p_nitems, st);
+    dev_free(d.p2p_split, st); dev_free(d.p2p_arrived, st); dev_free(d.p2p_part, st); dev_free(d.tc_items, st); dev_free(d.tc_block_first, st); dev_free(d.tc_item_list, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
     dev_free(d.rem_start, st); dev_free(d.rem_chunks, st);
     dev_free(d.dag_cnt_init, st); dev_free(d.dag_cnt, st); dev_free(d.dag_q_init, st); dev_free(d.dag_q, st);
     dev_free(d.dag_lvl, st); dev_free(d.dag_ctr, st); dev_free(d.dag_zero_first, st);

@@ -12,7 +12,11 @@ from tests.gpu_common import gpu_eval, gpu_tree, torch_dev
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 1e-12), (2, 1e-5)])
+# Precision 1 (FP32 P2P, FP64 expansions): the stage-by-stage kernel splits the
+# near-field list of a leaf with many source records over several blocks and
+# adds their FP32 partial sums in FP64, where the task queue sums the whole list
+# in one FP32 stream, so the two differ by FP32 rounding of the near field.
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 1e-6), (2, 1e-5)])
 @pytest.mark.parametrize("name,n,p,leaf,theta", [("plummer", 30000, 8, 64, 0.4), ("clustered", 20000, 5, 16, 0.5),
                                                  ("uniform", 3000, 12, 32, 0.6)])
 def test_queue_matches_staged(prec, tol, name, n, p, leaf, theta):
