@@ -85,6 +85,10 @@ def parse():
     ap.add_argument("--task-graph", action="store_true",
                     help="mixed form: run the evaluation as one persistent task-graph launch (FMM_TASK_GRAPH)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--granularity-n", default="100000,1000000,10000000",
+                    help="granularity study: particle counts (comma-separated)")
+    ap.add_argument("--granularity-p", default="6,9", help="granularity study: expansion orders")
+    ap.add_argument("--granularity-leaf", default="16,32,64,128,256", help="granularity study: leaf sizes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=1 << 21,
                     help="particles of the oracle's timed sample (about 10-20 s on 16 host cores)")
@@ -905,12 +909,13 @@ def run_granularity(args):
 
     dev = torch.device("cuda", 0)
     rows = []
-    for n in (100_000, 1_000_000, 10_000_000):
+    ints = lambda s: [int(v) for v in s.split(",") if v]  # noqa: E731
+    for n in ints(args.granularity_n):
         wl = W.make_workload("uniform", n=n, seed=12030889 * 10 + 6)
         pos = torch.tensor(wl.pos, dtype=torch.float64, device=dev)
         q = torch.tensor(wl.q, dtype=torch.float32, device=dev)
-        for p in (6, 9):
-            for leaf in (16, 32, 64, 128, 256):
+        for p in ints(args.granularity_p):
+            for leaf in ints(args.granularity_leaf):
                 t = fmm.build_tree(pos, p=p, leaf_size=leaf, theta=0.5, precision=fmm.PREC_FP32)
                 info = t.info()
                 t.evaluate(q)

@@ -104,6 +104,14 @@ typedef struct {
     int32_t flags;       /* FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP | FMM_BUILD_FALLBACKS
                             | FMM_TASK_GRAPH */
     int64_t timeout_ns;  /* budget of each bounded device-side wait; 0 = 2 s */
+    /* Work-shape tunables (0 = the default; the values change the schedule,
+       not the set of pair interactions): */
+    int32_t p2p_item_records; /* stage-by-stage P2P: a leaf whose near-field list holds
+                                 more source records than this is split into work
+                                 items of this many records; 0 = 64, else 8..65536 */
+    int32_t tc_min_pairs;     /* FMM_PREC_MIXED_TC: translation classes of at most this
+                                 many M2L pairs go to the CUDA-core M2L instead of the
+                                 tensor cores; 0 = 64, else 1..4096 */
 } fmm_params;
 
 /* Sizes and geometry of a built tree. */

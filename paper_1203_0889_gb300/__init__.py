@@ -26,7 +26,7 @@ __all__ = [
     "PREC_FP64", "PREC_FP32_P2P", "PREC_FP32", "PREC_MIXED_TC", "OUT_FIELD", "STAGED", "TIMING", "NO_OVERLAP", "BUILD_FALLBACKS",
     "TASK_GRAPH",
     "FMMError", "Params", "TreeInfo", "Tree", "build_tree", "build_tree_batched", "evaluate", "library_path", "load",
-    "capture_graph", "autotune_leaf_size",
+    "capture_graph", "autotune_leaf_size", "autotune",
 ]
 
 FMM_OK, FMM_ERR_ARG, FMM_ERR_ALLOC, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, FMM_ERR_STATE = 0, -1, -2, -3, -4, -5
@@ -50,7 +50,8 @@ class FMMError(RuntimeError):
 
 class Params(C.Structure):
     _fields_ = [("p", C.c_int32), ("leaf_size", C.c_int32), ("theta", C.c_double),
-                ("precision", C.c_int32), ("flags", C.c_int32), ("timeout_ns", C.c_int64)]
+                ("precision", C.c_int32), ("flags", C.c_int32), ("timeout_ns", C.c_int64),
+                ("p2p_item_records", C.c_int32), ("tc_min_pairs", C.c_int32)]
 
 
 class TreeInfo(C.Structure):
@@ -143,14 +144,16 @@ class Tree:
     """A built octree with interaction lists, owned by the library."""
 
     def __init__(self, pos, p: int = 4, leaf_size: int = 64, theta: float = 0.5,
-                 precision: int = PREC_FP64, flags: int = 0, timeout_ns: int = 0, stream=None, offsets=None):
+                 precision: int = PREC_FP64, flags: int = 0, timeout_ns: int = 0, stream=None, offsets=None,
+                 p2p_item_records: int = 0, tc_min_pairs: int = 0):
         torch = _torch()
         lib = load()
         if not (pos.is_cuda and pos.dim() == 2 and pos.shape[1] == 3):
             raise ValueError("pos must be a CUDA tensor of shape (n, 3)")
         self._pos_key = _tensor_key(pos)
         pos = pos.contiguous()
-        self.params = Params(int(p), int(leaf_size), float(theta), int(precision), int(flags), int(timeout_ns))
+        self.params = Params(int(p), int(leaf_size), float(theta), int(precision), int(flags), int(timeout_ns),
+                             int(p2p_item_records), int(tc_min_pairs))
         self.n = int(pos.shape[0])
         self.device = pos.device
         h = _P()
@@ -308,6 +311,47 @@ def autotune_leaf_size(pos, q, offsets=None, candidates=(24, 32, 48, 64, 96, 128
                 best = min(best, e0.elapsed_time(e1))
         times[int(leaf)] = best
     return min(times, key=times.get), times
+
+
+def _time_build_evaluate(pos, q, offsets, repeats, kw):
+    """Best of `repeats` timed build + evaluate runs (after one untimed run), ms."""
+    torch = _torch()
+    best = float("inf")
+    for r in range(repeats + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        t = Tree(pos, offsets=offsets, **kw)
+        t.evaluate(q)
+        e1.record()
+        torch.cuda.synchronize()
+        t.close()
+        if r > 0:
+            best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def autotune(pos, q, offsets=None, leaf_sizes=(32, 48, 64, 96), p2p_item_records=(16, 32, 64, 128, 256),
+             tc_min_pairs=(16, 32, 64, 128, 256), repeats: int = 2, **params):
+    """Choose the work shape by measurement on the actual input: the leaf size
+    (the P2P / M2L balance), the records per P2P work item of a split leaf (the
+    near-field load balance) and, for the mixed form, the smallest translation
+    class worth a tensor-core operator.  One coordinate sweep in that order,
+    each starting from the best values found so far.  Returns (best keyword
+    arguments for build_tree, {(name, value): ms}).  Every candidate computes
+    the same pair interactions; only the schedule differs."""
+    best = dict(params)
+    best.setdefault("leaf_size", 64)
+    times = {}
+    sweeps = [("leaf_size", leaf_sizes), ("p2p_item_records", p2p_item_records)]
+    if params.get("precision", PREC_FP64) == PREC_MIXED_TC:
+        sweeps.append(("tc_min_pairs", tc_min_pairs))
+    for name, values in sweeps:
+        scored = {}
+        for v in values:
+            kw = dict(best, **{name: int(v)})
+            scored[int(v)] = times[(name, int(v))] = _time_build_evaluate(pos, q, offsets, repeats, kw)
+        best[name] = min(scored, key=scored.get)
+    return best, times
 
 
 def evaluate(tree: Tree, q, **kw):

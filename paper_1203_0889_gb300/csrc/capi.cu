@@ -35,6 +35,14 @@ int check_params(const fmm_params* prm) {
     }
     if (prm->flags & ~(FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP | FMM_BUILD_FALLBACKS | FMM_TASK_GRAPH)) { fmm_set_error("unknown flags 0x%x", prm->flags); return FMM_ERR_ARG; }
     if (prm->timeout_ns < 0) { fmm_set_error("timeout_ns < 0"); return FMM_ERR_ARG; }
+    if (prm->p2p_item_records != 0 && (prm->p2p_item_records < 8 || prm->p2p_item_records > 65536)) {
+        fmm_set_error("p2p_item_records=%d outside {0} and [8, 65536]", prm->p2p_item_records);
+        return FMM_ERR_ARG;
+    }
+    if (prm->tc_min_pairs != 0 && (prm->tc_min_pairs < 1 || prm->tc_min_pairs > 4096)) {
+        fmm_set_error("tc_min_pairs=%d outside {0} and [1, 4096]", prm->tc_min_pairs);
+        return FMM_ERR_ARG;
+    }
     return FMM_OK;
 }
 
@@ -122,6 +130,8 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
     if (offsets) t->h_sys_off = *offsets;
     t->prm = *params;
     if (t->prm.timeout_ns == 0) t->prm.timeout_ns = 2000000000LL;
+    if (t->prm.p2p_item_records == 0) t->prm.p2p_item_records = fmm::P2P_ITEM_RECORDS;
+    if (t->prm.tc_min_pairs == 0) t->prm.tc_min_pairs = fmm::TC_MIN_PAIRS;
     t->n = n;
     if (t->h_sys_off.empty()) t->h_sys_off = {0, n};
     t->nsys = (int)t->h_sys_off.size() - 1;
@@ -158,12 +168,21 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
             if (t->ev_join) cudaEventDestroy(t->ev_join);
             t->side_stream = nullptr; t->ev_fork = nullptr; t->ev_join = nullptr; t->ev_ops = nullptr;
         }
-        if (t->side_stream && t->prm.precision == FMM_PREC_MIXED_TC &&
-            cudaStreamCreateWithFlags(&t->ops_stream, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            t->ops_stream = nullptr;
-        }
         int least = 0, greatest = 0;
+        // the mixed form's third stream: the class operators at build time, the
+        // CUDA-core M2L pairs beside the tensor-core kernel at evaluation time
+        // (on the far field's critical path, hence the high priority)
+        if (t->side_stream && t->prm.precision == FMM_PREC_MIXED_TC &&
+            (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+             cudaStreamCreateWithPriority(&t->ops_stream, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+             cudaEventCreateWithFlags(&t->ev_rem_fork, cudaEventDisableTiming) != cudaSuccess ||
+             cudaEventCreateWithFlags(&t->ev_rem_join, cudaEventDisableTiming) != cudaSuccess)) {
+            cudaGetLastError();
+            if (t->ops_stream) cudaStreamDestroy(t->ops_stream);
+            if (t->ev_rem_fork) cudaEventDestroy(t->ev_rem_fork);
+            if (t->ev_rem_join) cudaEventDestroy(t->ev_rem_join);
+            t->ops_stream = nullptr; t->ev_rem_fork = nullptr; t->ev_rem_join = nullptr;
+        }
         if (t->side_stream && (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
                                cudaStreamCreateWithPriority(&t->hi_stream, cudaStreamNonBlocking, greatest) !=
                                    cudaSuccess ||
@@ -193,6 +212,8 @@ static int build_common(const fmm_params* params, int64_t n, const void* pos, in
         if (t->ev_join) cudaEventDestroy(t->ev_join);
         if (t->ev_join_hi) cudaEventDestroy(t->ev_join_hi);
         if (t->ev_ops) cudaEventDestroy(t->ev_ops);
+        if (t->ev_rem_fork) cudaEventDestroy(t->ev_rem_fork);
+        if (t->ev_rem_join) cudaEventDestroy(t->ev_rem_join);
         fmm::pinned_slot_release(t->h_pin);
         delete t;
         return rc;
@@ -411,6 +432,8 @@ void fmm_tree_destroy(fmm_tree* t) {
     if (t->ev_fork) cudaEventDestroy(t->ev_fork);
     if (t->ev_join) cudaEventDestroy(t->ev_join);
     if (t->ev_ops) cudaEventDestroy(t->ev_ops);
+    if (t->ev_rem_fork) cudaEventDestroy(t->ev_rem_fork);
+    if (t->ev_rem_join) cudaEventDestroy(t->ev_rem_join);
     fmm::pinned_slot_release(t->h_pin);
     delete t;
 }

@@ -246,11 +246,18 @@ __global__ void k_p2m(int p, int nleaf, const int32_t* __restrict__ leaves, cons
                       const int32_t* __restrict__ count, const double4_32a* __restrict__ centre,
                       const double4_32a* __restrict__ xq, cplx<T>* __restrict__ M) {
     extern __shared__ unsigned char smem_raw[];
+    // the recurrence's reciprocals from tables holding the values the
+    // divisions give (the same products as the division form)
+    __shared__ T rm[FMM_MAX_P + 1], rt[(FMM_MAX_P + 1) * (FMM_MAX_P + 2) / 2];
+    for (int m = threadIdx.x; m <= p; m += blockDim.x) rm[m] = m > 0 ? T(1) / T(2 * m) : T(0);
+    for (int n = 0; n <= p; n++)
+        for (int m = threadIdx.x; m <= n; m += blockDim.x) rt[tri(n, m)] = n >= m + 2 ? T(1) / T((n + m) * (n - m)) : T(0);
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     cplx<T>* acc = reinterpret_cast<cplx<T>*>(smem_raw) + warp * ntri(p);
     const int li = blockIdx.x * (blockDim.x >> 5) + warp;
     if (li >= nleaf) return;
-    p2m_leaf<T>(p, leaves[li], lane, first, count, centre, xq, M, acc);
+    p2m_leaf<T>(p, leaves[li], lane, first, count, centre, xq, M, acc, rm, rt);
 }
 
 // M2L (any pair of cells): one warp per target, each half-warp one source
@@ -673,15 +680,31 @@ static int far_field(fmm_tree* t, cplx<T>* M, cplx<T>* L, const double4_32a* xq6
     int rc;
     if (d.rem_start) {
         // every L from zero, then the pairs the tensor cores do not take on the
-        // CUDA cores in chunks, then the classes on the tensor cores; both add
-        // into L
+        // CUDA cores in chunks (atomics into L), and the classes on the tensor
+        // cores (into the real-basis accumulator, folded into L at the end).
+        // With a third stream the chunks run beside the tensor-core kernel and
+        // join before the fold, which reads and writes L.
         FMM_CUDA_TRY(cudaMemsetAsync(L, 0, sizeof(cplx<T>) * (size_t)t->ncell * kstride(p), st));
         rc = FMM_OK;
+        cudaEvent_t rem_done = nullptr;
         if constexpr (sizeof(T) == 4) {
-            if (t->rem_nchunk > 0) rc = launch_m2l_chunks(t, p, d, (const cplx<float>*)M, (float*)L, st);
+            if (t->rem_nchunk > 0) {
+                cudaStream_t sr = st;
+                if (t->ops_stream && t->ev_rem_fork && t->ev_rem_join && t->tc_nitems > 0 &&
+                    !(t->prm.flags & FMM_NO_OVERLAP)) {
+                    sr = t->ops_stream;
+                    FMM_CUDA_TRY(cudaEventRecord(t->ev_rem_fork, st));
+                    FMM_CUDA_TRY(cudaStreamWaitEvent(sr, t->ev_rem_fork, 0));
+                }
+                rc = launch_m2l_chunks(t, p, d, (const cplx<float>*)M, (float*)L, sr);
+                if (!rc && sr != st) {
+                    FMM_CUDA_TRY(cudaEventRecord(t->ev_rem_join, sr));
+                    rem_done = t->ev_rem_join;
+                }
+            }
         }
         if (rc) return rc;
-        rc = m2l_tensor_cores(t, (const float*)M, (float*)L, st);
+        rc = m2l_tensor_cores(t, (const float*)M, (float*)L, st, rem_done);
     } else {
         rc = launch_m2l_generic<T>(t, p, 0, t->ncell, d.m2l_start, d.m2l_src, d, M, L, st);
     }

@@ -168,7 +168,7 @@ struct TreeDev {
     int4* p2p_rec = nullptr;      // [np2p] (first, count, particle offset within the target's sources, source)
     // stage-by-stage P2P work items (target cell, first record - p2p_start[cell],
     // records, flags: 1 = the leaf is split over several items, 2 = the item adds
-    // the leaf's own particles); leaves split into runs of P2P_ITEM_RECORDS
+    // the leaf's own particles); leaves split into runs of prm.p2p_item_records
     // records come first.  p2p_nitems: [items, split items, partial slots (low,
     // high word)].
     // Split items: p2p_split (items of the leaf, rank, first partial slot of the
@@ -243,6 +243,8 @@ struct fmm_tree {
     // the tensor-core class operators are built on a stream of their own (they
     // overlap the rest of the build and the start of the evaluation)
     cudaStream_t ops_stream = nullptr;
+    // fork and join of the CUDA-core M2L pairs on ops_stream during evaluation
+    cudaEvent_t ev_rem_fork = nullptr, ev_rem_join = nullptr;
     int64_t* launch_ctr = nullptr;  // which counter launches currently go to
     int64_t n = 0;
     int ncell = 0, nlevel = 0, nleaf = 0;
@@ -301,15 +303,21 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
 constexpr int PIN_WORDS = 4;
 int32_t* pinned_slot_acquire();
 void pinned_slot_release(int32_t* p);
-// records per P2P work item of a split leaf
+// defaults of the work-shape tunables (fmm_params): records per P2P work item
+// of a split leaf; the largest class left to the CUDA-core M2L (the
+// tensor-core kernel assembles one operator per class, which does not pay for
+// a handful of pairs: on a clustered 4M-particle tree 97 % of the classes hold
+// under 1 % of the pairs)
 constexpr int P2P_ITEM_RECORDS = 64;
+constexpr int TC_MIN_PAIRS = 64;
 int evaluate_impl(fmm_tree* t, const void* q, void* phi, void* force, int dtype, cudaStream_t st);
 int alloc_eval_workspace(fmm_tree* t, cudaStream_t st);
 int set_positions_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st);
 int grad_combine(fmm_tree* t, const void* q, const void* w, const void* eq, const void* ew, void* dx, int dtype,
                  cudaStream_t st);
 int build_m2l_classes(fmm_tree* t, const int2* pairs, cudaStream_t st);
-int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st);
+// before_fold: an event the fold into L waits for (other M2L work adding into L)
+int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st, cudaEvent_t before_fold = nullptr);
 int tc_kin(int p);
 bool queue_supported(const fmm_tree* t);
 int build_queue(fmm_tree* t, cudaStream_t st);

@@ -469,14 +469,11 @@ static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const in
     return FMM_OK;
 }
 
-// A class with at most TC_MIN_PAIRS pairs is left to the CUDA-core kernel: the
-// tensor-core kernel assembles one operator per class, which does not pay for
-// a handful of pairs (on a clustered 4M-particle tree, 97 % of the classes hold
-// under 1 % of the pairs).
-constexpr int TC_MIN_PAIRS = 64;
+// A class with at most prm.tc_min_pairs pairs (default TC_MIN_PAIRS) is left
+// to the CUDA-core kernel.
 
 // flag[i] = pair i (of `order`, classes in class order first) belongs to a kept class
-__global__ void k_pair_keep(int64_t np, int64_t ntc, int nclass, const int32_t* __restrict__ cfirst,
+__global__ void k_pair_keep(int64_t np, int64_t ntc, int nclass, int min_pairs, const int32_t* __restrict__ cfirst,
                             const int32_t* __restrict__ counts, char* __restrict__ flag) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= np) return;
@@ -487,16 +484,16 @@ __global__ void k_pair_keep(int64_t np, int64_t ntc, int nclass, const int32_t* 
             const int mid = (lo + hi) >> 1;
             if (cfirst[mid] <= i) lo = mid; else hi = mid;
         }
-        f = counts[lo] > TC_MIN_PAIRS;
+        f = counts[lo] > min_pairs;
     }
     flag[i] = f;
 }
-__global__ void k_class_keep(int nclass, const int32_t* __restrict__ counts, char* __restrict__ keep) {
+__global__ void k_class_keep(int nclass, int min_pairs, const int32_t* __restrict__ counts, char* __restrict__ keep) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < nclass) keep[c] = counts[c] > TC_MIN_PAIRS;
+    if (c < nclass) keep[c] = counts[c] > min_pairs;
 }
 
-// Drops the classes of at most TC_MIN_PAIRS pairs: order[np] (pair indices, the
+// Drops the classes of at most prm.tc_min_pairs pairs: order[np] (pair indices, the
 // ntc classed ones in class order first) is partitioned stably into the kept
 // classes' pairs followed by all others; ukeys and counts are compacted to the
 // kept classes; nclass and ntc are updated.
@@ -526,8 +523,8 @@ static int drop_small_classes(fmm_tree* t, int64_t np, int32_t* order, int& ncla
     tb = std::max(tb, tb2);
     if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
     FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, counts, cfirst, nclass, st));
-    k_pair_keep<<<nblk(np, 256), 256, 0, st>>>(np, ntc, nclass, cfirst, counts, flag);
-    k_class_keep<<<nblk(nclass, 256), 256, 0, st>>>(nclass, counts, keep);
+    k_pair_keep<<<nblk(np, 256), 256, 0, st>>>(np, ntc, nclass, t->prm.tc_min_pairs, cfirst, counts, flag);
+    k_class_keep<<<nblk(nclass, 256), 256, 0, st>>>(nclass, t->prm.tc_min_pairs, counts, keep);
     FMM_CUDA_TRY(cub::DevicePartition::Flagged(tmp, tb, order, flag, order2, nsel, np, st));
     FMM_CUDA_TRY(cub::DeviceSelect::Flagged(tmp, tb, ukeys, keep, ukeys2, nsel + 1, nclass, st));
     FMM_CUDA_TRY(cub::DeviceSelect::Flagged(tmp, tb, counts, keep, counts2, nsel + 2, nclass, st));
@@ -1382,7 +1379,7 @@ static int tc_setup(fmm_tree* t, size_t wscratch, TcArgs& a, size_t& smem, cudaS
     return FMM_OK;
 }
 
-int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st) {
+int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st, cudaEvent_t before_fold) {
     TreeDev& d = t->d;
     const int p = t->prm.p, KR = tc_kreal(p), KI = tc_kin(p), KS = kstride(p);
     if (t->tc_nitems == 0) return FMM_OK;
@@ -1397,6 +1394,7 @@ int m2l_tensor_cores(fmm_tree* t, const float* M, float* L, cudaStream_t st) {
     k_m2l_tc<false, float, 3><<<t->tc_nblocks, TC_THREADS, smem, st>>>(t->tc_tmap, a, DagArgs{});
     count_launch(t);
     stage_end(t, FMM_STAGE_M2L_TC, st);
+    if (before_fold) FMM_CUDA_TRY(cudaStreamWaitEvent(st, before_fold, 0));
     k_fold_real<<<nblk((int64_t)t->ncell * KR, 256), 256, 0, st>>>(t->ncell, KR, 2 * KS, (const float*)d.tc_lr, L);
     count_launch(t);
     FMM_CUDA_TRY(cudaGetLastError());

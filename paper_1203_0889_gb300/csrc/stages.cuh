@@ -44,7 +44,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 template <typename T>
 __device__ void p2m_leaf(int p, int c, int lane, const int32_t* __restrict__ first, const int32_t* __restrict__ count,
                          const double4_32a* __restrict__ centre, const double4_32a* __restrict__ xq,
-                         cplx<T>* __restrict__ M, cplx<T>* acc) {
+                         cplx<T>* __restrict__ M, cplx<T>* acc, const T* rm = nullptr, const T* rt = nullptr) {
     const int K = ntri(p), KS = kstride(p);
     for (int j = lane; j < K; j += 32) acc[j] = cmk<T>(0, 0);
     __syncwarp();
@@ -62,14 +62,14 @@ __device__ void p2m_leaf(int p, int c, int lane, const int32_t* __restrict__ fir
         const T r2 = ux * ux + uy * uy + uz * uz;
         cplx<T> rmm = cmk<T>(q, 0);
         for (int m = 0; m <= p; m++) {
-            if (m > 0) rmm = cscale(cmul(rmm, cmk<T>(ux, uy)), T(1) / T(2 * m));
+            if (m > 0) rmm = cscale(cmul(rmm, cmk<T>(ux, uy)), rm ? rm[m] : T(1) / T(2 * m));
             cplx<T> a = rmm, b = cscale(rmm, uz);
             for (int n = m; n <= p; n++) {
                 cplx<T> v;
                 if (n == m) v = a;
                 else if (n == m + 1) v = b;
                 else {
-                    const T inv = T(1) / T((n + m) * (n - m));
+                    const T inv = rt ? rt[tri(n, m)] : T(1) / T((n + m) * (n - m));
                     v = cmk<T>((T(2 * n - 1) * uz * b.re - r2 * a.re) * inv, (T(2 * n - 1) * uz * b.im - r2 * a.im) * inv);
                     a = b; b = v;
                 }

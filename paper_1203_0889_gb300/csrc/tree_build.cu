@@ -847,23 +847,23 @@ __global__ void k_p2p_records(int64_t np, const int32_t* src, const int32_t* tgt
 }
 
 // P2P work items of the stage-by-stage kernel.  A leaf whose list holds more
-// than P2P_ITEM_RECORDS source records (a coarse leaf beside much finer ones
+// than R (prm.p2p_item_records) source records (a coarse leaf beside much finer ones
 // can hold thousands) is split into runs of that many records, so that no
 // block carries a large share of the kernel; the split leaves' items come
 // first in the grid, then one item per other leaf.
-__global__ void k_p2p_item_counts(int nleaf, int split_ok, const int32_t* __restrict__ leaves,
+__global__ void k_p2p_item_counts(int nleaf, int split_ok, int R, const int32_t* __restrict__ leaves,
                                   const int64_t* __restrict__ start, const int32_t* __restrict__ count,
                                   int32_t* nsplit, int32_t* nwhole, int64_t* nslot) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nleaf) return;
     const int c = leaves[i];
     const int64_t nrec = start[c + 1] - start[c];
-    const int k = split_ok && nrec > P2P_ITEM_RECORDS ? (int)((nrec + P2P_ITEM_RECORDS - 1) / P2P_ITEM_RECORDS) : 1;
+    const int k = split_ok && nrec > R ? (int)((nrec + R - 1) / R) : 1;
     nsplit[i] = k > 1 ? k : 0;
     nwhole[i] = k > 1 ? 0 : 1;
     nslot[i] = k > 1 ? (int64_t)k * count[c] : 0;   // partial slots: items x targets
 }
-__global__ void k_p2p_items(int nleaf, const int32_t* __restrict__ leaves, const int64_t* __restrict__ start,
+__global__ void k_p2p_items(int nleaf, int R, const int32_t* __restrict__ leaves, const int64_t* __restrict__ start,
                             const int32_t* __restrict__ nsplit, const int32_t* __restrict__ osplit,
                             const int32_t* __restrict__ owhole, const int64_t* __restrict__ nslot,
                             const int64_t* __restrict__ oslot, int4* items, int4* split, int32_t* nitems) {
@@ -876,8 +876,7 @@ __global__ void k_p2p_items(int nleaf, const int32_t* __restrict__ leaves, const
     if (k > 0) {
         const int64_t b = oslot[i];
         for (int j = 0; j < k; j++) {
-            items[osplit[i] + j] = make_int4(c, j * P2P_ITEM_RECORDS, min(P2P_ITEM_RECORDS, nrec - j * P2P_ITEM_RECORDS),
-                                             1 | (j == 0 ? 2 : 0));
+            items[osplit[i] + j] = make_int4(c, j * R, min(R, nrec - j * R), 1 | (j == 0 ? 2 : 0));
             split[osplit[i] + j] = make_int4(k, j, (int)(uint32_t)b, (int)(b >> 32));
         }
     } else {
@@ -1019,7 +1018,8 @@ static int finish_p2p_list(fmm_tree* t, int2* pairs, int64_t np, cudaStream_t st
     // tree's pinned words when the build synchronises
     if (t->nleaf > 0) {
         const int nl = t->nleaf;
-        t->p2p_items_bound = nl + (np + P2P_ITEM_RECORDS - 1) / P2P_ITEM_RECORDS;
+        const int R = t->prm.p2p_item_records;
+        t->p2p_items_bound = nl + (np + R - 1) / R;
         int32_t* w = nullptr;
         int64_t* w64 = nullptr;
         const size_t nb = (size_t)t->p2p_items_bound;
@@ -1030,7 +1030,7 @@ static int finish_p2p_list(fmm_tree* t, int2* pairs, int64_t np, cudaStream_t st
         if ((rc = dev_alloc(&w, (size_t)4 * nl, nullptr, st))) return rc;
         if ((rc = dev_alloc(&w64, (size_t)2 * nl, nullptr, st))) return rc;
         FMM_CUDA_TRY(cudaMemsetAsync(d.p2p_arrived, 0, sizeof(int32_t) * nb, st));
-        k_p2p_item_counts<<<nblk(nl, 256), 256, 0, st>>>(nl, t->h_pin ? 1 : 0, d.leaves, d.p2p_start, d.count, w,
+        k_p2p_item_counts<<<nblk(nl, 256), 256, 0, st>>>(nl, t->h_pin ? 1 : 0, R, d.leaves, d.p2p_start, d.count, w,
                                                           w + nl, w64);
         size_t sb = 0, sb64 = 0;
         cub::DeviceScan::ExclusiveSum(nullptr, sb, w, w + 2 * nl, nl, st);
@@ -1039,7 +1039,7 @@ static int finish_p2p_list(fmm_tree* t, int2* pairs, int64_t np, cudaStream_t st
         FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, w, w + 2 * nl, nl, st));
         FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb, w + nl, w + 3 * nl, nl, st));
         FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, sb64, w64, w64 + nl, nl, st));
-        k_p2p_items<<<nblk(nl, 256), 256, 0, st>>>(nl, d.leaves, d.p2p_start, w, w + 2 * nl, w + 3 * nl, w64, w64 + nl,
+        k_p2p_items<<<nblk(nl, 256), 256, 0, st>>>(nl, R, d.leaves, d.p2p_start, w, w + 2 * nl, w + 3 * nl, w64, w64 + nl,
                                                     d.p2p_items, d.p2p_split, d.p2p_nitems);
         count_launch(t, 5);
         if (t->h_pin) FMM_CUDA_TRY(cudaMemcpyAsync(t->h_pin, d.p2p_nitems, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));

@@ -49,7 +49,9 @@ def test_version_and_argument_errors(lib):
     assert b"params" in lib.fmm_last_error()
     bad = [fmm.Params(-1, 64, 0.5, 0, 0, 0), fmm.Params(4, 0, 0.5, 0, 0, 0), fmm.Params(4, 64, 1.5, 0, 0, 0),
            fmm.Params(4, 64, 0.5, 9, 0, 0), fmm.Params(4, 64, 0.5, 0, 64, 0), fmm.Params(21, 64, 0.5, 0, 0, 0),
-           fmm.Params(4, 64, 0.0, 0, 0, 0), fmm.Params(4, 64, 0.5, 0, 0, -1)]
+           fmm.Params(4, 64, 0.0, 0, 0, 0), fmm.Params(4, 64, 0.5, 0, 0, -1),
+           fmm.Params(4, 64, 0.5, 0, 0, 0, 4, 0), fmm.Params(4, 64, 0.5, 0, 0, 0, 70000, 0),
+           fmm.Params(4, 64, 0.5, 0, 0, 0, 0, -3), fmm.Params(4, 64, 0.5, 0, 0, 0, 0, 5000)]
     for prm in bad:
         assert lib.fmm_build_tree(C.byref(prm), 10, C.c_void_p(8), 0, C.byref(out), None) == fmm.FMM_ERR_ARG
         assert out.value is None
