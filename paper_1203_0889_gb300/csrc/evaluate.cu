@@ -448,10 +448,13 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st) {
     // partial slots of the split P2P leaves: their number comes back from the
     // build through the pinned words (the build's work has to finish before it
     // returns anyway, so waiting for it here costs next to nothing)
-    if (d.p2p_items && t->h_pin) {
+    if (t->h_pin && (d.p2p_items || t->rem_nchunk < 0)) {
         FMM_CUDA_TRY(cudaStreamSynchronize(st));
-        const int64_t nslot = (int64_t)(uint32_t)t->h_pin[2] | ((int64_t)t->h_pin[3] << 32);
-        if (nslot > 0 && (rc = dev_alloc(&d.p2p_part, (size_t)nslot * 4, t, st))) return rc;
+        if (d.p2p_items) {
+            const int64_t nslot = (int64_t)(uint32_t)t->h_pin[2] | ((int64_t)t->h_pin[3] << 32);
+            if (nslot > 0 && (rc = dev_alloc(&d.p2p_part, (size_t)nslot * 4, t, st))) return rc;
+        }
+        if (t->rem_nchunk < 0) t->rem_nchunk = t->h_pin[4];
     }
     {
         const int K2 = 2 * ntri(t->prm.p);

@@ -176,6 +176,7 @@ struct TreeDev {
     // back to 0 after the combine), p2p_part (4 doubles per slot: item x target)
     int4* p2p_items = nullptr;
     int32_t* p2p_nitems = nullptr;
+    int32_t* rem_count = nullptr;   // chunks of the CUDA-core M2L (device word, copied to h_pin[4])
     int4* p2p_split = nullptr;
     int32_t* p2p_arrived = nullptr;
     double* p2p_part = nullptr;
@@ -300,7 +301,7 @@ inline void count_launch(fmm_tree* t, int k = 1) {
 }
 int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st);
 // a slot of PIN_WORDS pinned host words for one tree (nullptr when none is free)
-constexpr int PIN_WORDS = 4;
+constexpr int PIN_WORDS = 8;   // [0..3] P2P work items, [4] CUDA-core M2L chunks
 int32_t* pinned_slot_acquire();
 void pinned_slot_release(int32_t* p);
 // defaults of the work-shape tunables (fmm_params): records per P2P work item

@@ -472,7 +472,15 @@ static int emit_classes(fmm_tree* t, int nclass, const uint64_t* ukeys, const in
 // A class with at most prm.tc_min_pairs pairs (default TC_MIN_PAIRS) is left
 // to the CUDA-core kernel.
 
-// flag[i] = pair i (of `order`, classes in class order first) belongs to a kept class
+// flag[i] = pair i (of `order`, classes in class order first) belongs to a kept
+// class: from its class id when the grouping gives one (cid, sorted like order),
+// else by bisection over the classes' first pairs
+__global__ void k_pair_keep_ids(int64_t np, int64_t ntc, int min_pairs, const int32_t* __restrict__ cid,
+                                const int32_t* __restrict__ counts, char* __restrict__ flag) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    flag[i] = i < ntc && counts[cid[i]] > min_pairs;
+}
 __global__ void k_pair_keep(int64_t np, int64_t ntc, int nclass, int min_pairs, const int32_t* __restrict__ cfirst,
                             const int32_t* __restrict__ counts, char* __restrict__ flag) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -498,7 +506,7 @@ __global__ void k_class_keep(int nclass, int min_pairs, const int32_t* __restric
 // classes' pairs followed by all others; ukeys and counts are compacted to the
 // kept classes; nclass and ntc are updated.
 static int drop_small_classes(fmm_tree* t, int64_t np, int32_t* order, int& nclass, uint64_t* ukeys, int32_t* counts,
-                              int64_t& ntc, cudaStream_t st) {
+                              int64_t& ntc, cudaStream_t st, const int32_t* cid = nullptr) {
     int rc;
     if (nclass == 0) return FMM_OK;
     int32_t *cfirst = nullptr, *order2 = nullptr, *counts2 = nullptr;
@@ -523,7 +531,10 @@ static int drop_small_classes(fmm_tree* t, int64_t np, int32_t* order, int& ncla
     tb = std::max(tb, tb2);
     if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
     FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, counts, cfirst, nclass, st));
-    k_pair_keep<<<nblk(np, 256), 256, 0, st>>>(np, ntc, nclass, t->prm.tc_min_pairs, cfirst, counts, flag);
+    if (cid)
+        k_pair_keep_ids<<<nblk(np, 256), 256, 0, st>>>(np, ntc, t->prm.tc_min_pairs, cid, counts, flag);
+    else
+        k_pair_keep<<<nblk(np, 256), 256, 0, st>>>(np, ntc, nclass, t->prm.tc_min_pairs, cfirst, counts, flag);
     k_class_keep<<<nblk(nclass, 256), 256, 0, st>>>(nclass, t->prm.tc_min_pairs, counts, keep);
     FMM_CUDA_TRY(cub::DevicePartition::Flagged(tmp, tb, order, flag, order2, nsel, np, st));
     FMM_CUDA_TRY(cub::DeviceSelect::Flagged(tmp, tb, ukeys, keep, ukeys2, nsel + 1, nclass, st));
@@ -554,8 +565,15 @@ __global__ void k_rem_fill(int ncell, const int64_t* __restrict__ start, const i
     for (int64_t e = start[c]; e < start[c + 1]; e += M2L_CHUNK) chunks[k++] = make_int2(c, (int)e);
 }
 
+__global__ void k_rem_count(int ncell, const int32_t* __restrict__ off, const int32_t* __restrict__ nch, int32_t* n) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *n = off[ncell - 1] + nch[ncell - 1];
+}
+
 // The pairs without a class, tc_tgt/tc_src[ntc, np), sorted by (target,
-// source), and their CSR by target for the CUDA-core kernel.
+// source), and their CSR by target for the CUDA-core kernel.  The number of
+// chunks comes back through the tree's pinned words when it can wait for the
+// build's last synchronisation (rem_nchunk = -1 until then); the task graph
+// needs it now.
 static int finish_remainder(fmm_tree* t, int64_t ntc, int64_t nrem, cudaStream_t st) {
     TreeDev& d = t->d;
     int rc;
@@ -591,12 +609,22 @@ static int finish_remainder(fmm_tree* t, int64_t ntc, int64_t nrem, cudaStream_t
         cub::DeviceScan::ExclusiveSum(nullptr, tb, nch, off, nc, st);
         if ((rc = dev_alloc(&tmp, tb, nullptr, st))) return rc;
         FMM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, tb, nch, off, nc, st));
-        int32_t h[2] = {0, 0};
-        FMM_CUDA_TRY(cudaMemcpyAsync(h, off + nc - 1, 4, cudaMemcpyDeviceToHost, st));
-        FMM_CUDA_TRY(cudaMemcpyAsync(h + 1, nch + nc - 1, 4, cudaMemcpyDeviceToHost, st));
-        FMM_CUDA_TRY(cudaStreamSynchronize(st));
-        t->rem_nchunk = (int64_t)h[0] + h[1];
-        if ((rc = dev_alloc(&d.rem_chunks, (size_t)std::max<int64_t>(1, t->rem_nchunk), t, st))) return rc;
+        if (t->h_pin && !tc_uses_dag(t)) {
+            // at most nrem / M2L_CHUNK full chunks plus one partial chunk per target
+            const int64_t bound = nrem / M2L_CHUNK + std::min<int64_t>(nc, nrem) + 1;
+            if ((rc = dev_alloc(&d.rem_chunks, (size_t)bound, t, st))) return rc;
+            if ((rc = dev_alloc(&d.rem_count, 1, t, st))) return rc;
+            k_rem_count<<<1, 32, 0, st>>>(nc, off, nch, d.rem_count);
+            FMM_CUDA_TRY(cudaMemcpyAsync(t->h_pin + 4, d.rem_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            t->rem_nchunk = -1;
+        } else {
+            int32_t h[2] = {0, 0};
+            FMM_CUDA_TRY(cudaMemcpyAsync(h, off + nc - 1, 4, cudaMemcpyDeviceToHost, st));
+            FMM_CUDA_TRY(cudaMemcpyAsync(h + 1, nch + nc - 1, 4, cudaMemcpyDeviceToHost, st));
+            FMM_CUDA_TRY(cudaStreamSynchronize(st));
+            t->rem_nchunk = (int64_t)h[0] + h[1];
+            if ((rc = dev_alloc(&d.rem_chunks, (size_t)std::max<int64_t>(1, t->rem_nchunk), t, st))) return rc;
+        }
         k_rem_fill<<<nblk(nc, 256), 256, 0, st>>>(nc, d.rem_start, off, d.rem_chunks);
         count_launch(t, 3);
         cudaFreeAsync(tmp, st);
@@ -676,7 +704,7 @@ static int classes_by_hash(fmm_tree* t, const int2* pairs, bool* done, cudaStrea
     cudaFreeAsync(tmp, st);
     k_class_bounds<<<nblk(nclass + 1, 256), 256, 0, st>>>(nclass, cid1, np, counts);
     count_launch(t, 3);
-    if ((rc = drop_small_classes(t, np, idx1, nclass, skeys, counts, ntc, st))) return rc;
+    if ((rc = drop_small_classes(t, np, idx1, nclass, skeys, counts, ntc, st, cid1))) return rc;
     const int64_t nrem = np - ntc;
     int64_t h_items = 0;
     if ((rc = emit_classes(t, nclass, skeys, counts, idx1, ntc, pairs, &h_items, st))) return rc;

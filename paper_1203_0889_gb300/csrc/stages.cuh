@@ -511,7 +511,7 @@ __device__ void p2p_range(int c, int64_t s0, int64_t s1, bool own, double* parti
             if (active) {
                 if constexpr (sizeof(T) == 4) {
                     const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(buf);
-#pragma unroll 4
+#pragma unroll 8
                     for (int j = sub; j < lim; j += G)
                         p2p_pair_x2<false>(X, Y, Z, b2[2 * j], b2[2 * j + 1], NP, GX, GY, GZ);
                 } else {

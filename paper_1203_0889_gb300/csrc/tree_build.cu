@@ -1515,7 +1515,7 @@ void free_tree_device(fmm_tree* t) {
     if (d.grad_tmp) cudaFreeAsync(d.grad_tmp, st);
     d.grad_tmp = nullptr;
     dev_free(d.m2l_tgt, st); dev_free(d.p2p_rec, st); dev_free(d.p2p_items, st); dev_free(d.p2p_nitems, st);
-    dev_free(d.p2p_split, st); dev_free(d.p2p_arrived, st); dev_free(d.p2p_part, st); dev_free(d.tc_items, st); dev_free(d.tc_block_first, st); dev_free(d.tc_item_list, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
+    dev_free(d.p2p_split, st); dev_free(d.p2p_arrived, st); dev_free(d.p2p_part, st); dev_free(d.rem_count, st); dev_free(d.tc_items, st); dev_free(d.tc_block_first, st); dev_free(d.tc_item_list, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
     dev_free(d.rem_start, st); dev_free(d.rem_chunks, st);
     dev_free(d.dag_cnt_init, st); dev_free(d.dag_cnt, st); dev_free(d.dag_q_init, st); dev_free(d.dag_q, st);
     dev_free(d.dag_lvl, st); dev_free(d.dag_ctr, st); dev_free(d.dag_zero_first, st);
