@@ -108,7 +108,7 @@ typedef struct {
        not the set of pair interactions): */
     int32_t p2p_item_records; /* stage-by-stage P2P: a leaf whose near-field list holds
                                  more source records than this is split into work
-                                 items of this many records; 0 = 64, else 8..65536 */
+                                 items of this many records; 0 = 256, else 8..65536 */
     int32_t tc_min_pairs;     /* FMM_PREC_MIXED_TC: translation classes of at most this
                                  many M2L pairs go to the CUDA-core M2L instead of the
                                  tensor cores; 0 = 64, else 1..4096 */

@@ -305,11 +305,14 @@ constexpr int PIN_WORDS = 8;   // [0..3] P2P work items, [4] CUDA-core M2L chunk
 int32_t* pinned_slot_acquire();
 void pinned_slot_release(int32_t* p);
 // defaults of the work-shape tunables (fmm_params): records per P2P work item
-// of a split leaf; the largest class left to the CUDA-core M2L (the
+// of a split leaf (256: on a Plummer core, leaves of 64..256 records gain
+// nothing from a split and lose the partial sums' combine; a clustered tree's
+// leaves beside dense clusters hold thousands); the largest class left to the
+// CUDA-core M2L (the
 // tensor-core kernel assembles one operator per class, which does not pay for
 // a handful of pairs: on a clustered 4M-particle tree 97 % of the classes hold
 // under 1 % of the pairs)
-constexpr int P2P_ITEM_RECORDS = 64;
+constexpr int P2P_ITEM_RECORDS = 256;
 constexpr int TC_MIN_PAIRS = 64;
 int evaluate_impl(fmm_tree* t, const void* q, void* phi, void* force, int dtype, cudaStream_t st);
 int alloc_eval_workspace(fmm_tree* t, cudaStream_t st);
