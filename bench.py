@@ -203,9 +203,10 @@ FP64_TFLOPS_MEASURED = 1.256
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # stands; None once the kernel has changed since.
-TRAFFIC = {"plummer": {"k_p2p": 89276160 + 15623680,       # one launch, dram__bytes_read + write
-                       "k_m2l_tc": 530205440 + 14841344},
-           "clustered": {"k_p2p": None, "k_m2l_tc": None}}
+# dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of the
+# kernel as it stands (one-pass ncu captures, profiles/traffic_full_size.md)
+TRAFFIC = {"plummer": {"k_p2p": 89927936 + 15948288, "k_m2l_tc": 159664384 + 7156736},
+           "clustered": {"k_p2p": 296292096 + 112957184, "k_m2l_tc": 14935927000 + 7914889000}}
 
 
 def traffic(kernel: str):
@@ -498,6 +499,11 @@ def run_ours(args):
         for r in roofs:
             if r["kernel"] in iso:
                 r["isolated"] = {k: iso[r["kernel"]][k] for k in ("ms", "achieved", "frac")}
+        # the dominant kernel is the one with the most work, i.e. the longest time
+        # alone (inside the step P2P is stretched by the far field beside it); its
+        # share agrees with the serialised ncu launch list
+        if roofs:
+            roof = max(roofs, key=lambda r: r.get("isolated", {}).get("ms", r["ms"]))
 
     # the other precisions on the same system, a few steps each (context for the
     # headline: the plain FP64 GPU path is the accuracy reference)
