@@ -622,7 +622,7 @@ def run_ours(args):
 
 def cpu_baseline(sample_n: int):
     """The FP64 oracle as it stands (tree build + full FMM) on the host cores, on a
-    smaller Plummer system of the same recipe; particles/s of that sample."""
+    smaller system of the bench workload's recipe; particles/s of that sample."""
     import oracle
     import workloads as W
     cores = os.cpu_count() or 1
