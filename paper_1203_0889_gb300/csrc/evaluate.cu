@@ -240,24 +240,84 @@ __global__ void __launch_bounds__(32 * NW) k_shift_block(int p, int lb, int le, 
                                        (int)(threadIdx.x >> 5), (int)threadIdx.x, BlockSync{});
 }
 
-// one warp per leaf
+// One warp per leaf, one particle per lane (32 at a time).  Each lane builds its
+// particle's regular harmonics column by column (order m outer, degree n inner,
+// the recurrence of p2m_leaf with the reciprocals from tables holding the values
+// the divisions give, so every term is the same); a column goes to shared
+// memory and the lane owning row r sums the column's entry n = m + r over the
+// lanes with four independent partial sums.  No shuffle reduction per
+// coefficient: the warp's dependent chains are 32 / 4 adds per column instead of
+// five shuffle levels per coefficient.  Shared memory per warp: a column of
+// p + 1 rows x 33 (padded) entries and the leaf's K accumulators.
+constexpr int P2M_WARPS = 4;
 template <typename T>
-__global__ void k_p2m(int p, int nleaf, const int32_t* __restrict__ leaves, const int32_t* __restrict__ first,
-                      const int32_t* __restrict__ count, const double4_32a* __restrict__ centre,
-                      const double4_32a* __restrict__ xq, cplx<T>* __restrict__ M) {
+__host__ __device__ inline size_t p2m_warp_smem(int p) {
+    return ((size_t)(p + 1) * 33 + ntri(p)) * sizeof(cplx<T>);
+}
+template <typename T>
+__global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, int nleaf, const int32_t* __restrict__ leaves,
+                                                        const int32_t* __restrict__ first,
+                                                        const int32_t* __restrict__ count,
+                                                        const double4_32a* __restrict__ centre,
+                                                        const double4_32a* __restrict__ xq, cplx<T>* __restrict__ M) {
     extern __shared__ unsigned char smem_raw[];
-    // the recurrence's reciprocals from tables holding the values the
-    // divisions give (the same products as the division form)
     __shared__ T rm[FMM_MAX_P + 1], rt[(FMM_MAX_P + 1) * (FMM_MAX_P + 2) / 2];
     for (int m = threadIdx.x; m <= p; m += blockDim.x) rm[m] = m > 0 ? T(1) / T(2 * m) : T(0);
     for (int n = 0; n <= p; n++)
         for (int m = threadIdx.x; m <= n; m += blockDim.x) rt[tri(n, m)] = n >= m + 2 ? T(1) / T((n + m) * (n - m)) : T(0);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cplx<T>* acc = reinterpret_cast<cplx<T>*>(smem_raw) + warp * ntri(p);
     const int li = blockIdx.x * (blockDim.x >> 5) + warp;
     if (li >= nleaf) return;
-    p2m_leaf<T>(p, leaves[li], lane, first, count, centre, xq, M, acc, rm, rt);
+    const int K = ntri(p), KS = kstride(p);
+    cplx<T>* col = reinterpret_cast<cplx<T>*>(smem_raw + (size_t)warp * p2m_warp_smem<T>(p));
+    cplx<T>* acc = col + (size_t)(p + 1) * 33;
+    for (int j = lane; j < K; j += 32) acc[j] = cmk<T>(0, 0);
+    const int c = leaves[li];
+    const double4_32a cc = centre[c];
+    const double invh = 1.0 / cc.w;
+    const int f = first[c], cnt = count[c];
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        T ux = 0, uy = 0, uz = 0, q = 0;
+        if (i < cnt) {
+            const double4_32a a = xq[f + i];
+            ux = (T)((a.x - cc.x) * invh); uy = (T)((a.y - cc.y) * invh); uz = (T)((a.z - cc.z) * invh);
+            q = (T)a.w;
+        }
+        const T r2 = ux * ux + uy * uy + uz * uz;
+        cplx<T> rmm = cmk<T>(q, 0);
+        for (int m = 0; m <= p; m++) {
+            if (m > 0) rmm = cscale(cmul(rmm, cmk<T>(ux, uy)), rm[m]);
+            cplx<T> a = rmm, b = cscale(rmm, uz);
+            for (int n = m; n <= p; n++) {
+                cplx<T> v;
+                if (n == m) v = a;
+                else if (n == m + 1) v = b;
+                else {
+                    const T inv = rt[tri(n, m)];
+                    v = cmk<T>((T(2 * n - 1) * uz * b.re - r2 * a.re) * inv, (T(2 * n - 1) * uz * b.im - r2 * a.im) * inv);
+                    a = b; b = v;
+                }
+                col[(n - m) * 33 + lane] = v;
+            }
+            __syncwarp();
+            if (lane <= p - m) {
+                const cplx<T>* row = col + lane * 33;
+                cplx<T> s0 = row[0], s1 = row[1], s2 = row[2], s3 = row[3];
+#pragma unroll
+                for (int l = 4; l < 32; l += 4) {
+                    s0 = cadd(s0, row[l]); s1 = cadd(s1, row[l + 1]);
+                    s2 = cadd(s2, row[l + 2]); s3 = cadd(s3, row[l + 3]);
+                }
+                cplx<T>& o = acc[tri(m + lane, m)];
+                o = cadd(o, cadd(cadd(s0, s1), cadd(s2, s3)));
+            }
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    for (int j = lane; j < K; j += 32) M[(int64_t)c * KS + j] = acc[j];
 }
 
 // M2L (any pair of cells): one warp per target, each half-warp one source
@@ -660,10 +720,14 @@ static int far_field(fmm_tree* t, cplx<T>* M, cplx<T>* L, const double4_32a* xq6
     const TreeDev& d = t->d;
     const int p = t->prm.p, K = ntri(p);
     // upward pass
-    const int W = 4;
     stage_begin(t, FMM_STAGE_P2M, st);
-    k_p2m<T><<<nblk(t->nleaf, W), 32 * W, W * K * sizeof(cplx<T>), st>>>(p, t->nleaf, d.leaves, d.first, d.count,
+    {
+        const size_t smem = P2M_WARPS * p2m_warp_smem<T>(p);   // 59 KB at most (p = 20, FP64)
+        if (smem > 48 * 1024)
+            FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_p2m<T><<<nblk(t->nleaf, P2M_WARPS), 32 * P2M_WARPS, smem, st>>>(p, t->nleaf, d.leaves, d.first, d.count,
                                                                           d.centre, xq64, M);
+    }
     count_launch(t);
     stage_end(t, FMM_STAGE_P2M, st);
     stage_begin(t, FMM_STAGE_M2M, st);
