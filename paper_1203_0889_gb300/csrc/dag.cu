@@ -34,7 +34,7 @@ __global__ void k_dag_seed(int64_t n_hi, int ngroups, int32_t* q) {
 __global__ void k_dag_reset(DagCounters* c, unsigned n0) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         c->head_hi = 0u; c->tail_hi = n0; c->head_lo = 0u; c->done = 0u; c->avail = (int)n0;
-        c->cells_final = 0u; c->m2l_done = 0u; c->pad = 0u;
+        c->cells_final = 0u; c->m2l_done = 0u; c->released = 0u;
     }
 }
 

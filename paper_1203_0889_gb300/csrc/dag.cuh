@@ -51,7 +51,7 @@ struct DagCounters {
     int avail;                // tasks pushed (slot written) and not yet claimed
     unsigned cells_final;     // cells whose multipole and split row are final
     unsigned m2l_done;        // tensor-core item completions (per epilogue warp) + REM chunks
-    unsigned pad;
+    unsigned released;        // 1 once the last final cell has queued the REM tasks
 };
 
 struct DagArgs {
@@ -133,12 +133,16 @@ __device__ __forceinline__ void dag_push_n_warp(const DagArgs& a, int kind, int 
 }
 
 // One thread: the next task, or -1 when the graph is finished or failed (-2:
-// until_upward is set and every multipole is final).  A claim that finds
-// nothing available is undone and a P2P task is taken instead.
+// until_upward is set, every multipole is final and no high-priority task is
+// queued or being queued -- the CUDA-core M2L tasks the last final cell
+// releases are taken first).  A claim that finds nothing available is undone
+// and a P2P task is taken instead.
 static __device__ int dag_pop(const DagArgs& a, bool until_upward) {
     const long long t0 = clock64();
     for (;;) {
-        if (until_upward && dag_vload(&a.ctr->cells_final) >= (unsigned)a.ncell) return -2;
+        if (until_upward && dag_vload(&a.ctr->released) != 0u && dag_vload(&a.ctr->avail) <= 0 &&
+            dag_vload(&a.ctr->head_hi) >= dag_vload(&a.ctr->tail_hi))
+            return -2;
         if (dag_vload(&a.ctr->avail) > 0) {
             if (atomicSub(&a.ctr->avail, 1) > 0) {
                 const unsigned h = atomicAdd(&a.ctr->head_hi, 1u);
@@ -200,7 +204,11 @@ static __device__ void dag_m_final(const DagArgs& a, int c, int lane) {
     }
     if (__shfl_sync(0xffffffffu, last, 0)) {
         dag_push_n_warp(a, DK_REM, 0, a.nrem_tasks, lane);
-        if (lane == 0 && a.m2l_total == 0) dag_open_gate(a);
+        if (lane == 0) {
+            if (a.m2l_total == 0) dag_open_gate(a);
+            __threadfence();
+            atomicExch(&a.ctr->released, 1u);
+        }
     }
 }
 
@@ -243,7 +251,8 @@ __host__ __device__ inline size_t dag_group_scratch(int p) {
 
 // One worker group (threads gtid = 0..127 of group `group`): takes tasks until
 // the graph is finished or has failed, or, with until_upward, until every
-// multipole is final.  slot: the group's shared word.
+// multipole is final and the high-priority queue is empty.  slot: the group's
+// shared word.
 template <typename O, int R>
 __device__ void dag_worker(const DagArgs& a, int group, int gtid, unsigned char* scratch, int* slot,
                            bool until_upward = false) {

@@ -1043,9 +1043,10 @@ __global__ void __maxnreg__(TC_MAX_REGS) k_m2l_tc(const __grid_constant__ CUtens
     const bool stage_scratch = (size_t)a.stages * TC_STAGE_BYTES >= (size_t)4 * a.wscratch;
 
     if (DAG && warp <= TC_MMA_WARP) {
-        // until every multipole is final (every item then ready at once), the
-        // epilogue and gatherer warps run as four more worker groups, with the
-        // stages as their scratch; then every tensor-core role starts together
+        // until every multipole is final (every item then ready at once) and the
+        // CUDA-core M2L tasks it releases are taken, the epilogue and gatherer
+        // warps run as four more worker groups, with the stages as their
+        // scratch; then every tensor-core role starts together
         if (warp < TC_PROD_WARP && stage_scratch) {
             const int grp = DAG_GROUPS + warp / 4;
             dag_worker<O, R>(g, grp, tid & (DAG_GROUP_THREADS - 1), sm + (size_t)(grp - DAG_GROUPS) * a.wscratch,
