@@ -71,7 +71,8 @@ int build_dag(fmm_tree* t, cudaStream_t st) {
 }
 
 template <typename O>
-int evaluate_dag(fmm_tree* t, const double4_32a* xq64, const float4* xq32, O* phi, O* force, cudaStream_t st) {
+int evaluate_dag(fmm_tree* t, const double4_32a* xq64, const float4* xq32, const float4* xlo32, O* phi, O* force,
+                 cudaStream_t st) {
     TreeDev& d = t->d;
     const int nc = t->ncell, p = t->prm.p;
     if (nc == 0) return FMM_OK;
@@ -93,7 +94,7 @@ int evaluate_dag(fmm_tree* t, const double4_32a* xq64, const float4* xq32, O* ph
     g.leaves = d.leaves; g.first = d.first; g.count = d.count; g.parent = d.parent;
     g.child_first = d.child_first; g.child_count = d.child_count; g.level = d.level; g.ckey = d.ckey;
     g.centre = d.centre; g.icentre = d.icentre; g.perm = d.perm; g.shift_ops = (const float*)d.shift_ops;
-    g.xq64 = xq64; g.xq32 = xq32; g.p2p_start = d.p2p_start; g.p2p_rec = d.p2p_rec; g.cu2f = d.cu2f;
+    g.xq64 = xq64; g.xq32 = xq32; g.xlo32 = xlo32; g.p2p_start = d.p2p_start; g.p2p_rec = d.p2p_rec; g.cu2f = d.cu2f;
     g.rem_chunks = d.rem_chunks; g.rem_start = d.rem_start; g.rem_src = d.tc_src + t->tc_npairs;
     g.M = (float*)d.M; g.L = (float*)d.L; g.Lr = (const float*)d.tc_lr; g.Ms = (__nv_bfloat16*)d.tc_msplit;
     g.near = d.near; g.phi_out = phi; g.force_out = force;
@@ -106,7 +107,9 @@ int evaluate_dag(fmm_tree* t, const double4_32a* xq64, const float4* xq32, O* ph
     return rc;
 }
 
-template int evaluate_dag<float>(fmm_tree*, const double4_32a*, const float4*, float*, float*, cudaStream_t);
-template int evaluate_dag<double>(fmm_tree*, const double4_32a*, const float4*, double*, double*, cudaStream_t);
+template int evaluate_dag<float>(fmm_tree*, const double4_32a*, const float4*, const float4*, float*, float*,
+                                  cudaStream_t);
+template int evaluate_dag<double>(fmm_tree*, const double4_32a*, const float4*, const float4*, double*, double*,
+                                   cudaStream_t);
 
 }  // namespace fmm

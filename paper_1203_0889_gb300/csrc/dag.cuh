@@ -74,6 +74,7 @@ struct DagArgs {
     const float* shift_ops;
     const double4_32a* xq64;
     const float4* xq32;
+    const float4* xlo32;       // residuals of the FP32 coordinates
     const int64_t* p2p_start;
     const int4* p2p_rec;
     const float* cu2f;
@@ -343,7 +344,7 @@ __device__ void dag_worker(const DagArgs& a, int group, int gtid, unsigned char*
         } else {   // DK_P2P: leaf rank idx
             float4* buf = reinterpret_cast<float4*>(scratch);
             float(*part)[4] = reinterpret_cast<float(*)[4]>(scratch + P2P_BUF * sizeof(float4));
-            p2p_leaf<float, GroupSync>(a.leaves[idx], a.first, a.count, a.p2p_start, a.p2p_rec, a.xq32, a.icentre,
+            p2p_leaf<float, GroupSync>(a.leaves[idx], a.first, a.count, a.p2p_start, a.p2p_rec, a.xq32, a.xlo32, a.icentre,
                                        a.cu2f, a.near, buf, part, gtid, GroupSync{bar});
         }
         // publish the task's writes, then the releases that need the whole group

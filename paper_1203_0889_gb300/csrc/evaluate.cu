@@ -37,17 +37,21 @@ __global__ void k_prepare64(const double* __restrict__ spos, const int32_t* __re
 }
 
 // FP32 copy relative to the centre of the particle's own leaf, so that the
-// rounding of a coordinate scales with the leaf size, not with the position.
+// rounding of a coordinate scales with the leaf size, not with the position;
+// xlo: what that rounding dropped (FP32 again), for very close pairs within a leaf.
 template <typename Q>
 __global__ void k_prepare32(const double* __restrict__ spos, const int32_t* __restrict__ perm,
                             const Q* __restrict__ q, int64_t n, const int32_t* __restrict__ pleaf,
-                            const double4_32a* __restrict__ centre, double4_32a* xq64, float4* xq32) {
+                            const double4_32a* __restrict__ centre, double4_32a* xq64, float4* xq32, float4* xlo) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double x = spos[3 * i], y = spos[3 * i + 1], z = spos[3 * i + 2], qq = (double)q[perm[i]];
     xq64[i] = make_double4_32a(x, y, z, qq);
     double4_32a c = centre[pleaf[i]];
-    xq32[i] = make_float4((float)(x - c.x), (float)(y - c.y), (float)(z - c.z), (float)qq);
+    const double dx = x - c.x, dy = y - c.y, dz = z - c.z;
+    const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
+    xq32[i] = make_float4(hx, hy, hz, (float)qq);
+    xlo[i] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz), 0.f);
 }
 
 // Dense real forms of the child <-> parent shifts, one per octant (the shift
@@ -414,6 +418,7 @@ __global__ void __launch_bounds__(P2P_THREADS, sizeof(T) == 4 ? 9 : 1) k_p2p(con
                                                      const int64_t* __restrict__ start,
                                                      const int4* __restrict__ rec,
                                                      const typename Vec4<T>::type* __restrict__ xq,
+                                                     const float4* __restrict__ xlo,
                                                      const int4* __restrict__ icentre, const float* __restrict__ cu2f,
                                                      double* __restrict__ near) {
     __shared__ typename Vec4<T>::type buf[P2P_BUF];
@@ -423,16 +428,16 @@ __global__ void __launch_bounds__(P2P_THREADS, sizeof(T) == 4 ? 9 : 1) k_p2p(con
     const int4 it = items[blockIdx.x];
     const int64_t s0 = start[it.x] + it.y;
     if (!(it.w & 1)) {
-        p2p_range<T>(it.x, s0, s0 + it.z, (it.w & 2) != 0, nullptr, first, count, rec, xq, icentre, cu2f, near, buf,
-                     part, threadIdx.x);
+        p2p_range<T>(it.x, s0, s0 + it.z, sizeof(T) == 8 && (it.w & 2) != 0, nullptr, first, count, rec, xq, xlo,
+                     icentre, cu2f, near, buf, part, threadIdx.x);
         return;
     }
     // split leaf: si = (items k, this item's rank j, partial slot base lo / hi)
     const int4 si = split[blockIdx.x];
     const int nt = count[it.x];
     const int64_t pbase = (int64_t)(uint32_t)si.z | ((int64_t)si.w << 32);   // slot of (j = 0, target 0)
-    p2p_range<T>(it.x, s0, s0 + it.z, (it.w & 2) != 0, partial + 4 * (pbase + (int64_t)si.y * nt), first, count,
-                 rec, xq, icentre, cu2f, near, buf, part, threadIdx.x);
+    p2p_range<T>(it.x, s0, s0 + it.z, sizeof(T) == 8 && (it.w & 2) != 0, partial + 4 * (pbase + (int64_t)si.y * nt),
+                 first, count, rec, xq, xlo, icentre, cu2f, near, buf, part, threadIdx.x);
     __threadfence();
     __syncthreads();
     int32_t* ctr = arrived + (blockIdx.x - si.y);   // the leaf's first item
@@ -451,6 +456,53 @@ __global__ void __launch_bounds__(P2P_THREADS, sizeof(T) == 4 ? 9 : 1) k_p2p(con
         o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3;
     }
     if (threadIdx.x == 0) *ctr = 0;   // ready for the next evaluation
+}
+
+// FP32 P2P: the pairs within each leaf, after k_p2p (which stages a leaf's own
+// particles at zero charge), added into near.  One warp per leaf, a lane per
+// target.  Separations come from the leaf-relative FP32 coordinates plus the
+// difference of their residuals, so two particles much closer than the leaf's
+// side keep their separation to FP32 precision; coincident pairs (separation
+// at or below FLT_MIN) contribute nothing.
+constexpr int P2P_OWN_WARPS = 4;
+__global__ void __launch_bounds__(32 * P2P_OWN_WARPS) k_p2p_own(int nleaf, const int32_t* __restrict__ leaves,
+                                                                const int32_t* __restrict__ first,
+                                                                const int32_t* __restrict__ count,
+                                                                const float4* __restrict__ xq,
+                                                                const float4* __restrict__ xlo, double* __restrict__ near) {
+    __shared__ float4 sh[P2P_OWN_WARPS][32], sl[P2P_OWN_WARPS][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int li = blockIdx.x * P2P_OWN_WARPS + warp;
+    if (li >= nleaf) return;
+    const int c = leaves[li], tf = first[c], nt = count[c];
+    for (int base = 0; base < nt; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < nt;
+        const float4 a = valid ? xq[tf + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 al = valid ? xlo[tf + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        for (int jb = 0; jb < nt; jb += 32) {
+            __syncwarp();
+            if (jb + lane < nt) { sh[warp][lane] = xq[tf + jb + lane]; sl[warp][lane] = xlo[tf + jb + lane]; }
+            __syncwarp();
+            const int nj = min(32, nt - jb);
+            for (int j = 0; j < nj; j++) {
+                const float4 s = sh[warp][j], l = sl[warp][j];
+                const float dx = (a.x - s.x) + (al.x - l.x), dy = (a.y - s.y) + (al.y - l.y),
+                            dz = (a.z - s.z) + (al.z - l.z);
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                const float rinv = r2 > pair_floor(r2) ? rsqrt_t(r2) : 0.f;
+                const float qr = s.w * rinv;
+                ph += qr;
+                const float qr3 = qr * rinv * rinv;
+                gx = fmaf(-qr3, dx, gx); gy = fmaf(-qr3, dy, gy); gz = fmaf(-qr3, dz, gz);
+            }
+        }
+        if (valid) {
+            double* o = near + 4 * ((int64_t)tf + i);
+            o[0] += (double)ph; o[1] += (double)gx; o[2] += (double)gy; o[3] += (double)gz;
+        }
+    }
 }
 
 // L2P + near field + output in input order, one thread per sorted particle
@@ -501,7 +553,7 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st) {
     if ((rc = dev_alloc(&M, (size_t)t->ncell * K * csz, t, st))) return rc;
     if ((rc = dev_alloc(&L, (size_t)t->ncell * K * csz, t, st))) return rc;
     // double4_32a copy always (P2M/L2P positions), plus float4 for FP32 P2P
-    size_t xb = (size_t)t->n * sizeof(double4_32a) + (p2p_fp64(t) ? 0 : (size_t)t->n * sizeof(float4));
+    size_t xb = (size_t)t->n * sizeof(double4_32a) + (p2p_fp64(t) ? 0 : (size_t)2 * t->n * sizeof(float4));
     if ((rc = dev_alloc(&xq, xb, t, st))) return rc;
     if ((rc = dev_alloc(&d.near, (size_t)t->n * 4, t, st))) return rc;
     d.M = M; d.L = L; d.xq = xq;
@@ -643,6 +695,7 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     const int64_t n = t->n;
     double4_32a* xq64 = (double4_32a*)d.xq;
     float4* xq32 = (float4*)((char*)d.xq + (size_t)n * sizeof(double4_32a));
+    float4* xlo32 = xq32 + n;   // residuals of the FP32 coordinates (FP32 P2P only)
     cplx<T>* M = (cplx<T>*)d.M;
     cplx<T>* L = (cplx<T>*)d.L;
     // particles in sorted order
@@ -650,18 +703,18 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     if (p2p_fp64(t))
         k_prepare64<Q><<<nblk(n, 256), 256, 0, st>>>(d.spos, d.perm, q, n, xq64);
     else
-        k_prepare32<Q><<<nblk(n, 256), 256, 0, st>>>(d.spos, d.perm, q, n, d.pleaf, d.centre, xq64, xq32);
+        k_prepare32<Q><<<nblk(n, 256), 256, 0, st>>>(d.spos, d.perm, q, n, d.pleaf, d.centre, xq64, xq32, xlo32);
     count_launch(t);
     stage_end(t, FMM_STAGE_PREPARE, st);
     if constexpr (sizeof(T) == 4) {
-        if (tc_uses_dag(t)) return evaluate_dag<O>(t, xq64, xq32, phi, force, st);
+        if (tc_uses_dag(t)) return evaluate_dag<O>(t, xq64, xq32, xlo32, phi, force, st);
     }
     if (queue_supported(t)) {
         // one persistent launch runs the whole task graph
         if constexpr (std::is_same<T, double>::value) {
             if (p2p_fp64(t)) return evaluate_queue<T, double, O>(t, xq64, xq64, phi, force, st);
         }
-        return evaluate_queue<T, float, O>(t, xq64, xq32, phi, force, st);
+        return evaluate_queue<T, float, O>(t, xq64, xq32, phi, force, st, xlo32);
     }
     // P2P (near field) depends on nothing but the particles: it runs on the
     // tree's second stream, concurrently with the upward pass, M2L and L2L,
@@ -681,12 +734,17 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     else if (p2p_fp64(t))
         k_p2p<double><<<nitems, P2P_THREADS, 0, sp>>>(d.p2p_items, d.p2p_nitems, d.p2p_split, d.p2p_arrived,
                                                         d.p2p_part, d.first, d.count, d.p2p_start,
-                                                        d.p2p_rec, xq64, d.icentre, d.cu2f, d.near);
+                                                        d.p2p_rec, xq64, nullptr, d.icentre, d.cu2f, d.near);
     else
         k_p2p<float><<<nitems, P2P_THREADS, 0, sp>>>(d.p2p_items, d.p2p_nitems, d.p2p_split, d.p2p_arrived,
                                                        d.p2p_part, d.first, d.count, d.p2p_start,
-                                                       d.p2p_rec, xq32, d.icentre, d.cu2f, d.near);
+                                                       d.p2p_rec, xq32, xlo32, d.icentre, d.cu2f, d.near);
     count_launch(t);
+    if (nitems > 0 && !p2p_fp64(t)) {
+        k_p2p_own<<<nblk(t->nleaf, P2P_OWN_WARPS), 32 * P2P_OWN_WARPS, 0, sp>>>(t->nleaf, d.leaves, d.first, d.count,
+                                                                                xq32, xlo32, d.near);
+        count_launch(t);
+    }
     stage_end(t, FMM_STAGE_P2P, sp);
     if (sp != st) FMM_CUDA_TRY(cudaEventRecord(t->ev_join, sp));
     // the far-field chain on the high-priority stream (joined before L2P)

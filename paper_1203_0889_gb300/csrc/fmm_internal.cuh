@@ -326,7 +326,8 @@ int tc_kin(int p);
 bool queue_supported(const fmm_tree* t);
 int build_queue(fmm_tree* t, cudaStream_t st);
 template <typename T, typename TP, typename O>
-int evaluate_queue(fmm_tree* t, const double4_32a* xq64, const void* xqp, O* phi, O* force, cudaStream_t st);
+int evaluate_queue(fmm_tree* t, const double4_32a* xq64, const void* xqp, O* phi, O* force, cudaStream_t st,
+                   const float4* xlo = nullptr);
 bool tc_supported(int p);
 // the mixed form runs as one task-graph launch unless a stage-by-stage flag is set
 inline bool tc_uses_dag(const fmm_tree* t) {
@@ -339,7 +340,8 @@ struct DagArgs;
 template <typename O>
 int launch_m2l_dag(fmm_tree* t, const DagArgs& g, cudaStream_t st);
 template <typename O>
-int evaluate_dag(fmm_tree* t, const double4_32a* xq64, const float4* xq32, O* phi, O* force, cudaStream_t st);
+int evaluate_dag(fmm_tree* t, const double4_32a* xq64, const float4* xq32, const float4* xlo32, O* phi, O* force,
+                 cudaStream_t st);
 void free_tree_device(fmm_tree* t);
 template <typename T>
 int dev_alloc(T** p, size_t count, fmm_tree* t, cudaStream_t st);

@@ -72,6 +72,7 @@ struct QueueArgs {
     const void* shift_ops;
     const double4_32a* xq64;
     const void* xqp;        // P2P records (double4 or float4)
+    const float4* xlo;      // FP32 P2P: residuals of the coordinates (null for FP64)
     void* M;
     void* L;
     double* near;
@@ -213,8 +214,8 @@ __global__ void __launch_bounds__(QUEUE_THREADS) k_queue(QueueArgs a) {
         } else {  // TK_P2P
             VP* buf = reinterpret_cast<VP*>(sm);
             TP(*part)[4] = reinterpret_cast<TP(*)[4]>(sm + P2P_BUF * sizeof(VP));
-            p2p_leaf<TP>(a.leaves[idx], a.first, a.count, a.p2p_start, a.p2p_rec, (const VP*)a.xqp, a.icentre, a.cu2f,
-                         a.near, buf, part, tid);
+            p2p_leaf<TP>(a.leaves[idx], a.first, a.count, a.p2p_start, a.p2p_rec, (const VP*)a.xqp,
+                         sizeof(TP) == 4 ? a.xlo : nullptr, a.icentre, a.cu2f, a.near, buf, part, tid);
         }
         // publish this task's writes, then release its successors
         __threadfence();
@@ -377,7 +378,8 @@ static int launch_queue(fmm_tree* t, QueueArgs& a, size_t smem, cudaStream_t st)
 }
 
 template <typename T, typename TP, typename O>
-int evaluate_queue(fmm_tree* t, const double4_32a* xq64, const void* xqp, O* phi, O* force, cudaStream_t st) {
+int evaluate_queue(fmm_tree* t, const double4_32a* xq64, const void* xqp, O* phi, O* force, cudaStream_t st,
+                   const float4* xlo) {
     TreeDev& d = t->d;
     const int p = t->prm.p, K = ntri(p), KI = ntri(2 * p);
     const int nc = t->ncell;
@@ -394,7 +396,7 @@ int evaluate_queue(fmm_tree* t, const double4_32a* xq64, const void* xqp, O* phi
     a.child_first = d.child_first; a.child_count = d.child_count; a.ckey = d.ckey; a.centre = d.centre;
     a.icentre = d.icentre; a.perm = d.perm; a.m2l_start = d.m2l_start; a.m2l_src = d.m2l_src;
     a.p2p_start = d.p2p_start; a.p2p_rec = d.p2p_rec; a.tr_start = d.tr_start; a.tr_tgt = d.tr_tgt;
-    a.shift_ops = d.shift_ops; a.xq64 = xq64; a.xqp = xqp; a.M = d.M; a.L = d.L; a.near = d.near;
+    a.shift_ops = d.shift_ops; a.xq64 = xq64; a.xqp = xqp; a.xlo = xlo; a.M = d.M; a.L = d.L; a.near = d.near;
     a.phi_out = phi; a.force_out = force; a.q = d.q_work;
     a.mcnt = d.q_cnt; a.lcnt = d.q_cnt + nc; a.dcnt = d.q_cnt + 2 * nc; a.pcnt = d.q_cnt + 3 * nc;
     a.ctr = (QueueCounters*)d.q_ctr; a.status = d.status;
@@ -413,16 +415,16 @@ int evaluate_queue(fmm_tree* t, const double4_32a* xq64, const void* xqp, O* phi
 }
 
 template int evaluate_queue<double, double, double>(fmm_tree*, const double4_32a*, const void*, double*, double*,
-                                                    cudaStream_t);
+                                                    cudaStream_t, const float4*);
 template int evaluate_queue<double, double, float>(fmm_tree*, const double4_32a*, const void*, float*, float*,
-                                                   cudaStream_t);
+                                                   cudaStream_t, const float4*);
 template int evaluate_queue<double, float, double>(fmm_tree*, const double4_32a*, const void*, double*, double*,
-                                                   cudaStream_t);
+                                                   cudaStream_t, const float4*);
 template int evaluate_queue<double, float, float>(fmm_tree*, const double4_32a*, const void*, float*, float*,
-                                                  cudaStream_t);
+                                                  cudaStream_t, const float4*);
 template int evaluate_queue<float, float, double>(fmm_tree*, const double4_32a*, const void*, double*, double*,
-                                                  cudaStream_t);
+                                                  cudaStream_t, const float4*);
 template int evaluate_queue<float, float, float>(fmm_tree*, const double4_32a*, const void*, float*, float*,
-                                                 cudaStream_t);
+                                                 cudaStream_t, const float4*);
 
 }  // namespace fmm

@@ -420,6 +420,36 @@ __device__ __forceinline__ void p2p_pair_x2(f2::u64 X, f2::u64 Y, f2::u64 Z, con
     GZ = f2::fma(nqr3, dz, GZ);
 }
 
+// A source of the target leaf itself (guarded like p2p_pair_x2<true>).  Two
+// particles of one leaf much closer than its side lose their separation to the
+// rounding of their leaf-relative FP32 coordinates (about 2^-24 of the side):
+// a pair closer than sqrt(close2) gets the difference of the coordinates'
+// residuals added, fix(dx, dy, dz) doing so, which is rare enough to stay out
+// of the common path.
+template <typename Fix>
+__device__ __forceinline__ void p2p_pair_x2_own(f2::u64 X, f2::u64 Y, f2::u64 Z, const ulonglong2 s01,
+                                                const ulonglong2 s23, float close2, Fix fix, f2::u64& NP,
+                                                f2::u64& GX, f2::u64& GY, f2::u64& GZ) {
+    f2::u64 dx = f2::add(X, s01.x), dy = f2::add(Y, s01.y), dz = f2::add(Z, s23.x);
+    f2::u64 r2 = f2::fma(dz, dz, f2::fma(dy, dy, f2::mul(dx, dx)));
+    float ra, rb;
+    f2::unpack(r2, ra, rb);
+    if (ra < close2 || rb < close2) {
+        fix(dx, dy, dz);
+        r2 = f2::fma(dz, dz, f2::fma(dy, dy, f2::mul(dx, dx)));
+        f2::unpack(r2, ra, rb);
+    }
+    ra = ra > pair_floor(ra) ? rsqrt_t(ra) : 0.f;
+    rb = rb > pair_floor(rb) ? rsqrt_t(rb) : 0.f;
+    const f2::u64 rinv = f2::pack(ra, rb);
+    const f2::u64 nqr = f2::mul(s23.y, rinv);
+    NP = f2::add(NP, nqr);
+    const f2::u64 nqr3 = f2::mul(f2::mul(nqr, rinv), rinv);
+    GX = f2::fma(nqr3, dx, GX);
+    GY = f2::fma(nqr3, dy, GY);
+    GZ = f2::fma(nqr3, dz, GZ);
+}
+
 // Targets held by one thread: each staged source feeds this many pair
 // interactions (four was measured slower than two in FP32: fewer source
 // streams per target and more registers).
@@ -438,13 +468,15 @@ struct P2PBlocking { static constexpr int TPT = 2; };
 
 // p2p_range: records s0 .. s1 - 1 of the leaf's list only (a contiguous run of
 // its source stream); own: add the leaf's own particles (FP32: they are staged
-// at zero charge and added by a guarded loop); partial: when not null, the
+// at zero charge and added by a guarded loop, very close pairs with the
+// coordinates' residuals xlo, which every FP32 caller passes); partial: when not null, the
 // sums go to partial[4 t + 0..3] (t = target within the leaf) instead of near
 // (the leaf's list is split over several blocks, combined afterwards).
 template <typename T, typename Sync = BlockSync>
 __device__ void p2p_range(int c, int64_t s0, int64_t s1, bool own, double* partial, const int32_t* __restrict__ first,
                           const int32_t* __restrict__ count, const int4* __restrict__ rec,
-                          const typename Vec4<T>::type* __restrict__ xq, const int4* __restrict__ icentre,
+                          const typename Vec4<T>::type* __restrict__ xq, const float4* __restrict__ xlo,
+                          const int4* __restrict__ icentre,
                           const float* __restrict__ cu2f, double* __restrict__ near, typename Vec4<T>::type* buf,
                           T (*part)[4], int tix, Sync sync = Sync()) {
     typedef typename Vec4<T>::type V;
@@ -540,11 +572,19 @@ __device__ void p2p_range(int c, int64_t s0, int64_t s1, bool own, double* parti
         if constexpr (sizeof(T) == 4) {
             // the target leaf's own particles (same leaf frame, no shift), guarded
             if (active && own) {
+                // pairs closer than 1 % of the leaf's side: separation from the residuals too
+                const float side = ldexpf(u2f, 22 - ict.w), close2 = 1e-4f * side * side;
+                const int t0 = tf + tb + TPT * u, t1 = tf + tb + (TPT * u + 1 < ntc ? TPT * u + 1 : TPT * u);
                 for (int j = sub; j < nt; j += G) {
                     const V s = xq[tf + j];
                     const ulonglong2 s01 = make_ulonglong2(f2::pack(-s.x, -s.x), f2::pack(-s.y, -s.y));
                     const ulonglong2 s23 = make_ulonglong2(f2::pack(-s.z, -s.z), f2::pack(-s.w, -s.w));
-                    p2p_pair_x2<true>(X, Y, Z, s01, s23, NP, GX, GY, GZ);
+                    p2p_pair_x2_own(X, Y, Z, s01, s23, close2, [&](f2::u64& dx, f2::u64& dy, f2::u64& dz) {
+                        const float4 a = xlo[t0], b = xlo[t1], l = xlo[tf + j];
+                        dx = f2::add(dx, f2::pack(a.x - l.x, b.x - l.x));
+                        dy = f2::add(dy, f2::pack(a.y - l.y, b.y - l.y));
+                        dz = f2::add(dz, f2::pack(a.z - l.z, b.z - l.z));
+                    }, NP, GX, GY, GZ);
                 }
             }
             float a, b;
@@ -579,16 +619,16 @@ __device__ void p2p_range(int c, int64_t s0, int64_t s1, bool own, double* parti
     }
 }
 
-// the whole list of target leaf c
+// the whole list of target leaf c (xlo: residuals of the FP32 coordinates, null for FP64)
 template <typename T, typename Sync = BlockSync>
 __device__ __forceinline__ void p2p_leaf(int c, const int32_t* __restrict__ first, const int32_t* __restrict__ count,
                                          const int64_t* __restrict__ start, const int4* __restrict__ rec,
                                          const typename Vec4<T>::type* __restrict__ xq,
-                                         const int4* __restrict__ icentre, const float* __restrict__ cu2f,
-                                         double* __restrict__ near, typename Vec4<T>::type* buf, T (*part)[4], int tix,
-                                         Sync sync = Sync()) {
-    p2p_range<T, Sync>(c, start[c], start[c + 1], true, nullptr, first, count, rec, xq, icentre, cu2f, near, buf, part,
-                       tix, sync);
+                                         const float4* __restrict__ xlo, const int4* __restrict__ icentre,
+                                         const float* __restrict__ cu2f, double* __restrict__ near,
+                                         typename Vec4<T>::type* buf, T (*part)[4], int tix, Sync sync = Sync()) {
+    p2p_range<T, Sync>(c, start[c], start[c + 1], true, nullptr, first, count, rec, xq, xlo, icentre, cu2f, near, buf,
+                       part, tix, sync);
 }
 
 // ---------------------------------------------------------------- L2P
