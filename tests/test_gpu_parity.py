@@ -199,3 +199,25 @@ def test_tensor_core_m2l_every_padding(p):
     phitc, ftc = gpu_eval(ttc, wl.q)
     assert ttc.status() == fmm.FMM_OK
     assert O.rel_l2(phitc, phi32) <= 2e-5 and O.rel_l2(ftc, f32) <= 2e-5
+
+
+@pytest.mark.parametrize("prec,flags", [(1, 0), (2, 0), (3, 0), (3, "staged"), (3, "task_graph")])
+def test_close_pair_within_a_leaf(prec, flags):
+    """Two particles 1e-6 apart inside one leaf: their leaf-relative FP32
+    coordinates round at about 2^-24 of the leaf side, which would put a
+    relative error near 1e-3 on their separation; the FP32 forms recover it from
+    the coordinates' residuals, so the pair's force matches the FP64 path."""
+    import paper_1203_0889_gb300 as fmm
+    rng = np.random.default_rng(7)
+    pos = rng.random((6000, 3))
+    pos[1] = pos[0] + np.array([1e-6, 0.0, 0.0])
+    q = rng.uniform(-1, 1, 6000)
+    fl = {0: 0, "staged": fmm.STAGED, "task_graph": fmm.TASK_GRAPH}[flags]
+    t64 = gpu_tree(pos, p=6, leaf_size=32, theta=0.5, precision=fmm.PREC_FP64)
+    t = gpu_tree(pos, p=6, leaf_size=32, theta=0.5, precision=prec, flags=fl)
+    _, f64 = gpu_eval(t64, q)
+    _, f = gpu_eval(t, q)
+    assert t.status() == fmm.FMM_OK
+    for i in (0, 1):
+        assert np.linalg.norm(f[i] - f64[i]) <= 1e-5 * np.linalg.norm(f64[i]), (i, f[i], f64[i])
+    assert O.rel_l2(f, f64) <= 1e-5
