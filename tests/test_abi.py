@@ -83,3 +83,32 @@ def test_binding_refuses_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(fmm, "_LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         fmm.load()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structs have the sizes and field offsets that a C
+    compiler gives the structs of include/fmm.h."""
+    import shutil
+    import subprocess
+
+    import paper_1203_0889_gb300 as fmm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"fmm_params": fmm.Params, "fmm_tree_info": fmm.TreeInfo}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fmm.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
