@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--staged", action="store_true", help="one kernel per stage instead of the task queue")
     ap.add_argument("--task-graph", action="store_true",
                     help="mixed form: run the evaluation as one persistent task-graph launch (FMM_TASK_GRAPH)")
+    ap.add_argument("--mutual", action="store_true",
+                    help="mutual near field (FMM_MUTUAL): cross-leaf pairs evaluated once for both leaves")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--granularity-n", default="100000,1000000,10000000",
                     help="granularity study: particle counts (comma-separated)")
@@ -213,7 +215,7 @@ def traffic(kernel: str):
     return TRAFFIC.get(WORKLOAD, {}).get(kernel)
 
 
-def kernel_rooflines(stage_ms: dict, ex, prec: int, n_sm: int, info=None):
+def kernel_rooflines(stage_ms: dict, ex, prec: int, n_sm: int, info=None, mutual: bool = False):
     """Roofline objects of the evaluation's heavy kernels.  Their times are the
     library's own CUDA events around each stage inside the timed region,
     recorded on the stream the stage is launched on (P2P runs on the tree's
@@ -240,8 +242,11 @@ def kernel_rooflines(stage_ms: dict, ex, prec: int, n_sm: int, info=None):
         t = stage_ms["p2p"] * 1e-3
         flops = pairs * float(P2P_FLOPS_PER_PAIR)
         peak = FP64_TFLOPS_MEASURED if prec == 0 else fp32_peak
-        out.append({"kernel": "k_p2p", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
-                    "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": traffic("k_p2p"),
+        # the mutual form does the same directed pairs' work (each cross-leaf pair once)
+        kname = "k_p2p_mutual" if mutual and prec != 0 else "k_p2p"
+        out.append({"kernel": kname, "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak,
+                    "traffic": traffic("k_p2p") if kname == "k_p2p" else None,
                     "ms": stage_ms["p2p"],
                     "algorithmic": f"{pairs} pair interactions x {P2P_FLOPS_PER_PAIR} flops",
                     "peak_source": fp64_src if prec == 0 else fp32_src})
@@ -315,6 +320,8 @@ def fp64_roofline_ratio(value: float, n: int, ex, v64):
 
 
 def execution_name(args) -> str:
+    if args.mutual and args.precision != 0:
+        return "staged kernels, mutual near field"
     if args.staged:
         return "staged kernels"
     if args.precision == 3:
@@ -352,6 +359,53 @@ def schedule_variant(fmm, torch, pos, q, phi64, f64, flush, stream, flags: int, 
             "dtype": PREC_DTYPE[3],
             "rel_l2_vs_fp64_gpu": {"phi": float(((phi - phi64).norm() / phi64.norm()).item()),
                                    "force": float(((force - f64).norm() / f64.norm()).item())}}
+
+
+def mutual_variant(fmm, torch, pos, q, phi64, f64, flush, stream, ex, iso_p2p_ms, steps: int = 3):
+    """The mixed form with the mutual near field (FMM_MUTUAL, paper Section 4:
+    each cross-leaf pair evaluated once for both leaves) on the same system:
+    build + evaluation particles/s, the evaluation alone, the near-field stage
+    alone (FMM_NO_OVERLAP) against the non-mutual stage timed the same way, and
+    the error against the FP64 GPU path.  Pair rates count directed pairs, the
+    same algorithmic work in both forms."""
+    n = pos.shape[0]
+    phi = torch.empty_like(phi64)
+    force = torch.empty_like(f64)
+    ts, te, tp = [], [], []
+    for k in range(2 * steps + 2):
+        isolated = k >= steps + 1
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        t = fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=3,
+                           flags=fmm.MUTUAL | fmm.TIMING | (fmm.NO_OVERLAP if isolated else 0))
+        e1.record(stream)
+        t.evaluate(q, phi=phi, force=force)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        status = t.status()
+        stages = t.stage_times()
+        t.close()
+        if status != fmm.FMM_OK:
+            return {"error": f"status {status}"}
+        if isolated:
+            if k > steps + 1:
+                tp.append(stages.get("p2p", 0.0))
+        elif k >= 1:
+            ts.append(e0.elapsed_time(e2))
+            te.append(e1.elapsed_time(e2))
+    ms = statistics.median(ts)
+    pairs = p2p_pairs(ex)
+    p2p_ms = statistics.median(tp)
+    out = {"execution": "staged kernels, mutual near field", "value": n / (ms * 1e-3), "ms_per_step": ms,
+           "evaluate_ms": statistics.median(te), "steps": steps, "dtype": PREC_DTYPE[3],
+           "p2p_stage_ms_isolated": p2p_ms, "p2p_pairs_per_s_isolated": pairs / (p2p_ms * 1e-3),
+           "rel_l2_vs_fp64_gpu": {"phi": float(((phi - phi64).norm() / phi64.norm()).item()),
+                                  "force": float(((force - f64).norm() / f64.norm()).item())}}
+    if iso_p2p_ms:
+        out["non_mutual_p2p_stage_ms_isolated"] = iso_p2p_ms
+        out["non_mutual_p2p_pairs_per_s_isolated"] = pairs / (iso_p2p_ms * 1e-3)
+    return out
 
 
 def plummer_variant(fmm, torch, dev, flush, stream, steps: int = 3):
@@ -407,7 +461,8 @@ def run_ours(args):
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     force = torch.empty((n, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    flags = fmm.TIMING | (fmm.STAGED if args.staged else 0) | (fmm.TASK_GRAPH if args.task_graph else 0)
+    flags = fmm.TIMING | (fmm.STAGED if args.staged else 0) | (fmm.TASK_GRAPH if args.task_graph else 0) | \
+        (fmm.MUTUAL if args.mutual else 0)
 
     def step():
         t = fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=args.precision, flags=flags)
@@ -465,11 +520,11 @@ def run_ours(args):
     value = job_throughput(n, world, args.steps, total_s)
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
     props = torch.cuda.get_device_properties(dev)
-    roofs = kernel_rooflines(stage_ms, ex, args.precision, props.multi_processor_count, info)
+    roofs = kernel_rooflines(stage_ms, ex, args.precision, props.multi_processor_count, info, args.mutual)
     roof = max(roofs, key=lambda r: r["ms"]) if roofs else None
     passes = pass_rooflines(stage_ms, ex, args.precision, info, n)
     for r in roofs:
-        if r["kernel"] == "k_p2p":
+        if r["kernel"] in ("k_p2p", "k_p2p_mutual"):
             # the same pairs against the reciprocal-square-root (MUFU) bound, and both
             # bounds at the median SM clock seen under load
             f_load = clocks.get("sm_mhz") or 2070.0
@@ -482,8 +537,8 @@ def run_ours(args):
     # the same kernels with nothing running beside them (FMM_NO_OVERLAP: P2P and
     # the far field one after the other), outside the timed region: the step
     # overlaps P2P with the far field, which stretches both kernels' event times
-    if (args.precision == 3 and not args.task_graph) or args.staged:
-        iso_acc = {}
+    iso_acc = {}
+    if (args.precision == 3 and not args.task_graph) or args.staged or (args.mutual and args.precision != 0):
         for k in range(4):
             flush.zero_()
             ti = fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=args.precision,
@@ -495,7 +550,7 @@ def run_ours(args):
                     iso_acc[name] = iso_acc.get(name, 0.0) + ms / 3
             ti.close()
         iso = {r["kernel"]: r for r in kernel_rooflines(iso_acc, ex, args.precision, props.multi_processor_count,
-                                                         info)}
+                                                         info, args.mutual)}
         for r in roofs:
             if r["kernel"] in iso:
                 r["isolated"] = {k: iso[r["kernel"]][k] for k in ("ms", "achieved", "frac")}
@@ -547,6 +602,10 @@ def run_ours(args):
         if args.precision == 3:
             variants["task_graph" if not args.task_graph else "staged"] = schedule_variant(
                 fmm, torch, pos, q, phi64, f64, flush, stream, 0 if args.task_graph else fmm.TASK_GRAPH)
+            if not args.mutual:
+                variants["mutual_p2p"] = mutual_variant(
+                    fmm, torch, pos, q, phi64, f64, flush, stream, ex,
+                    iso_acc.get("p2p") if not args.task_graph else None)
 
     # end to end through the public API with host buffers
     e2e = None

@@ -70,6 +70,13 @@ extern "C" {
                                inside the same launch); without it the mixed form runs stage by
                                stage.  Ignored with FMM_STAGED or FMM_NO_OVERLAP and for the other
                                precisions (they run the persistent task queue by default). */
+#define FMM_MUTUAL      64  /* FP32 near field (precisions 1-3): mutual interaction (paper Section 4):
+                               the pairs of two different leaves are evaluated once and added to
+                               the particles of both leaves.  The evaluation runs stage by stage
+                               (no persistent queue or task graph).  Both sides' sums are added
+                               with floating-point atomics, so results are not bitwise
+                               reproducible from run to run (within the FP32 bar of the
+                               non-mutual form).  Ignored for FMM_PREC_FP64. */
 
 /* stage indices for fmm_stage_times / fmm_stage_name */
 #define FMM_STAGE_KEYS      0   /* root cube, Morton keys, key sort */

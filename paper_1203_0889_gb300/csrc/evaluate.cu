@@ -459,7 +459,8 @@ __global__ void __launch_bounds__(P2P_THREADS, sizeof(T) == 4 ? 9 : 1) k_p2p(con
 }
 
 // FP32 P2P: the pairs within each leaf, after k_p2p (which stages a leaf's own
-// particles at zero charge), added into near.  One warp per leaf, a lane per
+// particles at zero charge), added into near (acc given: the mutual form, near =
+// acc + the leaf's own pairs).  One warp per leaf, a lane per
 // target.  Separations come from the leaf-relative FP32 coordinates plus the
 // difference of their residuals, so two particles much closer than the leaf's
 // side keep their separation to FP32 precision; coincident pairs (separation
@@ -469,7 +470,9 @@ __global__ void __launch_bounds__(32 * P2P_OWN_WARPS) k_p2p_own(int nleaf, const
                                                                 const int32_t* __restrict__ first,
                                                                 const int32_t* __restrict__ count,
                                                                 const float4* __restrict__ xq,
-                                                                const float4* __restrict__ xlo, double* __restrict__ near) {
+                                                                const float4* __restrict__ xlo,
+                                                                const float4* __restrict__ acc,
+                                                                double* __restrict__ near) {
     __shared__ float4 sh[P2P_OWN_WARPS][32], sl[P2P_OWN_WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int li = blockIdx.x * P2P_OWN_WARPS + warp;
@@ -500,7 +503,13 @@ __global__ void __launch_bounds__(32 * P2P_OWN_WARPS) k_p2p_own(int nleaf, const
         }
         if (valid) {
             double* o = near + 4 * ((int64_t)tf + i);
-            o[0] += (double)ph; o[1] += (double)gx; o[2] += (double)gy; o[3] += (double)gz;
+            if (acc) {   // the mutual form's sums of the other leaves
+                const float4 b = acc[tf + i];
+                o[0] = (double)b.x + (double)ph; o[1] = (double)b.y + (double)gx;
+                o[2] = (double)b.z + (double)gy; o[3] = (double)b.w + (double)gz;
+            } else {
+                o[0] += (double)ph; o[1] += (double)gx; o[2] += (double)gy; o[3] += (double)gz;
+            }
         }
     }
 }
@@ -553,7 +562,9 @@ int alloc_eval_workspace(fmm_tree* t, cudaStream_t st) {
     if ((rc = dev_alloc(&M, (size_t)t->ncell * K * csz, t, st))) return rc;
     if ((rc = dev_alloc(&L, (size_t)t->ncell * K * csz, t, st))) return rc;
     // double4_32a copy always (P2M/L2P positions), plus float4 for FP32 P2P
-    size_t xb = (size_t)t->n * sizeof(double4_32a) + (p2p_fp64(t) ? 0 : (size_t)2 * t->n * sizeof(float4));
+    // (and, for the mutual near field, a float4 accumulator per particle)
+    size_t xb = (size_t)t->n * sizeof(double4_32a) +
+                (p2p_fp64(t) ? 0 : (size_t)(p2p_mutual(t) ? 3 : 2) * t->n * sizeof(float4));
     if ((rc = dev_alloc(&xq, xb, t, st))) return rc;
     if ((rc = dev_alloc(&d.near, (size_t)t->n * 4, t, st))) return rc;
     d.M = M; d.L = L; d.xq = xq;
@@ -696,6 +707,7 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     double4_32a* xq64 = (double4_32a*)d.xq;
     float4* xq32 = (float4*)((char*)d.xq + (size_t)n * sizeof(double4_32a));
     float4* xlo32 = xq32 + n;   // residuals of the FP32 coordinates (FP32 P2P only)
+    float4* acc32 = xq32 + 2 * n;   // mutual near field: sums of both leaves of every pair
     cplx<T>* M = (cplx<T>*)d.M;
     cplx<T>* L = (cplx<T>*)d.L;
     // particles in sorted order
@@ -729,20 +741,26 @@ static int evaluate_typed(fmm_tree* t, const Q* q, O* phi, O* force, cudaStream_
     // the item count from the build (pinned host words), else the bound with the
     // surplus blocks returning at once; split leaves add into a zeroed near
     const unsigned nitems = (unsigned)(t->h_pin && t->h_pin[0] >= 0 ? t->h_pin[0] : t->p2p_items_bound);
+    // mutual form: the cross-leaf pairs once for both leaves into acc32, then
+    // near = acc32 + each leaf's own pairs
+    const bool mutual = p2p_mutual(t);
     if (nitems == 0)
         ;
     else if (p2p_fp64(t))
         k_p2p<double><<<nitems, P2P_THREADS, 0, sp>>>(d.p2p_items, d.p2p_nitems, d.p2p_split, d.p2p_arrived,
                                                         d.p2p_part, d.first, d.count, d.p2p_start,
                                                         d.p2p_rec, xq64, nullptr, d.icentre, d.cu2f, d.near);
-    else
+    else if (mutual) {
+        const int rcm = p2p_mutual_launch(t, xq32, acc32, sp);
+        if (rcm) return rcm;
+    } else
         k_p2p<float><<<nitems, P2P_THREADS, 0, sp>>>(d.p2p_items, d.p2p_nitems, d.p2p_split, d.p2p_arrived,
                                                        d.p2p_part, d.first, d.count, d.p2p_start,
                                                        d.p2p_rec, xq32, xlo32, d.icentre, d.cu2f, d.near);
-    count_launch(t);
+    if (!mutual) count_launch(t);
     if (nitems > 0 && !p2p_fp64(t)) {
-        k_p2p_own<<<nblk(t->nleaf, P2P_OWN_WARPS), 32 * P2P_OWN_WARPS, 0, sp>>>(t->nleaf, d.leaves, d.first, d.count,
-                                                                                xq32, xlo32, d.near);
+        k_p2p_own<<<nblk(t->nleaf, P2P_OWN_WARPS), 32 * P2P_OWN_WARPS, 0, sp>>>(
+            t->nleaf, d.leaves, d.first, d.count, xq32, xlo32, mutual ? acc32 : nullptr, d.near);
         count_launch(t);
     }
     stage_end(t, FMM_STAGE_P2P, sp);

@@ -176,6 +176,7 @@ struct TreeDev {
     // back to 0 after the combine), p2p_part (4 doubles per slot: item x target)
     int4* p2p_items = nullptr;
     int32_t* p2p_nitems = nullptr;
+    int8_t* p2p_mode = nullptr;     // [np2p] FMM_MUTUAL: 0 skip, 1 this direction only, 2 both leaves
     int32_t* rem_count = nullptr;   // chunks of the CUDA-core M2L (device word, copied to h_pin[4])
     int4* p2p_split = nullptr;
     int32_t* p2p_arrived = nullptr;
@@ -329,10 +330,17 @@ template <typename T, typename TP, typename O>
 int evaluate_queue(fmm_tree* t, const double4_32a* xq64, const void* xqp, O* phi, O* force, cudaStream_t st,
                    const float4* xlo = nullptr);
 bool tc_supported(int p);
+// FMM_MUTUAL with an FP32 near field: cross-leaf pairs evaluated once for both
+// leaves (p2p_mutual.cu); the evaluation then runs stage by stage
+inline bool p2p_mutual(const fmm_tree* t) {
+    return (t->prm.flags & FMM_MUTUAL) && t->prm.precision != FMM_PREC_FP64;
+}
+int build_p2p_modes(fmm_tree* t, const int32_t* tgt, cudaStream_t st);   // tgt: target of every record
+int p2p_mutual_launch(fmm_tree* t, const float4* xq32, float4* acc, cudaStream_t st);
 // the mixed form runs as one task-graph launch unless a stage-by-stage flag is set
 inline bool tc_uses_dag(const fmm_tree* t) {
     return t->prm.precision == FMM_PREC_MIXED_TC && tc_supported(t->prm.p) && (t->prm.flags & FMM_TASK_GRAPH) &&
-           !(t->prm.flags & (FMM_STAGED | FMM_NO_OVERLAP));
+           !(t->prm.flags & (FMM_STAGED | FMM_NO_OVERLAP)) && !p2p_mutual(t);
 }
 int build_dag(fmm_tree* t, cudaStream_t st);
 int tc_epilogue_warps();   // epilogue warps per tensor-core block: each counts an item once

@@ -292,7 +292,8 @@ __global__ void k_iota(int n, int32_t* v) {
 }
 
 bool queue_supported(const fmm_tree* t) {
-    return !(t->prm.flags & FMM_STAGED) && t->prm.precision != FMM_PREC_MIXED_TC && ntri(t->prm.p) <= 96;
+    return !(t->prm.flags & FMM_STAGED) && t->prm.precision != FMM_PREC_MIXED_TC && ntri(t->prm.p) <= 96 &&
+           !p2p_mutual(t);
 }
 
 int build_queue(fmm_tree* t, cudaStream_t st) {

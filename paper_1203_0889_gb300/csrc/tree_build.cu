@@ -46,6 +46,7 @@ template int dev_alloc<double4_32a>(double4_32a**, size_t, fmm_tree*, cudaStream
 template int dev_alloc<unsigned long long>(unsigned long long**, size_t, fmm_tree*, cudaStream_t);
 template int dev_alloc<cplx<float>>(cplx<float>**, size_t, fmm_tree*, cudaStream_t);
 template int dev_alloc<char2>(char2**, size_t, fmm_tree*, cudaStream_t);
+template int dev_alloc<int8_t>(int8_t**, size_t, fmm_tree*, cudaStream_t);
 
 template <typename T>
 static void dev_free(T*& p, cudaStream_t st) {
@@ -1010,6 +1011,7 @@ static int finish_p2p_list(fmm_tree* t, int2* pairs, int64_t np, cudaStream_t st
         k_p2p_records<<<nblk(np, 256), 256, 0, st>>>(np, d.p2p_src, tgt, d.p2p_start, d.first, d.count, gcum,
                                                         d.p2p_rec);
         count_launch(t, 2);
+        if (p2p_mutual(t) && (rc = build_p2p_modes(t, tgt, st))) return rc;
     }
     dev_free(cnt, st);
     dev_free(gcum, st);
@@ -1515,7 +1517,7 @@ void free_tree_device(fmm_tree* t) {
     if (d.grad_tmp) cudaFreeAsync(d.grad_tmp, st);
     d.grad_tmp = nullptr;
     dev_free(d.m2l_tgt, st); dev_free(d.p2p_rec, st); dev_free(d.p2p_items, st); dev_free(d.p2p_nitems, st);
-    dev_free(d.p2p_split, st); dev_free(d.p2p_arrived, st); dev_free(d.p2p_part, st); dev_free(d.rem_count, st); dev_free(d.tc_items, st); dev_free(d.tc_block_first, st); dev_free(d.tc_item_list, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
+    dev_free(d.p2p_mode, st); dev_free(d.p2p_split, st); dev_free(d.p2p_arrived, st); dev_free(d.p2p_part, st); dev_free(d.rem_count, st); dev_free(d.tc_items, st); dev_free(d.tc_block_first, st); dev_free(d.tc_item_list, st); dev_free(d.tc_tgt, st); dev_free(d.tc_src, st);
     dev_free(d.rem_start, st); dev_free(d.rem_chunks, st);
     dev_free(d.dag_cnt_init, st); dev_free(d.dag_cnt, st); dev_free(d.dag_q_init, st); dev_free(d.dag_q, st);
     dev_free(d.dag_lvl, st); dev_free(d.dag_ctr, st); dev_free(d.dag_zero_first, st);

@@ -48,7 +48,7 @@ def test_version_and_argument_errors(lib):
     assert lib.fmm_build_tree(None, 10, None, 0, C.byref(out), None) == fmm.FMM_ERR_ARG
     assert b"params" in lib.fmm_last_error()
     bad = [fmm.Params(-1, 64, 0.5, 0, 0, 0), fmm.Params(4, 0, 0.5, 0, 0, 0), fmm.Params(4, 64, 1.5, 0, 0, 0),
-           fmm.Params(4, 64, 0.5, 9, 0, 0), fmm.Params(4, 64, 0.5, 0, 64, 0), fmm.Params(21, 64, 0.5, 0, 0, 0),
+           fmm.Params(4, 64, 0.5, 9, 0, 0), fmm.Params(4, 64, 0.5, 0, 128, 0), fmm.Params(21, 64, 0.5, 0, 0, 0),
            fmm.Params(4, 64, 0.0, 0, 0, 0), fmm.Params(4, 64, 0.5, 0, 0, -1),
            fmm.Params(4, 64, 0.5, 0, 0, 0, 4, 0), fmm.Params(4, 64, 0.5, 0, 0, 0, 70000, 0),
            fmm.Params(4, 64, 0.5, 0, 0, 0, 0, -3), fmm.Params(4, 64, 0.5, 0, 0, 0, 0, 5000)]
@@ -75,6 +75,19 @@ def test_stage_names_agree(lib):
     assert len(fmm.STAGE_NAMES) == nstage
     assert [lib.fmm_stage_name(i).decode() for i in range(nstage)] == list(fmm.STAGE_NAMES)
     assert lib.fmm_stage_name(nstage) == b"" and lib.fmm_stage_name(-1) == b""
+
+
+def test_flag_values_match_the_header():
+    """Every FMM_* flag and precision the binding exports has the header's value."""
+    import paper_1203_0889_gb300 as fmm
+    txt = open(os.path.join(ROOT, "include", "fmm.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define FMM_(\w+)\s+(-?\d+)", txt)}
+    for name in ("OUT_FIELD", "STAGED", "TIMING", "NO_OVERLAP", "BUILD_FALLBACKS", "TASK_GRAPH", "MUTUAL",
+                 "PREC_FP64", "PREC_FP32_P2P", "PREC_FP32", "PREC_MIXED_TC"):
+        assert defs[name] == getattr(fmm, name), name
+    flags = [defs[k] for k in ("OUT_FIELD", "STAGED", "TIMING", "NO_OVERLAP", "BUILD_FALLBACKS", "TASK_GRAPH",
+                               "MUTUAL")]
+    assert sorted(flags) == [1 << i for i in range(len(flags))]
 
 
 def test_binding_refuses_without_library(monkeypatch, tmp_path):

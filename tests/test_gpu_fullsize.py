@@ -71,6 +71,31 @@ def test_metric_workload(clustered, prec):
     assert e_phi <= TIGHT[prec] and e_f <= TIGHT[prec], (e_phi, e_f)
 
 
+@pytest.mark.parametrize("prec", [1, 3])
+def test_metric_workload_mutual(clustered, prec):
+    """The mutual near field (FMM_MUTUAL) on the 4M clustered workload: sampled
+    leaves against the oracle at the non-mutual form's bars, every particle
+    against the non-mutual form on the same positions."""
+    import paper_1203_0889_gb300 as fmm
+    torch, dev = torch_dev()
+    wl, ref, idx, ref_phi, ref_f = clustered
+    pos = torch.tensor(wl.pos, dtype=torch.float64, device=dev)
+    q = torch.tensor(wl.q, dtype=torch.float64, device=dev)
+    kw = dict(p=wl.p, leaf_size=wl.leaf_size, theta=wl.theta, precision=prec)
+    staged = fmm.STAGED if prec != 3 else 0
+    t = fmm.build_tree(pos, flags=fmm.MUTUAL | staged, **kw)
+    phi, force = t.evaluate(q)
+    t1 = fmm.build_tree(pos, flags=staged, **kw)
+    phi1, force1 = t1.evaluate(q)
+    torch.cuda.synchronize()
+    assert t.status() == fmm.FMM_OK
+    assert ((phi - phi1).norm() / phi1.norm()).item() <= 1e-6
+    assert ((force - force1).norm() / force1.norm()).item() <= 1e-6
+    phi, force = phi.cpu().numpy()[idx], force.cpu().numpy()[idx]
+    e_phi, e_f = O.rel_l2(phi, ref_phi), O.rel_l2(force, ref_f)
+    assert e_phi <= TIGHT[prec] and e_f <= TIGHT[prec], (e_phi, e_f)
+
+
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_bench_workload(plummer, prec):
     import paper_1203_0889_gb300 as fmm
