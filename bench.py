@@ -13,10 +13,12 @@ radius 1 truncated at r = 50, charges 1/N, p = 8, leaf 64, theta = 0.4).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 The headline is the mixed form (tensor-core M2L from split bf16 products,
-FP32 elsewhere), whose error against the plain FP64 GPU path is measured in
-the same run and printed beside it; the FP64, FP32-P2P/FP64-expansion and
-FP32 forms are timed on the same system as context ("variants"), and the
-mixed form of the Plummer configuration with its own error.
+FP32 elsewhere, the near field in the mutual form: each pair of two different
+leaves evaluated once for both), whose error against the plain FP64 GPU path
+is measured in the same run and printed beside it; the FP64,
+FP32-P2P/FP64-expansion and FP32 forms, the non-mutual near field and the task
+graph are timed on the same system as context ("variants"), and the mixed form
+of the Plummer configuration with its own error.
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own system
 (replicas: the single-system path has no exchange step) and the value is the
@@ -84,8 +86,9 @@ def parse():
     ap.add_argument("--staged", action="store_true", help="one kernel per stage instead of the task queue")
     ap.add_argument("--task-graph", action="store_true",
                     help="mixed form: run the evaluation as one persistent task-graph launch (FMM_TASK_GRAPH)")
-    ap.add_argument("--mutual", action="store_true",
-                    help="mutual near field (FMM_MUTUAL): cross-leaf pairs evaluated once for both leaves")
+    ap.add_argument("--mutual", action=argparse.BooleanOptionalAction, default=True,
+                    help="mutual near field (FMM_MUTUAL): cross-leaf pairs evaluated once for both leaves "
+                         "(FP32 near field, stage-by-stage evaluation; not with --task-graph)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--granularity-n", default="100000,1000000,10000000",
                     help="granularity study: particle counts (comma-separated)")
@@ -319,8 +322,14 @@ def fp64_roofline_ratio(value: float, n: int, ex, v64):
             "fp64_frac_of_roofline": ideal_s * 1e3 / v64["ms_per_step"]}
 
 
+def use_mutual(args) -> bool:
+    """The mutual near field applies to the FP32 near field of the stage-by-stage
+    evaluation (the task graph and the FP64 path keep the non-mutual form)."""
+    return args.mutual and args.precision != 0 and not args.task_graph
+
+
 def execution_name(args) -> str:
-    if args.mutual and args.precision != 0:
+    if use_mutual(args):
         return "staged kernels, mutual near field"
     if args.staged:
         return "staged kernels"
@@ -361,13 +370,14 @@ def schedule_variant(fmm, torch, pos, q, phi64, f64, flush, stream, flags: int, 
                                    "force": float(((force - f64).norm() / f64.norm()).item())}}
 
 
-def mutual_variant(fmm, torch, pos, q, phi64, f64, flush, stream, ex, iso_p2p_ms, steps: int = 3):
-    """The mixed form with the mutual near field (FMM_MUTUAL, paper Section 4:
-    each cross-leaf pair evaluated once for both leaves) on the same system:
-    build + evaluation particles/s, the evaluation alone, the near-field stage
-    alone (FMM_NO_OVERLAP) against the non-mutual stage timed the same way, and
-    the error against the FP64 GPU path.  Pair rates count directed pairs, the
-    same algorithmic work in both forms."""
+def p2p_form_variant(fmm, torch, pos, q, phi64, f64, flush, stream, ex, mutual: bool, iso_p2p_ms, steps: int = 3):
+    """The mixed form with the other near-field form on the same system: the
+    mutual one (FMM_MUTUAL, paper Section 4: each cross-leaf pair evaluated once
+    for both leaves) or the non-mutual one (each leaf's sums by its own work
+    items).  Build + evaluation particles/s, the evaluation alone, the near-field
+    stage alone (FMM_NO_OVERLAP) beside the headline form's stage timed the same
+    way, and the error against the FP64 GPU path.  Pair rates count directed
+    pairs, the same algorithmic work in both forms."""
     n = pos.shape[0]
     phi = torch.empty_like(phi64)
     force = torch.empty_like(f64)
@@ -378,7 +388,7 @@ def mutual_variant(fmm, torch, pos, q, phi64, f64, flush, stream, ex, iso_p2p_ms
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         t = fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=3,
-                           flags=fmm.MUTUAL | fmm.TIMING | (fmm.NO_OVERLAP if isolated else 0))
+                           flags=(fmm.MUTUAL if mutual else 0) | fmm.TIMING | (fmm.NO_OVERLAP if isolated else 0))
         e1.record(stream)
         t.evaluate(q, phi=phi, force=force)
         e2.record(stream)
@@ -397,14 +407,14 @@ def mutual_variant(fmm, torch, pos, q, phi64, f64, flush, stream, ex, iso_p2p_ms
     ms = statistics.median(ts)
     pairs = p2p_pairs(ex)
     p2p_ms = statistics.median(tp)
-    out = {"execution": "staged kernels, mutual near field", "value": n / (ms * 1e-3), "ms_per_step": ms,
-           "evaluate_ms": statistics.median(te), "steps": steps, "dtype": PREC_DTYPE[3],
+    out = {"execution": "staged kernels" + (", mutual near field" if mutual else ""), "value": n / (ms * 1e-3),
+           "ms_per_step": ms, "evaluate_ms": statistics.median(te), "steps": steps, "dtype": PREC_DTYPE[3],
            "p2p_stage_ms_isolated": p2p_ms, "p2p_pairs_per_s_isolated": pairs / (p2p_ms * 1e-3),
            "rel_l2_vs_fp64_gpu": {"phi": float(((phi - phi64).norm() / phi64.norm()).item()),
                                   "force": float(((force - f64).norm() / f64.norm()).item())}}
     if iso_p2p_ms:
-        out["non_mutual_p2p_stage_ms_isolated"] = iso_p2p_ms
-        out["non_mutual_p2p_pairs_per_s_isolated"] = pairs / (iso_p2p_ms * 1e-3)
+        out["headline_p2p_stage_ms_isolated"] = iso_p2p_ms
+        out["headline_p2p_pairs_per_s_isolated"] = pairs / (iso_p2p_ms * 1e-3)
     return out
 
 
@@ -462,7 +472,7 @@ def run_ours(args):
     force = torch.empty((n, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     flags = fmm.TIMING | (fmm.STAGED if args.staged else 0) | (fmm.TASK_GRAPH if args.task_graph else 0) | \
-        (fmm.MUTUAL if args.mutual else 0)
+        (fmm.MUTUAL if use_mutual(args) else 0)
 
     def step():
         t = fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=args.precision, flags=flags)
@@ -520,7 +530,7 @@ def run_ours(args):
     value = job_throughput(n, world, args.steps, total_s)
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
     props = torch.cuda.get_device_properties(dev)
-    roofs = kernel_rooflines(stage_ms, ex, args.precision, props.multi_processor_count, info, args.mutual)
+    roofs = kernel_rooflines(stage_ms, ex, args.precision, props.multi_processor_count, info, use_mutual(args))
     roof = max(roofs, key=lambda r: r["ms"]) if roofs else None
     passes = pass_rooflines(stage_ms, ex, args.precision, info, n)
     for r in roofs:
@@ -538,7 +548,7 @@ def run_ours(args):
     # the far field one after the other), outside the timed region: the step
     # overlaps P2P with the far field, which stretches both kernels' event times
     iso_acc = {}
-    if (args.precision == 3 and not args.task_graph) or args.staged or (args.mutual and args.precision != 0):
+    if (args.precision == 3 and not args.task_graph) or args.staged or use_mutual(args):
         for k in range(4):
             flush.zero_()
             ti = fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=args.precision,
@@ -550,7 +560,7 @@ def run_ours(args):
                     iso_acc[name] = iso_acc.get(name, 0.0) + ms / 3
             ti.close()
         iso = {r["kernel"]: r for r in kernel_rooflines(iso_acc, ex, args.precision, props.multi_processor_count,
-                                                         info, args.mutual)}
+                                                         info, use_mutual(args))}
         for r in roofs:
             if r["kernel"] in iso:
                 r["isolated"] = {k: iso[r["kernel"]][k] for k in ("ms", "achieved", "frac")}
@@ -602,10 +612,10 @@ def run_ours(args):
         if args.precision == 3:
             variants["task_graph" if not args.task_graph else "staged"] = schedule_variant(
                 fmm, torch, pos, q, phi64, f64, flush, stream, 0 if args.task_graph else fmm.TASK_GRAPH)
-            if not args.mutual:
-                variants["mutual_p2p"] = mutual_variant(
-                    fmm, torch, pos, q, phi64, f64, flush, stream, ex,
-                    iso_acc.get("p2p") if not args.task_graph else None)
+            if not args.task_graph:
+                other = not use_mutual(args)
+                variants["mutual_p2p" if other else "non_mutual_p2p"] = p2p_form_variant(
+                    fmm, torch, pos, q, phi64, f64, flush, stream, ex, other, iso_acc.get("p2p"))
 
     # end to end through the public API with host buffers
     e2e = None

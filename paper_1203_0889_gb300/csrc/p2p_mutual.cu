@@ -19,7 +19,8 @@
 // measured, so mode 1 is a safeguard).
 //
 // Kernel layout (one warp per P2P work item, i.e. a run of a target leaf's
-// records).  The target leaf's particles are held two per lane; W = ceil(nt/2)
+// records).  The target leaf's particles, 32 at a time, are held two per lane
+// (in the halves of 64-bit registers, paired f32x2 arithmetic); W = ceil(nt/2)
 // lanes form a ring and 32 / W rings share the warp.  The item's selected
 // sources form one stream (records compacted per chunk of 32 records); each
 // ring takes W sources at a time, one per lane, into shared memory, and runs W
@@ -72,10 +73,37 @@ __device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c,
 }
 
 constexpr int MU_WARPS = 4;
+// targets per pass over an item's sources: two per lane, so rings of at most 16
+// lanes and at least two rings per warp (64 left up to half the lanes idle on
+// leaves of 33 .. 64 particles; a second pass costs one more reaction add per
+// source)
+constexpr int MU_TARGETS = 32;
 // dummy particles (zero charge) of ragged rings: targets and sources far from
 // every particle and from each other, so that every pair they enter is finite
 // and contributes exactly zero to the real particles
 constexpr float MU_FAR = 1e18f;
+
+// the source of stream position k of the chunk (srec), in the target's frame,
+// negated (-x, -y, -z, q); gi = the particle that takes its reaction, or -1
+// (past the stream's end: a dummy at +MU_FAR)
+__device__ __forceinline__ void mu_source(int k, int total, bool inring, const int4* srec, int& cur,
+                                          const float4* __restrict__ xq, const int4* __restrict__ icentre, int4 ict,
+                                          float u2f, float4& s, int& gi) {
+    s = make_float4(-MU_FAR, -MU_FAR, -MU_FAR, 0.f);
+    gi = -1;
+    if (inring && k < total) {
+        while (srec[cur].z + srec[cur].y <= k) cur++;
+        const int4 q = srec[cur];
+        const int src = q.w & 0x7fffffff;
+        const int j = q.x + (k - q.z);
+        const int4 ics = icentre[src];
+        const float ox = (float)(ics.x - ict.x) * u2f, oy = (float)(ics.y - ict.y) * u2f,
+                    oz = (float)(ics.z - ict.z) * u2f;
+        const float4 v = xq[j];
+        s = make_float4(-(v.x + ox), -(v.y + oy), -(v.z + oz), v.w);
+        if (q.w < 0) gi = j;
+    }
+}
 
 __global__ void __launch_bounds__(32 * MU_WARPS) k_p2p_mutual(const int4* __restrict__ items,
                                                               const int32_t* __restrict__ nitems,
@@ -87,7 +115,7 @@ __global__ void __launch_bounds__(32 * MU_WARPS) k_p2p_mutual(const int4* __rest
                                                               const float4* __restrict__ xq,
                                                               const int4* __restrict__ icentre,
                                                               const float* __restrict__ cu2f, float4* acc) {
-    __shared__ float4 ssrc[MU_WARPS][32];   // the ring sources of the current round, in the target's frame
+    __shared__ float4 ssrc[MU_WARPS][32];   // the ring sources of the current round: -x, -y, -z, q
     __shared__ int4 srec[MU_WARPS][32];     // selected records of the chunk: first, count, stream offset, source
     const unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -99,18 +127,23 @@ __global__ void __launch_bounds__(32 * MU_WARPS) k_p2p_mutual(const int4* __rest
     const int tf = first[c], nt = count[c];
     const int4 ict = icentre[c];
     const float u2f = cu2f[c];
-    for (int tb = 0; tb < nt; tb += 64) {
-        const int ntc = min(64, nt - tb);
+    const f2::u64 EPS2 = f2::pack(1e-30f, 1e-30f);
+    for (int tb = 0; tb < nt; tb += MU_TARGETS) {
+        const int ntc = min(MU_TARGETS, nt - tb);
         const int W = (ntc + 1) >> 1, R = 32 / W;
         const int g = lane / W, pos = lane - g * W;
         const bool inring = g < R;
         // lanes outside every ring read their own slot and pass to themselves
         const int rbase = inring ? g * W : lane, rw = inring ? W : 1;
         const int nxt = inring ? rbase + (pos + 1 == W ? 0 : pos + 1) : lane;
-        float4 t0 = make_float4(-MU_FAR, -MU_FAR, -MU_FAR, 0.f), t1 = t0;
+        // targets pos (low halves) and pos + W (high halves); dummy: far, no charge
+        float4 t0 = make_float4(-MU_FAR, -MU_FAR, -MU_FAR, 0.f), t1 = t0;   // dummy sources sit at +MU_FAR
         if (inring) t0 = xq[tf + tb + pos];   // pos < W <= ntc
         if (inring && pos + W < ntc) t1 = xq[tf + tb + pos + W];
-        float p0 = 0.f, x0 = 0.f, y0 = 0.f, z0 = 0.f, p1 = 0.f, x1 = 0.f, y1 = 0.f, z1 = 0.f;
+        const f2::u64 X = f2::pack(t0.x, t1.x), Y = f2::pack(t0.y, t1.y), Z = f2::pack(t0.z, t1.z),
+                      Q = f2::pack(t0.w, t1.w);
+        // potential and G = sum q_s d / r^3 of both targets (the gradient is -G)
+        f2::u64 NP = 0, GX = 0, GY = 0, GZ = 0;
         for (int64_t cb = s0; cb < s1; cb += 32) {
             const int64_t e = cb + lane;
             int md = 0;
@@ -134,59 +167,57 @@ __global__ void __launch_bounds__(32 * MU_WARPS) k_p2p_mutual(const int4* __rest
             __syncwarp();
             const int nround = (total + W - 1) / W;
             int cur = 0;
+            float4 s;
+            int gi;
+            mu_source(g * W + pos, total, inring, srec[warp], cur, xq, icentre, ict, u2f, s, gi);
             for (int rb = 0; rb < nround; rb += R) {
-                const int k = (rb + g) * W + pos;   // this lane's source in the chunk's stream
-                float4 s = make_float4(MU_FAR, MU_FAR, MU_FAR, 0.f);
-                int gi = -1;   // source particle that receives the reaction (-1: none)
-                if (inring && k < total) {
-                    while (srec[warp][cur].z + srec[warp][cur].y <= k) cur++;
-                    const int4 q = srec[warp][cur];
-                    const int src = q.w & 0x7fffffff;
-                    const int j = q.x + (k - q.z);
-                    const int4 ics = icentre[src];
-                    const float ox = (float)(ics.x - ict.x) * u2f, oy = (float)(ics.y - ict.y) * u2f,
-                                oz = (float)(ics.z - ict.z) * u2f;
-                    const float4 v = xq[j];
-                    s = make_float4(v.x + ox, v.y + oy, v.z + oz, v.w);
-                    if (q.w < 0) gi = j;
-                }
                 __syncwarp();   // the previous round's reads of ssrc are done
                 ssrc[warp][lane] = s;
+                const int gcur = gi;
                 __syncwarp();
+                // the next round's source, loaded while this round runs
+                if (rb + R < nround)
+                    mu_source((rb + R + g) * W + pos, total, inring, srec[warp], cur, xq, icentre, ict, u2f, s, gi);
                 float ap = 0.f, ax = 0.f, ay = 0.f, az = 0.f;   // reaction of the source in this lane's slot
                 int idx = pos < rw ? pos : 0;
                 for (int step = 0; step < W; step++) {
                     const float4 sj = ssrc[warp][rbase + idx];
-                    const float dx0 = t0.x - sj.x, dy0 = t0.y - sj.y, dz0 = t0.z - sj.z;
-                    const float dx1 = t1.x - sj.x, dy1 = t1.y - sj.y, dz1 = t1.z - sj.z;
+                    const f2::u64 dx = f2::add(X, f2::pack(sj.x, sj.x)), dy = f2::add(Y, f2::pack(sj.y, sj.y)),
+                                  dz = f2::add(Z, f2::pack(sj.z, sj.z));
                     // r^2 from 1e-30 like the non-mutual cross-leaf pairs: a
                     // near-duplicate across a leaf boundary stays finite
-                    const float ri0 = rsqrt_t(fmaf(dz0, dz0, fmaf(dy0, dy0, fmaf(dx0, dx0, 1e-30f))));
-                    const float ri1 = rsqrt_t(fmaf(dz1, dz1, fmaf(dy1, dy1, fmaf(dx1, dx1, 1e-30f))));
-                    const float r20 = ri0 * ri0, r21 = ri1 * ri1;
-                    const float qs0 = sj.w * ri0, qs1 = sj.w * ri1;   // the source on the targets
-                    p0 += qs0; p1 += qs1;
-                    const float gs0 = qs0 * r20, gs1 = qs1 * r21;
-                    x0 = fmaf(-gs0, dx0, x0); y0 = fmaf(-gs0, dy0, y0); z0 = fmaf(-gs0, dz0, z0);
-                    x1 = fmaf(-gs1, dx1, x1); y1 = fmaf(-gs1, dy1, y1); z1 = fmaf(-gs1, dz1, z1);
-                    const float qt0 = t0.w * ri0, qt1 = t1.w * ri1;   // the targets on the source
-                    ap += qt0 + qt1;
-                    const float gt0 = qt0 * r20, gt1 = qt1 * r21;
-                    ax = fmaf(gt0, dx0, fmaf(gt1, dx1, ax));
-                    ay = fmaf(gt0, dy0, fmaf(gt1, dy1, ay));
-                    az = fmaf(gt0, dz0, fmaf(gt1, dz1, az));
+                    float ra, rb2;
+                    f2::unpack(f2::fma(dz, dz, f2::fma(dy, dy, f2::fma(dx, dx, EPS2))), ra, rb2);
+                    const f2::u64 ri = f2::pack(rsqrt_t(ra), rsqrt_t(rb2));
+                    const f2::u64 ri2 = f2::mul(ri, ri);
+                    const f2::u64 qs = f2::mul(f2::pack(sj.w, sj.w), ri);   // the source on the targets
+                    NP = f2::add(NP, qs);
+                    const f2::u64 gs = f2::mul(qs, ri2);
+                    GX = f2::fma(gs, dx, GX); GY = f2::fma(gs, dy, GY); GZ = f2::fma(gs, dz, GZ);
+                    const f2::u64 qt = f2::mul(Q, ri);   // the targets on the source
+                    const f2::u64 gt = f2::mul(qt, ri2);
+                    float qa, qb, ga, gb, da, db;
+                    f2::unpack(qt, qa, qb);
+                    f2::unpack(gt, ga, gb);
+                    ap += qa + qb;
+                    f2::unpack(dx, da, db); ax = fmaf(ga, da, fmaf(gb, db, ax));
+                    f2::unpack(dy, da, db); ay = fmaf(ga, da, fmaf(gb, db, ay));
+                    f2::unpack(dz, da, db); az = fmaf(ga, da, fmaf(gb, db, az));
                     ap = __shfl_sync(FULL, ap, nxt);
                     ax = __shfl_sync(FULL, ax, nxt);
                     ay = __shfl_sync(FULL, ay, nxt);
                     az = __shfl_sync(FULL, az, nxt);
                     idx = idx + 1 == rw ? 0 : idx + 1;
                 }
-                if (gi >= 0) red_add_v4(acc + gi, ap, ax, ay, az);
+                if (gcur >= 0) red_add_v4(acc + gcur, ap, ax, ay, az);
             }
         }
         if (inring) {
-            red_add_v4(acc + tf + tb + pos, p0, x0, y0, z0);
-            if (pos + W < ntc) red_add_v4(acc + tf + tb + pos + W, p1, x1, y1, z1);
+            float pa, pb, xa, xb, ya, yb, za, zb;
+            f2::unpack(NP, pa, pb);
+            f2::unpack(GX, xa, xb); f2::unpack(GY, ya, yb); f2::unpack(GZ, za, zb);
+            red_add_v4(acc + tf + tb + pos, pa, -xa, -ya, -za);
+            if (pos + W < ntc) red_add_v4(acc + tf + tb + pos + W, pb, -xb, -yb, -zb);
         }
     }
 }
