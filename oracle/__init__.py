@@ -17,6 +17,8 @@ Functions and what they follow:
   flow of Section 2.1.
 * ``p2m``, ``m2m``, ``m2l``, ``l2l``, ``l2p``, ``m2p`` -- single operators,
   used by the pins (complex coefficients, index n*n + n + m, m = -n..n).
+* ``uvwx`` (submodule) -- the parent-neighbour-child lists U, V, W, X of
+  Section 2.1's alternative separation rule and the potential through them.
 """
 from __future__ import annotations
 
