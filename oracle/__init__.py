@@ -19,6 +19,8 @@ Functions and what they follow:
   used by the pins (complex coefficients, index n*n + n + m, m = -n..n).
 * ``uvwx`` (submodule) -- the parent-neighbour-child lists U, V, W, X of
   Section 2.1's alternative separation rule and the potential through them.
+* ``force_grad`` (submodule) -- the direct-sum gradient of a loss on
+  potentials and forces (what a backward for force-dependent losses computes).
 """
 from __future__ import annotations
 

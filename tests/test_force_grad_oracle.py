@@ -1,0 +1,85 @@
+"""Pins of the oracle's gradient of a loss on potentials and forces (the
+backward a force-dependent loss needs), against quantities computed by the
+oracle's C direct sum, which shares no code with it:
+
+* central finite differences of L(x, q) in every coordinate and charge of a
+  small system (L evaluated from ``oracle.direct``);
+* with b = 0 the loss is linear in the potential, and its gradient is two
+  direct sums: dL/dq = the potential of the charges a, dL/dx_k = a_k grad phi_k
+  + q_k grad phi^(a)_k;
+* the loss only depends on differences of positions, so dL/dx sums to zero.
+A planted slip (a dropped source-side term) fails the finite differences."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import force_grad as FG
+
+
+def _system(n, seed):
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, 3))
+    q = rng.uniform(-1, 1, n)
+    a = rng.standard_normal(n)
+    b = rng.standard_normal((n, 3))
+    return pos, q, a, b
+
+
+def _loss(pos, q, a, b):
+    phi, g = O.direct(pos, q)
+    return FG.loss(pos, q, a, b, phi, g)
+
+
+def _fd(pos, q, a, b, h=1e-6):
+    n = len(q)
+    dx = np.zeros((n, 3))
+    dq = np.zeros(n)
+    for k in range(n):
+        for c in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[k, c] += h
+            pm[k, c] -= h
+            dx[k, c] = (_loss(pp, q, a, b) - _loss(pm, q, a, b)) / (2 * h)
+        qp, qm = q.copy(), q.copy()
+        qp[k] += h
+        qm[k] -= h
+        dq[k] = (_loss(pos, qp, a, b) - _loss(pos, qm, a, b)) / (2 * h)
+    return dx, dq
+
+
+@pytest.mark.parametrize("n,seed", [(12, 0), (40, 1)])
+def test_matches_finite_differences(n, seed):
+    pos, q, a, b = _system(n, seed)
+    dx, dq = FG.gradient(pos, q, a, b, block=7)
+    fx, fq = _fd(pos, q, a, b)
+    assert np.max(np.abs(dx - fx)) <= 1e-6 * max(1.0, np.max(np.abs(fx)))
+    assert np.max(np.abs(dq - fq)) <= 1e-6 * max(1.0, np.max(np.abs(fq)))
+
+
+def test_potential_only_loss_is_two_direct_sums():
+    pos, q, a, _ = _system(300, 2)
+    dx, dq = FG.gradient(pos, q, a, np.zeros((300, 3)))
+    phi_a, g_a = O.direct(pos, a)
+    _, g_q = O.direct(pos, q)
+    assert np.allclose(dq, phi_a, rtol=1e-12, atol=1e-12)
+    assert np.allclose(dx, a[:, None] * g_q + q[:, None] * g_a, rtol=1e-10, atol=1e-10)
+
+
+def test_translation_invariance_and_coincident_pairs():
+    pos, q, a, b = _system(200, 3)
+    pos[5] = pos[4]                     # a coincident pair contributes nothing, as in the direct sum
+    dx, _ = FG.gradient(pos, q, a, b)
+    assert np.all(np.isfinite(dx))
+    assert np.linalg.norm(dx.sum(axis=0)) <= 1e-9 * np.abs(dx).sum()
+
+
+def test_planted_slip_fails_finite_differences():
+    pos, q, a, b = _system(12, 4)
+    fx, _ = _fd(pos, q, a, b)
+    src = open(FG.__file__).read()
+    slip = src.replace("        dx[k0:k1] -= q[k0:k1, None] * np.einsum(\"kjc,j->kc\", tb_i, q)\n", "")
+    assert slip != src
+    ns = {}
+    exec(compile(slip, "force_grad_slip", "exec"), ns)
+    dx, _ = ns["gradient"](pos, q, a, b)
+    assert np.max(np.abs(dx - fx)) > 1e-3 * np.max(np.abs(fx))
