@@ -1,12 +1,12 @@
-"""Parent-neighbour-child interaction lists (U, V, W, X) and the FMM potential
-evaluated through them -- TEST INFRASTRUCTURE (oracle).
+"""Parent-neighbour-child interaction lists (U, V, W, X) and the FMM evaluated
+through them (potential and its gradient) -- TEST INFRASTRUCTURE (oracle).
 
 Section 2.1 of the paper names two ways to decide which cells are well
 separated: the size/distance ratio (the dual traversal of the rest of the
 oracle) and the parent-neighbour-child relationship of the adaptive octree,
 for which it refers to Cheng, Greengard and Rokhlin (1999).  This module
 restates the lists of that second approach from their definitions, by brute
-force over the boxes of a small tree, and evaluates the potential through them:
+force over the boxes of a small tree, and evaluates the FMM through them:
 
 * two boxes are *adjacent* when neither contains the other and their closed
   cubes share at least one point; the *neighbours* of a box are the adjacent
@@ -23,7 +23,10 @@ box gathers M2L from V(B) and the particles of X(B) (a particle's multipole
 about its own position is its charge alone, so its local expansion is the
 M2L of that monopole, exact up to the order p); L2L downwards; at a leaf the
 local expansion, the direct sum over U(B) and the multipoles of W(B) give the
-potential.  Every directed pair of particles is accounted for exactly once
+potential and its gradient.  A multipole is evaluated at a point x as the M2L
+to a local expansion about x read at x itself: its order-0 and order-1 terms
+sum every multipole term exactly, so this is the multipole's field and field
+gradient at x.  Every directed pair of particles is accounted for exactly once
 (``coverage`` checks it), and the result tends to the direct sum as p grows.
 Pure-Python loops over boxes: small trees only (a few thousand particles).
 """
@@ -31,7 +34,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import build_tree, l2l, l2p, m2l, m2m, m2p, ncoef, p2m
+from . import build_tree, l2l, l2p, m2l, m2m, ncoef, p2m
 
 
 class Boxes:
@@ -134,9 +137,9 @@ def coverage(tree, lists=None):
 
 
 def evaluate(pos, q, p: int, leaf_size: int = 16, theta: float = 0.5, tree=None, lists=None):
-    """Potential of every particle (input order) through the U/V/W/X lists.
-    theta only shapes the oracle tree's construction call; the lists use
-    adjacency alone."""
+    """(phi [n], grad phi [n, 3]) of every particle, input order, through the
+    U/V/W/X lists.  theta only shapes the oracle tree's construction call; the
+    lists use adjacency alone."""
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     q = np.ascontiguousarray(q, dtype=np.float64)
     tree = tree if tree is not None else build_tree(pos, leaf_size, theta)
@@ -172,19 +175,28 @@ def evaluate(pos, q, p: int, leaf_size: int = 16, theta: float = 0.5, tree=None,
             L[c] += l2l(p, L[par], ctr[c] - ctr[par])
     # at the leaves: local expansion + U direct + W multipoles
     phi_sorted = np.zeros(tree.n)
+    grad_sorted = np.zeros((tree.n, 3))
+    zero = np.zeros(3)
     for t in range(nc):
         if not bx.leaf[t]:
             continue
         for i in range(first[t], first[t] + count[t]):
-            v, _ = l2p(p, L[t], sp[i] - ctr[t])
+            v, g = l2p(p, L[t], sp[i] - ctr[t])
             for a in U[t]:
                 for j in range(first[a], first[a] + count[a]):
-                    r = np.sqrt(np.sum((sp[i] - sp[j]) ** 2))
+                    dv = sp[i] - sp[j]
+                    r = np.sqrt(np.sum(dv * dv))
                     if r > 0:
                         v += sq[j] / r
+                        g = g - sq[j] * dv / r ** 3
             for d in W[t]:
-                v += m2p(p, M[d], sp[i] - ctr[d])
+                vw, gw = l2p(p, m2l(p, M[d], sp[i] - ctr[d]), zero)
+                v += vw
+                g = g + gw
             phi_sorted[i] = v
+            grad_sorted[i] = g
     phi = np.zeros(tree.n)
+    grad = np.zeros((tree.n, 3))
     phi[tree.perm] = phi_sorted
-    return phi
+    grad[tree.perm] = grad_sorted
+    return phi, grad

@@ -4,7 +4,8 @@ Section 2.1, after Cheng, Greengard and Rokhlin 1999).
 The lists are pinned by what they must do, not by their own formulas:
 every directed particle pair is accounted for exactly once (direct, through a
 multipole, through a local expansion, or through the particles of an X box),
-the potential through them tends to the exact direct sum as p grows, and the
+the potential and its gradient through them tend to the exact direct sum as p
+grows, and the
 relations between the lists hold (U and V symmetric, X the dual of W, W and X
 empty on a tree whose leaves share one level).  A planted slip in any of the
 four definitions breaks the coverage."""
@@ -64,13 +65,16 @@ def test_one_level_tree_has_no_w_or_x():
     assert cov.min() == 1 and cov.max() == 1
 
 
-def test_potential_tends_to_the_direct_sum():
+def test_potential_and_field_tend_to_the_direct_sum():
     wl, t = _tree("plummer", 1200, 8)
     lists = uvwx.build_lists(t)
-    ref, _ = O.direct(wl.pos, wl.q)
-    err = [O.rel_l2(uvwx.evaluate(wl.pos, wl.q, p, tree=t, lists=lists), ref) for p in (2, 4, 6, 8)]
+    ref, gref = O.direct(wl.pos, wl.q)
+    res = [uvwx.evaluate(wl.pos, wl.q, p, tree=t, lists=lists) for p in (2, 4, 6, 8)]
+    err = [O.rel_l2(phi, ref) for phi, _ in res]
+    gerr = [O.rel_l2(g, gref) for _, g in res]
     assert all(b < a / 3 for a, b in zip(err, err[1:])), err
-    assert err[-1] <= 1e-5, err
+    assert all(b < a / 2 for a, b in zip(gerr, gerr[1:])), gerr
+    assert err[-1] <= 1e-5 and gerr[-1] <= 1e-4, (err, gerr)
 
 
 def _mutated(t, which):
