@@ -418,6 +418,44 @@ def p2p_form_variant(fmm, torch, pos, q, phi64, f64, flush, stream, ex, mutual: 
     return out
 
 
+def uvwx_variant(fmm, torch, pos, q, phi64, f64, flush, stream, flags: int, steps: int = 3):
+    """The mixed form on the same system with the lists built from the
+    parent-neighbour-child relationship (FMM_LISTS_UVWX, paper Section 2.1:
+    V lists by M2L, U and the W / X leaves by direct sums) instead of the
+    size/distance test: particles/s of build + evaluation, the list sizes, and
+    the error against the plain FP64 GPU path (a different FMM of the same
+    sum: the difference is both methods' truncation error)."""
+    n = pos.shape[0]
+    phi = torch.empty_like(phi64)
+    force = torch.empty_like(f64)
+    ts, te = [], []
+    info = None
+    for k in range(steps + 1):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        t = fmm.build_tree(pos, p=P, leaf_size=LEAF, theta=THETA, precision=3, flags=flags | fmm.LISTS_UVWX)
+        e1.record(stream)
+        t.evaluate(q, phi=phi, force=force)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        status = t.status()
+        info = t.info()
+        t.close()
+        if status != fmm.FMM_OK:
+            return {"error": f"status {status}"}
+        if k >= 1:
+            ts.append(e0.elapsed_time(e2))
+            te.append(e1.elapsed_time(e2))
+    ms = statistics.median(ts)
+    return {"execution": "staged kernels" + (", mutual near field" if flags & fmm.MUTUAL else ""),
+            "lists": "parent-neighbour-child (U/V/W/X, W and X as direct sums)",
+            "value": n / (ms * 1e-3), "ms_per_step": ms, "evaluate_ms": statistics.median(te), "steps": steps,
+            "dtype": PREC_DTYPE[3], "nm2l": int(info.nm2l), "np2p": int(info.np2p),
+            "rel_l2_vs_fp64_gpu": {"phi": float(((phi - phi64).norm() / phi64.norm()).item()),
+                                   "force": float(((force - f64).norm() / f64.norm()).item())}}
+
+
 def plummer_variant(fmm, torch, dev, flush, stream, steps: int = 3):
     """The mixed form on the Plummer configuration (1M particles, p = 8, leaf 64,
     theta = 0.4): particles/s of build + evaluation and its error against the
@@ -655,6 +693,15 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample_n)
+
+    # the parent-neighbour-child lists on the same system, after every other leg
+    # (an error there is reported in the variant and leaves the rest measured)
+    if not args.no_variants and args.precision == 3:
+        try:
+            variants["uvwx_lists"] = uvwx_variant(fmm, torch, pos, q, phi64, f64, flush, stream,
+                                                  fmm.MUTUAL if use_mutual(args) else 0)
+        except Exception as exc:   # noqa: BLE001
+            variants["uvwx_lists"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
 
     if rank == 0:
         out = {

@@ -77,6 +77,14 @@ extern "C" {
                                with floating-point atomics, so results are not bitwise
                                reproducible from run to run (within the FP32 bar of the
                                non-mutual form).  Ignored for FMM_PREC_FP64. */
+#define FMM_LISTS_UVWX  128 /* build the interaction lists from the parent-neighbour-child
+                               relationship (paper Section 2.1, after Cheng, Greengard and Rokhlin
+                               1999) instead of the size/distance acceptance test (theta is not
+                               used): M2L between the same-level cells of V lists (children of
+                               the parent's neighbours not adjacent to the cell), P2P between
+                               adjacent leaves (U lists) and, as direct sums, between a leaf and
+                               the leaves inside the cells of its W list (and back: X).  Every
+                               evaluation path runs on these lists unchanged. */
 
 /* stage indices for fmm_stage_times / fmm_stage_name */
 #define FMM_STAGE_KEYS      0   /* root cube, Morton keys, key sort */
@@ -109,7 +117,7 @@ typedef struct {
                             s = cell side, c = cell centre (Sections 2.1 and 4) */
     int32_t precision;   /* FMM_PREC_* */
     int32_t flags;       /* FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP | FMM_BUILD_FALLBACKS
-                            | FMM_TASK_GRAPH */
+                            | FMM_TASK_GRAPH | FMM_MUTUAL | FMM_LISTS_UVWX */
     int64_t timeout_ns;  /* budget of each bounded device-side wait; 0 = 2 s */
     /* Work-shape tunables (0 = the default; the values change the schedule,
        not the set of pair interactions): */

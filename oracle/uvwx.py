@@ -136,14 +136,43 @@ def coverage(tree, lists=None):
     return leaves, cov
 
 
-def evaluate(pos, q, p: int, leaf_size: int = 16, theta: float = 0.5, tree=None, lists=None):
+def pair_lists(tree, lists=None):
+    """The lists as (target, source) pairs with W and X taken as direct sums:
+    M2L pairs = V; P2P pairs = U, plus (b, L) and (L, b) for every leaf L
+    inside a box D of W(b) (X is the dual of W).  Both sorted by (target,
+    source); every P2P pair joins two leaves and the P2P relation is
+    symmetric."""
+    bx, U, V, W, X = lists if lists is not None else build_lists(tree)
+    m2l_pairs = sorted((b, c) for b in V for c in V[b])
+    p2p = set((b, a) for b in U for a in U[b])
+    for b, ws in W.items():
+        for d in ws:
+            for leaf in ([d] if bx.leaf[d] else [c for c in bx.descendants(d) if bx.leaf[c]]):
+                p2p.add((b, leaf))
+                p2p.add((leaf, b))
+    return (np.array(m2l_pairs, dtype=np.int32).reshape(-1, 2),
+            np.array(sorted(p2p), dtype=np.int32).reshape(-1, 2))
+
+
+def evaluate(pos, q, p: int, leaf_size: int = 16, theta: float = 0.5, tree=None, lists=None, wx: str = "expansions"):
     """(phi [n], grad phi [n, 3]) of every particle, input order, through the
-    U/V/W/X lists.  theta only shapes the oracle tree's construction call; the
-    lists use adjacency alone."""
+    U/V/W/X lists.  wx = "expansions": W by multipoles at the particles, X by
+    local expansions (Cheng et al.); wx = "direct": both by direct sums between
+    the leaves involved (``pair_lists``).  theta only shapes the oracle tree's
+    construction call; the lists use adjacency alone."""
+    if wx not in ("expansions", "direct"):
+        raise ValueError("wx must be 'expansions' or 'direct'")
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     q = np.ascontiguousarray(q, dtype=np.float64)
     tree = tree if tree is not None else build_tree(pos, leaf_size, theta)
     bx, U, V, W, X = lists if lists is not None else build_lists(tree)
+    if wx == "direct":
+        _, pp = pair_lists(tree, (bx, U, V, W, X))
+        U = {}
+        for b, a in pp:
+            U.setdefault(int(b), []).append(int(a))
+        W = {b: [] for b in W}
+        X = {c: [] for c in X}
     nc, K = tree.ncell, ncoef(p)
     sp = pos[tree.perm]          # sorted positions
     sq = q[tree.perm]

@@ -24,7 +24,7 @@ import numpy as np
 __all__ = [
     "FMM_OK", "FMM_ERR_ARG", "FMM_ERR_ALLOC", "FMM_ERR_CUDA", "FMM_ERR_TIMEOUT", "FMM_ERR_STATE",
     "PREC_FP64", "PREC_FP32_P2P", "PREC_FP32", "PREC_MIXED_TC", "OUT_FIELD", "STAGED", "TIMING", "NO_OVERLAP", "BUILD_FALLBACKS",
-    "TASK_GRAPH", "MUTUAL",
+    "TASK_GRAPH", "MUTUAL", "LISTS_UVWX",
     "FMMError", "Params", "TreeInfo", "Tree", "build_tree", "build_tree_batched", "evaluate", "library_path", "load",
     "capture_graph", "autotune_leaf_size", "autotune",
 ]
@@ -32,7 +32,7 @@ __all__ = [
 FMM_OK, FMM_ERR_ARG, FMM_ERR_ALLOC, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, FMM_ERR_STATE = 0, -1, -2, -3, -4, -5
 F64, F32 = 0, 1
 PREC_FP64, PREC_FP32_P2P, PREC_FP32, PREC_MIXED_TC = 0, 1, 2, 3
-OUT_FIELD, STAGED, TIMING, NO_OVERLAP, BUILD_FALLBACKS, TASK_GRAPH, MUTUAL = 1, 2, 4, 8, 16, 32, 64
+OUT_FIELD, STAGED, TIMING, NO_OVERLAP, BUILD_FALLBACKS, TASK_GRAPH, MUTUAL, LISTS_UVWX = 1, 2, 4, 8, 16, 32, 64, 128
 STAGE_NAMES = ("keys", "octree", "lists", "setup", "prepare", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p", "queue",
                "m2l_tc", "traversal", "classes", "p2p_list")
 

@@ -33,7 +33,7 @@ int check_params(const fmm_params* prm) {
         fmm_set_error("unknown precision %d", prm->precision);
         return FMM_ERR_ARG;
     }
-    if (prm->flags & ~(FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP | FMM_BUILD_FALLBACKS | FMM_TASK_GRAPH | FMM_MUTUAL)) { fmm_set_error("unknown flags 0x%x", prm->flags); return FMM_ERR_ARG; }
+    if (prm->flags & ~(FMM_OUT_FIELD | FMM_STAGED | FMM_TIMING | FMM_NO_OVERLAP | FMM_BUILD_FALLBACKS | FMM_TASK_GRAPH | FMM_MUTUAL | FMM_LISTS_UVWX)) { fmm_set_error("unknown flags 0x%x", prm->flags); return FMM_ERR_ARG; }
     if (prm->timeout_ns < 0) { fmm_set_error("timeout_ns < 0"); return FMM_ERR_ARG; }
     if (prm->p2p_item_records != 0 && (prm->p2p_item_records < 8 || prm->p2p_item_records > 65536)) {
         fmm_set_error("p2p_item_records=%d outside {0} and [8, 65536]", prm->p2p_item_records);

@@ -335,7 +335,9 @@ bool tc_supported(int p);
 inline bool p2p_mutual(const fmm_tree* t) {
     return (t->prm.flags & FMM_MUTUAL) && t->prm.precision != FMM_PREC_FP64;
 }
-int build_p2p_modes(fmm_tree* t, const int32_t* tgt, cudaStream_t st);   // tgt: target of every record
+int build_p2p_modes(fmm_tree* t, const int32_t* tgt, cudaStream_t st);
+// FMM_LISTS_UVWX: the M2L and P2P pairs from the parent-neighbour-child lists (uvwx.cu)
+int uvwx_lists(fmm_tree* t, int2** m2l, int64_t* nm, int2** p2p, int64_t* np, cudaStream_t st);   // tgt: target of every record
 int p2p_mutual_launch(fmm_tree* t, const float4* xq32, float4* acc, cudaStream_t st);
 // the mixed form runs as one task-graph launch unless a stage-by-stage flag is set
 inline bool tc_uses_dag(const fmm_tree* t) {

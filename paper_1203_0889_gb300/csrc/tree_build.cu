@@ -1363,82 +1363,89 @@ int build_tree_impl(fmm_tree* t, const void* pos, int pos_dtype, cudaStream_t st
     // --- a3: breadth-first dual traversal from (root, root)
     stage_begin(t, FMM_STAGE_LISTS, st);
     stage_begin(t, FMM_STAGE_TRAVERSAL, st);
-    size_t c_front = 1024, c_next = 1024, c_m = 1024, c_p = 1024;
-    int2 *front = nullptr, *next = nullptr, *m2l = nullptr, *p2p = nullptr;
-    if ((rc = grow(front, c_front = 0, std::max<size_t>(1024, nsys), 0, st))) return rc;
-    if ((rc = grow(next, c_next = 0, 1024, 0, st))) return rc;
-    if ((rc = grow(m2l, c_m = 0, 1024, 0, st))) return rc;
-    if ((rc = grow(p2p, c_p = 0, 1024, 0, st))) return rc;
-    TravCounters* ctr = nullptr;
-    if ((rc = dev_alloc(&ctr, 1, nullptr, st))) return rc;
-    FMM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(TravCounters), st));
-    k_init_frontier<<<nblk(nsys, 128), 128, 0, st>>>(nsys, front);
-    count_launch(t);
-    int64_t nf = nsys, nm = 0, npp = 0;
-    const double th2 = t->prm.theta * t->prm.theta;
-    {
-        // one cooperative launch for every round, with buffers sized from the
-        // cell count; the round-by-round loop below runs only on overflow
-        const size_t nc0 = (size_t)t->ncell;
-        const size_t cf = std::max<size_t>(1 << 20, 96 * nc0), cm = std::max<size_t>(1 << 22, 640 * nc0),
-                     cp = std::max<size_t>(1 << 20, 160 * nc0);
-        int2 *fa = nullptr, *fb = nullptr, *mm = nullptr, *pp = nullptr, *chpk = nullptr;
-        TravState* stt = nullptr;
-        bool ok = dev_alloc(&fa, cf, nullptr, st) == FMM_OK && dev_alloc(&fb, cf, nullptr, st) == FMM_OK &&
-                  dev_alloc(&mm, cm, nullptr, st) == FMM_OK && dev_alloc(&pp, cp, nullptr, st) == FMM_OK &&
-                  dev_alloc(&chpk, (size_t)t->ncell, nullptr, st) == FMM_OK &&
-                  dev_alloc((char**)&stt, sizeof(TravState), nullptr, st) == FMM_OK;
-        int per_sm = 0;
-        if (t->prm.flags & FMM_BUILD_FALLBACKS) ok = false;
-        if (ok) ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_coop, TRAV_THREADS, 0) ==
-                         cudaSuccess &&
-                     per_sm > 0;
-        if (ok) {
-            TravState h0 = {{(unsigned long long)nsys, 0ull, 0ull}, 0ull, 0ull, {0, 0}, 0};
-            FMM_CUDA_TRY(cudaMemcpyAsync(stt, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
-            k_init_frontier<<<nblk(nsys, 128), 128, 0, st>>>(nsys, fa);
-            k_child_pack<<<nblk(t->ncell, 256), 256, 0, st>>>(t->ncell, d.child_first, d.child_count, chpk);
-            unsigned long long a_cm = cm, a_cp = cp, a_cf = cf;
-            const int4* a_ic = d.icentre;
-            const int2* a_ch = chpk;
-            double a_th2 = th2;
-            void* args[] = {&fa, &fb, &a_ic, &a_ch, &a_th2, &mm, &pp, &stt, &a_cm, &a_cp, &a_cf};
-            dim3 grid(per_sm * t->num_sms), block(TRAV_THREADS);
-            FMM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_traverse_coop, grid, block, args, 0, st));
-            count_launch(t, 3);
-            TravState h;
-            FMM_CUDA_TRY(cudaMemcpyAsync(&h, stt, sizeof(h), cudaMemcpyDeviceToHost, st));
-            FMM_CUDA_TRY(cudaStreamSynchronize(st));
-            if (!h.ovf[0] && !h.ovf[1]) {
-                dev_free(m2l, st); dev_free(p2p, st);
-                m2l = mm; p2p = pp; c_m = cm; c_p = cp;
-                mm = pp = nullptr;
-                nm = (int64_t)h.nm2l;
-                npp = (int64_t)h.np2p;
-                nf = 0;   // done
-            }
-        }
-        dev_free(fa, st); dev_free(fb, st); dev_free(mm, st); dev_free(pp, st); dev_free(chpk, st);
-        if (stt) cudaFreeAsync(stt, st);
-    }
-    while (nf > 0) {
-        if ((rc = grow(next, c_next, (size_t)nf * 8, 0, st))) return rc;
-        if ((rc = grow(m2l, c_m, (size_t)(nm + nf), (size_t)nm, st))) return rc;
-        if ((rc = grow(p2p, c_p, (size_t)(npp + nf), (size_t)npp, st))) return rc;
-        FMM_CUDA_TRY(cudaMemsetAsync(&ctr->nnext, 0, 8, st));
-        k_traverse<<<nblk(nf, 256), 256, 0, st>>>(front, nf, d.level, d.ckey, d.child_first, d.child_count, th2,
-                                                    m2l, p2p, next, ctr);
+    int2 *m2l = nullptr, *p2p = nullptr;
+    int64_t nm = 0, npp = 0;
+    if (t->prm.flags & FMM_LISTS_UVWX) {
+        // the parent-neighbour-child lists instead of the size/distance test
+        if ((rc = uvwx_lists(t, &m2l, &nm, &p2p, &npp, st))) return rc;
+    } else {
+        size_t c_front = 1024, c_next = 1024, c_m = 1024, c_p = 1024;
+        int2 *front = nullptr, *next = nullptr;
+        if ((rc = grow(front, c_front = 0, std::max<size_t>(1024, nsys), 0, st))) return rc;
+        if ((rc = grow(next, c_next = 0, 1024, 0, st))) return rc;
+        if ((rc = grow(m2l, c_m = 0, 1024, 0, st))) return rc;
+        if ((rc = grow(p2p, c_p = 0, 1024, 0, st))) return rc;
+        TravCounters* ctr = nullptr;
+        if ((rc = dev_alloc(&ctr, 1, nullptr, st))) return rc;
+        FMM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(TravCounters), st));
+        k_init_frontier<<<nblk(nsys, 128), 128, 0, st>>>(nsys, front);
         count_launch(t);
-        TravCounters h;
-        FMM_CUDA_TRY(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
-        FMM_CUDA_TRY(cudaStreamSynchronize(st));
-        nm = (int64_t)h.nm2l;
-        npp = (int64_t)h.np2p;
-        nf = (int64_t)h.nnext;
-        std::swap(front, next);
-        std::swap(c_front, c_next);
+        int64_t nf = nsys;
+        const double th2 = t->prm.theta * t->prm.theta;
+        {
+            // one cooperative launch for every round, with buffers sized from the
+            // cell count; the round-by-round loop below runs only on overflow
+            const size_t nc0 = (size_t)t->ncell;
+            const size_t cf = std::max<size_t>(1 << 20, 96 * nc0), cm = std::max<size_t>(1 << 22, 640 * nc0),
+                         cp = std::max<size_t>(1 << 20, 160 * nc0);
+            int2 *fa = nullptr, *fb = nullptr, *mm = nullptr, *pp = nullptr, *chpk = nullptr;
+            TravState* stt = nullptr;
+            bool ok = dev_alloc(&fa, cf, nullptr, st) == FMM_OK && dev_alloc(&fb, cf, nullptr, st) == FMM_OK &&
+                      dev_alloc(&mm, cm, nullptr, st) == FMM_OK && dev_alloc(&pp, cp, nullptr, st) == FMM_OK &&
+                      dev_alloc(&chpk, (size_t)t->ncell, nullptr, st) == FMM_OK &&
+                      dev_alloc((char**)&stt, sizeof(TravState), nullptr, st) == FMM_OK;
+            int per_sm = 0;
+            if (t->prm.flags & FMM_BUILD_FALLBACKS) ok = false;
+            if (ok) ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_coop, TRAV_THREADS, 0) ==
+                             cudaSuccess &&
+                         per_sm > 0;
+            if (ok) {
+                TravState h0 = {{(unsigned long long)nsys, 0ull, 0ull}, 0ull, 0ull, {0, 0}, 0};
+                FMM_CUDA_TRY(cudaMemcpyAsync(stt, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+                k_init_frontier<<<nblk(nsys, 128), 128, 0, st>>>(nsys, fa);
+                k_child_pack<<<nblk(t->ncell, 256), 256, 0, st>>>(t->ncell, d.child_first, d.child_count, chpk);
+                unsigned long long a_cm = cm, a_cp = cp, a_cf = cf;
+                const int4* a_ic = d.icentre;
+                const int2* a_ch = chpk;
+                double a_th2 = th2;
+                void* args[] = {&fa, &fb, &a_ic, &a_ch, &a_th2, &mm, &pp, &stt, &a_cm, &a_cp, &a_cf};
+                dim3 grid(per_sm * t->num_sms), block(TRAV_THREADS);
+                FMM_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_traverse_coop, grid, block, args, 0, st));
+                count_launch(t, 3);
+                TravState h;
+                FMM_CUDA_TRY(cudaMemcpyAsync(&h, stt, sizeof(h), cudaMemcpyDeviceToHost, st));
+                FMM_CUDA_TRY(cudaStreamSynchronize(st));
+                if (!h.ovf[0] && !h.ovf[1]) {
+                    dev_free(m2l, st); dev_free(p2p, st);
+                    m2l = mm; p2p = pp; c_m = cm; c_p = cp;
+                    mm = pp = nullptr;
+                    nm = (int64_t)h.nm2l;
+                    npp = (int64_t)h.np2p;
+                    nf = 0;   // done
+                }
+            }
+            dev_free(fa, st); dev_free(fb, st); dev_free(mm, st); dev_free(pp, st); dev_free(chpk, st);
+            if (stt) cudaFreeAsync(stt, st);
+        }
+        while (nf > 0) {
+            if ((rc = grow(next, c_next, (size_t)nf * 8, 0, st))) return rc;
+            if ((rc = grow(m2l, c_m, (size_t)(nm + nf), (size_t)nm, st))) return rc;
+            if ((rc = grow(p2p, c_p, (size_t)(npp + nf), (size_t)npp, st))) return rc;
+            FMM_CUDA_TRY(cudaMemsetAsync(&ctr->nnext, 0, 8, st));
+            k_traverse<<<nblk(nf, 256), 256, 0, st>>>(front, nf, d.level, d.ckey, d.child_first, d.child_count, th2,
+                                                        m2l, p2p, next, ctr);
+            count_launch(t);
+            TravCounters h;
+            FMM_CUDA_TRY(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
+            FMM_CUDA_TRY(cudaStreamSynchronize(st));
+            nm = (int64_t)h.nm2l;
+            npp = (int64_t)h.np2p;
+            nf = (int64_t)h.nnext;
+            std::swap(front, next);
+            std::swap(c_front, c_next);
+        }
+        dev_free(front, st); dev_free(next, st); dev_free(ctr, st);
     }
-    dev_free(front, st); dev_free(next, st); dev_free(ctr, st);
     stage_end(t, FMM_STAGE_TRAVERSAL, st);
     t->nm2l = nm;
     t->np2p = npp;

@@ -48,7 +48,7 @@ def test_version_and_argument_errors(lib):
     assert lib.fmm_build_tree(None, 10, None, 0, C.byref(out), None) == fmm.FMM_ERR_ARG
     assert b"params" in lib.fmm_last_error()
     bad = [fmm.Params(-1, 64, 0.5, 0, 0, 0), fmm.Params(4, 0, 0.5, 0, 0, 0), fmm.Params(4, 64, 1.5, 0, 0, 0),
-           fmm.Params(4, 64, 0.5, 9, 0, 0), fmm.Params(4, 64, 0.5, 0, 128, 0), fmm.Params(21, 64, 0.5, 0, 0, 0),
+           fmm.Params(4, 64, 0.5, 9, 0, 0), fmm.Params(4, 64, 0.5, 0, 256, 0), fmm.Params(21, 64, 0.5, 0, 0, 0),
            fmm.Params(4, 64, 0.0, 0, 0, 0), fmm.Params(4, 64, 0.5, 0, 0, -1),
            fmm.Params(4, 64, 0.5, 0, 0, 0, 4, 0), fmm.Params(4, 64, 0.5, 0, 0, 0, 70000, 0),
            fmm.Params(4, 64, 0.5, 0, 0, 0, 0, -3), fmm.Params(4, 64, 0.5, 0, 0, 0, 0, 5000)]
@@ -83,10 +83,10 @@ def test_flag_values_match_the_header():
     txt = open(os.path.join(ROOT, "include", "fmm.h")).read()
     defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define FMM_(\w+)\s+(-?\d+)", txt)}
     for name in ("OUT_FIELD", "STAGED", "TIMING", "NO_OVERLAP", "BUILD_FALLBACKS", "TASK_GRAPH", "MUTUAL",
-                 "PREC_FP64", "PREC_FP32_P2P", "PREC_FP32", "PREC_MIXED_TC"):
+                 "LISTS_UVWX", "PREC_FP64", "PREC_FP32_P2P", "PREC_FP32", "PREC_MIXED_TC"):
         assert defs[name] == getattr(fmm, name), name
     flags = [defs[k] for k in ("OUT_FIELD", "STAGED", "TIMING", "NO_OVERLAP", "BUILD_FALLBACKS", "TASK_GRAPH",
-                               "MUTUAL")]
+                               "MUTUAL", "LISTS_UVWX")]
     assert sorted(flags) == [1 << i for i in range(len(flags))]
 
 

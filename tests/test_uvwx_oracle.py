@@ -101,3 +101,25 @@ def test_planted_mistakes_break_coverage(which):
     _, t = _tree("plummer", 800, 8)
     _, cov = uvwx.coverage(t, _mutated(t, which))
     assert cov.min() != 1 or cov.max() != 1
+
+
+def test_direct_wx_form():
+    """W and X as direct sums (the form of the GPU list builder): the P2P pairs
+    are symmetric leaf pairs, still cover every particle pair once with V, and
+    the result tends to the direct sum like the expansion form."""
+    wl, t = _tree("clustered", 1200, 16)
+    lists = uvwx.build_lists(t)
+    bx, U, V, Wl, X = lists
+    m2l, p2p = uvwx.pair_lists(t, lists)
+    pairs = set(map(tuple, p2p.tolist()))
+    assert all((b, a) in pairs for a, b in pairs)
+    assert all(bx.leaf[a] and bx.leaf[b] for a, b in pairs)
+    assert len(m2l) == sum(len(v) for v in V.values())
+    Ud = {}
+    for b, a in p2p:
+        Ud.setdefault(int(b), []).append(int(a))
+    _, cov = uvwx.coverage(t, (bx, Ud, V, {b: [] for b in Wl}, {c: [] for c in X}))
+    assert cov.min() == 1 and cov.max() == 1
+    ref, gref = O.direct(wl.pos, wl.q)
+    phi, g = uvwx.evaluate(wl.pos, wl.q, 8, tree=t, lists=lists, wx="direct")
+    assert O.rel_l2(phi, ref) <= 1e-5 and O.rel_l2(g, gref) <= 1e-4
