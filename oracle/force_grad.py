@@ -20,6 +20,8 @@ so, summing over ordered pairs (i, j), i != j:
 
 (the second and fourth terms are the reactions on k as a source).  Rows of
 pairs are processed in blocks, so a few thousand particles stay in memory.
+``dipole_direct`` gives the potential and gradient of point dipoles, the
+source type an FMM form of this gradient needs besides charges.
 """
 from __future__ import annotations
 
@@ -68,3 +70,27 @@ def gradient(pos, q, a, b, block: int = 256):
         tb_i = b[None, :, :] * r3[..., None] - 3.0 * d * (db_i * r5)[..., None]
         dx[k0:k1] -= q[k0:k1, None] * np.einsum("kjc,j->kc", tb_i, q)
     return dx, dq
+
+
+def dipole_direct(pos, dip, block: int = 256):
+    """Potential and its gradient at every particle of point dipoles dip_j at
+    x_j (pairs at distance 0 skipped): psi_k = sum_j dip_j . d_kj / r^3,
+    grad psi_k = sum_j T(d_kj) dip_j, d_kj = x_k - x_j.  A dipole p at x_j is
+    the limit of the charge pair +-|p|/e at x_j +- (e/2) p/|p|, and its
+    potential is p . grad_{x_j} (1 / |x - x_j|)."""
+    pos = np.asarray(pos, np.float64).reshape(-1, 3)
+    dip = np.asarray(dip, np.float64).reshape(-1, 3)
+    n = pos.shape[0]
+    psi = np.zeros(n)
+    grad = np.zeros((n, 3))
+    for k0 in range(0, n, block):
+        k1 = min(n, k0 + block)
+        d = pos[k0:k1, None, :] - pos[None, :, :]
+        r2 = np.sum(d * d, axis=-1)
+        ok = r2 > 0
+        rinv = np.where(ok, 1.0 / np.sqrt(np.where(ok, r2, 1.0)), 0.0)
+        r3, r5 = rinv ** 3, rinv ** 5
+        pd = np.einsum("kjc,jc->kj", d, dip)
+        psi[k0:k1] = np.sum(pd * r3, axis=1)
+        grad[k0:k1] = np.einsum("kj,jc->kc", r3, dip) - 3.0 * np.einsum("kj,kjc->kc", pd * r5, d)
+    return psi, grad

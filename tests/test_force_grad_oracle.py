@@ -83,3 +83,37 @@ def test_planted_slip_fails_finite_differences():
     exec(compile(slip, "force_grad_slip", "exec"), ns)
     dx, _ = ns["gradient"](pos, q, a, b)
     assert np.max(np.abs(dx - fx)) > 1e-3 * np.max(np.abs(fx))
+
+
+def test_dipole_direct_is_the_limit_of_charge_pairs():
+    """A dipole against the charge pair +-|p|/e at x_j +- (e/2) p/|p| (the
+    oracle's C direct sum), e -> 0."""
+    rng = np.random.default_rng(5)
+    pos = rng.random((30, 3))
+    dip = rng.standard_normal((30, 3))
+    psi, g = FG.dipole_direct(pos, dip)
+    e = 1e-5
+    for k in (0, 7):
+        others = [j for j in range(30) if j != k]
+        src = np.concatenate([pos[others] + 0.5 * e * dip[others], pos[others] - 0.5 * e * dip[others], pos[[k]]])
+        qs = np.concatenate([np.full(29, 1.0 / e), np.full(29, -1.0 / e), [0.0]])
+        phi, grad = O.direct_targets(src, qs, [58])
+        assert abs(phi[0] - psi[k]) <= 1e-6 * max(1.0, abs(psi[k]))
+        assert np.max(np.abs(grad[0] - g[k])) <= 1e-5 * max(1.0, np.max(np.abs(g[k])))
+
+
+def test_gradient_from_one_charge_pass_and_dipole_passes():
+    """The decomposition an FMM backward would run: dL/dq = phi^(a) + b . E +
+    psi and dL/dx = a grad phi + q grad phi^(a) - q H b + q grad psi, with psi
+    the potential of the dipoles -q_i b_i and the Hessian's columns the
+    gradients of the potentials of the dipoles -q_j e_c."""
+    pos, q, a, b = _system(80, 6)
+    dx, dq = FG.gradient(pos, q, a, b)
+    phi, g = O.direct(pos, q)
+    pha, ga = O.direct(pos, a)
+    psi, gpsi = FG.dipole_direct(pos, -q[:, None] * b)
+    H = np.stack([FG.dipole_direct(pos, -q[:, None] * np.eye(3)[c][None, :])[1] for c in range(3)], axis=2)
+    hb = np.einsum("kic,kc->ki", H, b)
+    assert np.allclose(dq, pha - np.einsum("kc,kc->k", b, g) + psi, rtol=1e-12, atol=1e-12)
+    assert np.allclose(dx, a[:, None] * g + q[:, None] * ga - q[:, None] * hb + q[:, None] * gpsi,
+                       rtol=1e-12, atol=1e-12)
