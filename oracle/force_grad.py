@@ -94,3 +94,32 @@ def dipole_direct(pos, dip, block: int = 256):
         psi[k0:k1] = np.sum(pd * r3, axis=1)
         grad[k0:k1] = np.einsum("kj,jc->kc", r3, dip) - 3.0 * np.einsum("kj,kjc->kc", pd * r5, d)
     return psi, grad
+
+
+def p2m_dipole(p, centre, pos, dip):
+    """Multipole expansion (the oracle's complex coefficients, index n*n + n + m)
+    of point dipoles dip_j at pos_j about centre: M_n^m = sum_j dip_j . grad
+    R_n^m(x_j - c).  The gradient of a regular solid harmonic is made of
+    harmonics one order lower: dz R_n^m = R_{n-1}^m, (dx + i dy) R_n^m =
+    -R_{n-1}^{m+1}, (dx - i dy) R_n^m = R_{n-1}^{m-1}, so
+    dip . grad R_n^m = dz_ R_{n-1}^m - (dx_ - i dy_)/2 R_{n-1}^{m+1}
+                       + (dx_ + i dy_)/2 R_{n-1}^{m-1}
+    (a harmonic whose |m| exceeds its degree is zero).  The harmonics of each
+    dipole's position are the unit-charge P2M of the order below."""
+    from . import hidx, ncoef, p2m
+    pos = np.asarray(pos, np.float64).reshape(-1, 3)
+    dip = np.asarray(dip, np.float64).reshape(-1, 3)
+    M = np.zeros(ncoef(p), dtype=np.complex128)
+    if p == 0:
+        return M
+    for x, d in zip(pos, dip):
+        Rl = p2m(p - 1, centre, x[None, :], np.ones(1))      # R_n^m(x - c), n <= p - 1
+
+        def r(n, m):
+            return Rl[hidx(n, m)] if abs(m) <= n else 0.0
+
+        up, down = -(d[0] - 1j * d[1]) / 2.0, (d[0] + 1j * d[1]) / 2.0
+        for n in range(1, p + 1):
+            for m in range(-n, n + 1):
+                M[hidx(n, m)] += d[2] * r(n - 1, m) + up * r(n - 1, m + 1) + down * r(n - 1, m - 1)
+    return M

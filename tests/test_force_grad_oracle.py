@@ -117,3 +117,32 @@ def test_gradient_from_one_charge_pass_and_dipole_passes():
     assert np.allclose(dq, pha - np.einsum("kc,kc->k", b, g) + psi, rtol=1e-12, atol=1e-12)
     assert np.allclose(dx, a[:, None] * g + q[:, None] * ga - q[:, None] * hb + q[:, None] * gpsi,
                        rtol=1e-12, atol=1e-12)
+
+
+def test_dipole_multipole_is_the_limit_of_charge_pairs():
+    """p2m_dipole against the P2M of the charge pair +-1/e at x +- (e/2) p."""
+    rng = np.random.default_rng(8)
+    c = np.array([0.5, 0.5, 0.5])
+    pos = c + 0.1 * rng.standard_normal((5, 3))
+    dip = rng.standard_normal((5, 3))
+    for p in (1, 4, 7):
+        M = FG.p2m_dipole(p, c, pos, dip)
+        e = 1e-5
+        pair = (O.p2m(p, c, pos + 0.5 * e * dip, np.full(5, 1.0 / e)) -
+                O.p2m(p, c, pos - 0.5 * e * dip, np.full(5, 1.0 / e)))
+        assert np.max(np.abs(M - pair)) <= 1e-6 * max(1.0, np.max(np.abs(M))), p
+
+
+def test_dipole_multipole_far_field():
+    """The dipoles' multipole, evaluated far away (M2P), converges in p to
+    their direct potential."""
+    rng = np.random.default_rng(9)
+    c = np.array([0.5, 0.5, 0.5])
+    pos = c + 0.05 * rng.standard_normal((8, 3))
+    dip = rng.standard_normal((8, 3))
+    y = np.array([1.4, -0.3, 0.9])
+    allpos = np.vstack([pos, y])
+    ref, _ = FG.dipole_direct(allpos, np.vstack([dip, np.zeros(3)]))
+    err = [abs(O.m2p(p, FG.p2m_dipole(p, c, pos, dip), y - c) - ref[-1]) for p in (2, 4, 6, 8)]
+    assert all(b < a / 5 for a, b in zip(err, err[1:])), err
+    assert err[-1] <= 1e-7 * abs(ref[-1]), err
