@@ -21,7 +21,10 @@ so, summing over ordered pairs (i, j), i != j:
 (the second and fourth terms are the reactions on k as a source).  Rows of
 pairs are processed in blocks, so a few thousand particles stay in memory.
 ``dipole_direct`` gives the potential and gradient of point dipoles, the
-source type an FMM form of this gradient needs besides charges.
+source type an FMM form of this gradient needs besides charges;
+``p2m_dipole`` their multipole, ``dipole_fmm`` their FMM through the oracle
+tree's lists, and ``fmm_gradient`` the whole gradient through the FMM (one
+charge pass with the charges a, the forward pass, four dipole passes).
 """
 from __future__ import annotations
 
@@ -123,3 +126,77 @@ def p2m_dipole(p, centre, pos, dip):
             for m in range(-n, n + 1):
                 M[hidx(n, m)] += d[2] * r(n - 1, m) + up * r(n - 1, m + 1) + down * r(n - 1, m - 1)
     return M
+
+
+def dipole_fmm(tree, pos, dip, p: int):
+    """Potential and gradient (input order) of point dipoles through the oracle
+    tree's dual-traversal lists: dipole P2M at the leaves, M2M, M2L over the
+    M2L pairs, L2L, then L2P plus the dipoles' direct terms over the P2P pairs
+    -- the charge FMM of Section 2.1 with the dipole as the source type."""
+    from . import l2l, l2p, m2l, m2m, ncoef
+    pos = np.asarray(pos, np.float64).reshape(-1, 3)
+    dip = np.asarray(dip, np.float64).reshape(-1, 3)
+    nc, K = tree.ncell, ncoef(p)
+    sp, sd = pos[tree.perm], dip[tree.perm]
+    first, count = tree.first, tree.count
+    ctr = tree.centres()
+    leaf = tree.child_count == 0
+    M = np.zeros((nc, K), dtype=np.complex128)
+    for c in np.argsort(-tree.level, kind="stable"):
+        if leaf[c]:
+            sl = slice(first[c], first[c] + count[c])
+            M[c] = p2m_dipole(p, ctr[c], sp[sl], sd[sl])
+        else:
+            for ch in range(tree.child_first[c], tree.child_first[c] + tree.child_count[c]):
+                M[c] += m2m(p, M[ch], ctr[ch] - ctr[c])
+    L = np.zeros((nc, K), dtype=np.complex128)
+    for t, s_ in tree.m2l:
+        L[t] += m2l(p, M[s_], ctr[t] - ctr[s_])
+    for c in np.argsort(tree.level, kind="stable"):
+        par = int(tree.parent[c])
+        if par >= 0:
+            L[c] += l2l(p, L[par], ctr[c] - ctr[par])
+    psi = np.zeros(tree.n)
+    grad = np.zeros((tree.n, 3))
+    near = {}
+    for t, s_ in tree.p2p:
+        near.setdefault(int(t), []).append(int(s_))
+    for t in np.nonzero(leaf)[0]:
+        ti = np.arange(first[t], first[t] + count[t])
+        for i in ti:
+            psi[i], grad[i] = l2p(p, L[t], sp[i] - ctr[t])
+        src = np.concatenate([np.arange(first[s_], first[s_] + count[s_]) for s_ in near.get(int(t), [])]) \
+            if near.get(int(t)) else np.zeros(0, np.int64)
+        if len(src):
+            d = sp[ti, None, :] - sp[None, src, :]
+            r2 = np.sum(d * d, axis=-1)
+            ok = r2 > 0
+            rinv = np.where(ok, 1.0 / np.sqrt(np.where(ok, r2, 1.0)), 0.0)
+            r3, r5 = rinv ** 3, rinv ** 5
+            pd = np.einsum("kjc,jc->kj", d, sd[src])
+            psi[ti] += np.sum(pd * r3, axis=1)
+            grad[ti] += np.einsum("kj,jc->kc", r3, sd[src]) - 3.0 * np.einsum("kj,kjc->kc", pd * r5, d)
+    out_psi = np.zeros(tree.n)
+    out_grad = np.zeros((tree.n, 3))
+    out_psi[tree.perm] = psi
+    out_grad[tree.perm] = grad
+    return out_psi, out_grad
+
+
+def fmm_gradient(tree, pos, q, a, b, p: int):
+    """(dL/dx, dL/dq) of the loss above with every sum through the FMM of the
+    oracle tree: one charge pass with the charges a, the forward pass, and
+    four dipole passes (the dipoles -q_i b_i, and -q_j e_c for the columns of
+    the Hessian), combined as dL/dq = phi^(a) + b . E + psi and
+    dL/dx = a grad phi + q grad phi^(a) - q H b + q grad psi."""
+    q = np.asarray(q, np.float64)
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64).reshape(-1, 3)
+    phi, g = tree.evaluate(p, q)
+    pha, ga = tree.evaluate(p, a)
+    psi, gpsi = dipole_fmm(tree, pos, -q[:, None] * b, p)
+    H = np.stack([dipole_fmm(tree, pos, -q[:, None] * np.eye(3)[c][None, :], p)[1] for c in range(3)], axis=2)
+    hb = np.einsum("kic,kc->ki", H, b)
+    dq = pha - np.einsum("kc,kc->k", b, g) + psi
+    dx = a[:, None] * g + q[:, None] * ga - q[:, None] * hb + q[:, None] * gpsi
+    return dx, dq

@@ -146,3 +146,29 @@ def test_dipole_multipole_far_field():
     err = [abs(O.m2p(p, FG.p2m_dipole(p, c, pos, dip), y - c) - ref[-1]) for p in (2, 4, 6, 8)]
     assert all(b < a / 5 for a, b in zip(err, err[1:])), err
     assert err[-1] <= 1e-7 * abs(ref[-1]), err
+
+
+def test_dipole_fmm_and_fmm_gradient_converge():
+    """The dipole-source FMM through the oracle tree's lists tends to the
+    dipoles' direct sum (exactly equal with no M2L pair), and the FMM form of
+    the force-loss gradient tends to the closed form."""
+    import workloads as W
+    wl = W.make_workload("plummer", n=600)
+    rng = np.random.default_rng(3)
+    a, b = rng.standard_normal(600), rng.standard_normal((600, 3))
+    psi0, g0 = FG.dipole_direct(wl.pos, b)
+    t0 = O.build_tree(wl.pos, 16, 1e-6)
+    assert len(t0.m2l) == 0
+    psi, g = FG.dipole_fmm(t0, wl.pos, b, 2)
+    assert O.rel_l2(psi, psi0) <= 1e-12 and O.rel_l2(g, g0) <= 1e-12
+    t = O.build_tree(wl.pos, 16, 0.5)
+    e_psi, e_g = [], []
+    for p in (2, 4, 6):
+        psi, g = FG.dipole_fmm(t, wl.pos, b, p)
+        e_psi.append(O.rel_l2(psi, psi0))
+        e_g.append(O.rel_l2(g, g0))
+    assert all(y < x / 2 for x, y in zip(e_psi, e_psi[1:])), e_psi
+    assert all(y < x / 2 for x, y in zip(e_g, e_g[1:])), e_g
+    dx0, dq0 = FG.gradient(wl.pos, wl.q, a, b)
+    ex = [O.rel_l2(FG.fmm_gradient(t, wl.pos, wl.q, a, b, p)[0], dx0) for p in (2, 6)]
+    assert ex[1] < ex[0] / 4 and ex[1] <= 2e-3, ex
